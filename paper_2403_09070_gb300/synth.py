@@ -1,0 +1,226 @@
+"""Seeded synthetic placement problems shaped like the paper's benchmarks.
+
+This module only *draws* inputs: netlists (pin/net CSR), per-die instance
+sizes, pin offsets and positions.  It holds none of the placement method's
+arithmetic (no density, no wirelength, no transform), so that both the CUDA
+path and the CPU oracle can take their inputs from it without sharing any part
+of the computation they are compared on.
+
+The paper's ICCAD 2023 contest cases and RISC-V designs (Tab. "benchmark-stat",
+Tab. "risc-stat") are not available; these recipes stand in for them:
+
+* net degree: 2 (55 %), 3-4 (25 %), 5-16 (17 %), 17-64 (3 %), P(d) ~ d^-2
+  inside each bucket (about 4.2 pins per net);
+* every pin of a net sits on a distinct instance drawn uniformly; macros take
+  1 % of the pins ("macros have many pins", Sec. III-A preconditioning text);
+* pin offsets uniform inside the bottom-die footprint, top offsets 0.8x;
+* std cells: bottom width uniform in 1..8 sites of 1.0, height (row) 1.0; top
+  die scaled by 0.8 in both dimensions (heterogeneous technology nodes);
+* macros: squares whose total area is 20 % of one die, split equally, 0.8x on
+  the top die;
+* positions: x, y uniform inside the die, z uniform in [d_z/4, 3 d_z/4]
+  ("uniform") or normal about the centre with sigma = 0.1 of each extent
+  ("center", the paper's initialisation, Sec. III-A free fillers text);
+* gamma = 4 bin widths, lambda = 1e-3, HBT cost beta = 10, HBT pitch 1.0,
+  row heights 0.8 (top) / 1.0 (bottom).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# Degree buckets (inclusive ranges) and their probabilities.
+_DEG_BUCKETS = ((2, 2, 0.55), (3, 4, 0.25), (5, 16, 0.17), (17, 64, 0.03))
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """Sizes of one synthetic workload."""
+
+    name: str
+    n_std: int
+    n_macro: int
+    n_net: int
+    die: float  # square die side, both dies share the outline
+    nx: int
+    ny: int
+    nz: int
+    seed: int
+    n_hifanout: int = 0  # extra nets with log-uniform 2k..20k pins
+    n_filler_fixed: int = 0  # z-fixed fillers (pinless), half per die
+    n_filler_free: int = 0  # free fillers (pinless)
+
+
+WORKLOADS = {
+    # 2,000 std cells + 4 macros, 2,100 nets, 200x200 dies, 64x64x2 bins.
+    "cells_2k": Workload("cells_2k", 2000, 4, 2100, 200.0, 64, 64, 2, 1),
+    # 200k std cells + 20 macros, 210k nets, 3,000x3,000 dies, 256x256x4 bins.
+    "cells_200k": Workload("cells_200k", 200_000, 20, 210_000, 3000.0, 256, 256, 4, 2),
+    # 1M std cells + 60 macros, 1.05M nets, 6,700x6,700 dies, 512x512x4 bins.
+    "cells_1m": Workload("cells_1m", 1_000_000, 60, 1_050_000, 6700.0, 512, 512, 4, 3),
+    # 4M std cells + 200 macros, 4.2M nets + 200 high-fanout nets, 1024x1024x4.
+    "cells_4m_skewed": Workload("cells_4m_skewed", 4_000_000, 200, 4_200_000, 13400.0,
+                                1024, 1024, 4, 5, n_hifanout=200),
+}
+
+
+def _degrees(rng: np.random.Generator, n: int) -> np.ndarray:
+    probs = np.array([b[2] for b in _DEG_BUCKETS])
+    which = rng.choice(len(_DEG_BUCKETS), size=n, p=probs / probs.sum())
+    deg = np.empty(n, dtype=np.int64)
+    for k, (lo, hi, _) in enumerate(_DEG_BUCKETS):
+        sel = np.nonzero(which == k)[0]
+        d = np.arange(lo, hi + 1)
+        w = 1.0 / d.astype(np.float64) ** 2
+        deg[sel] = rng.choice(d, size=sel.size, p=w / w.sum())
+    return deg
+
+
+def _distinct_pins(rng, net_start, n_std, n_macro, macro_frac):
+    """Draw one instance per pin so that no net holds an instance twice."""
+    n_net = net_start.size - 1
+    deg = np.diff(net_start)
+    P = int(net_start[-1])
+    net_of = np.repeat(np.arange(n_net, dtype=np.int64), deg)
+    n_inst = n_std + n_macro
+
+    def draw(k):
+        if n_macro > 0:
+            mac = rng.random(k) < macro_frac
+            return np.where(mac, n_std + rng.integers(0, n_macro, k), rng.integers(0, n_std, k))
+        return rng.integers(0, n_std, k)
+
+    inst = draw(P)
+    for it in range(200):
+        key = net_of * n_inst + inst
+        order = np.argsort(key, kind="stable")
+        dup = np.zeros(P, dtype=bool)
+        ks = key[order]
+        dup[order[1:]] = ks[1:] == ks[:-1]
+        nd = int(dup.sum())
+        if nd == 0:
+            return inst
+        idx = np.nonzero(dup)[0]
+        if it < 100:
+            inst[idx] = draw(nd)
+        else:  # fall back to std cells only (a net asked for more macros than exist)
+            inst[idx] = rng.integers(0, n_std, nd)
+    raise RuntimeError("could not draw distinct pins")
+
+
+def make_problem(wl: Workload | str, positions: str = "uniform", origin=(0.0, 0.0),
+                 seed: int | None = None, n_std: int | None = None,
+                 n_net: int | None = None) -> dict:
+    """Return a problem dict (numpy arrays + scalars) and positions x, y, z.
+
+    Keys follow the C ABI's ``place3d_problem`` field names.  ``positions`` is
+    "uniform" or "center".  ``origin`` shifts the die outline (and positions).
+    ``n_std``/``n_net`` override the workload's counts (smaller samples).
+    """
+    if isinstance(wl, str):
+        wl = WORKLOADS[wl]
+    if n_std is not None or n_net is not None:
+        wl = dataclasses.replace(wl, n_std=n_std or wl.n_std, n_net=n_net or wl.n_net)
+    rng = np.random.default_rng(wl.seed if seed is None else seed)
+    d = float(wl.die)
+    n_std, n_mac = wl.n_std, wl.n_macro
+    n_fill = wl.n_filler_fixed + wl.n_filler_free
+    n_inst = n_std + n_mac + n_fill
+
+    # --- sizes (bottom die; top die 0.8x) ---
+    w_bot = np.empty(n_inst)
+    h_bot = np.empty(n_inst)
+    w_bot[:n_std] = rng.integers(1, 9, n_std).astype(np.float64)
+    h_bot[:n_std] = 1.0
+    if n_mac:
+        side = math.sqrt(0.2 * d * d / n_mac)
+        w_bot[n_std:n_std + n_mac] = side
+        h_bot[n_std:n_std + n_mac] = side
+    if n_fill:
+        # Fillers: pinless squares of a few sites, identical on both dies.
+        w_bot[n_std + n_mac:] = 4.0
+        h_bot[n_std + n_mac:] = 4.0
+    w_top = 0.8 * w_bot
+    h_top = 0.8 * h_bot
+    if n_fill:
+        w_top[n_std + n_mac:] = w_bot[n_std + n_mac:]
+        h_top[n_std + n_mac:] = h_bot[n_std + n_mac:]
+    is_macro = np.zeros(n_inst, dtype=np.uint8)
+    is_macro[n_std:n_std + n_mac] = 1
+    z_fixed = np.zeros(n_inst, dtype=np.uint8)
+    z_fixed[n_std + n_mac:n_std + n_mac + wl.n_filler_fixed] = 1
+
+    # --- netlist ---
+    deg = _degrees(rng, wl.n_net)
+    if wl.n_hifanout:
+        hf = np.exp(rng.uniform(math.log(2000), math.log(20000), wl.n_hifanout)).astype(np.int64)
+        deg = np.concatenate([deg, hf])
+    net_start = np.zeros(deg.size + 1, dtype=np.int64)
+    np.cumsum(deg, out=net_start[1:])
+    pin_inst = _distinct_pins(rng, net_start, n_std, n_mac, 0.01)
+
+    # --- instance order: interleave macros/fillers among cells ---
+    perm = rng.permutation(n_inst)  # new index of old instance k is perm[k]
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(n_inst)
+    w_bot, h_bot, w_top, h_top = (a[inv] for a in (w_bot, h_bot, w_top, h_top))
+    is_macro, z_fixed = is_macro[inv], z_fixed[inv]
+    pin_inst = perm[pin_inst]
+
+    # --- pin offsets inside the bottom footprint; top offsets 0.8x ---
+    P = pin_inst.size
+    off_bx = (rng.random(P) - 0.5) * w_bot[pin_inst]
+    off_by = (rng.random(P) - 0.5) * h_bot[pin_inst]
+    off_tx = 0.8 * off_bx
+    off_ty = 0.8 * off_by
+
+    prob = dict(
+        n_inst=n_inst, is_macro=is_macro, z_fixed=z_fixed,
+        w_bot=w_bot, h_bot=h_bot, w_top=w_top, h_top=h_top,
+        n_net=int(deg.size), n_pin=int(P),
+        net_start=net_start.astype(np.int32), pin_inst=pin_inst.astype(np.int32),
+        off_bx=off_bx, off_by=off_by, off_tx=off_tx, off_ty=off_ty,
+        xl=float(origin[0]), yl=float(origin[1]),
+        xh=float(origin[0]) + d, yh=float(origin[1]) + d,
+        nx=wl.nx, ny=wl.ny, nz=wl.nz,
+        gamma=4.0 * d / wl.nx, gamma_z=0.0, lam=1e-3,
+        beta=10.0, w_hbt=1.0, rh_top=0.8, rh_bot=1.0,
+        workload=wl.name,
+    )
+    x, y, z = draw_positions(rng, prob, positions)
+    prob["x"], prob["y"], prob["z"] = x, y, z
+    return prob
+
+
+def depth_range(prob: dict) -> tuple[float, float]:
+    """(z_lo, z_hi) = (d_z/4, 3 d_z/4) of the problem's grid (Sec. V-A bin depth)."""
+    wb = (prob["xh"] - prob["xl"]) / prob["nx"]
+    hb = (prob["yh"] - prob["yl"]) / prob["ny"]
+    dz = prob["nz"] * 0.5 * (wb + hb)
+    return 0.25 * dz, 0.75 * dz
+
+
+def draw_positions(rng: np.random.Generator, prob: dict, kind: str = "uniform"):
+    n = prob["n_inst"]
+    xl, yl, xh, yh = prob["xl"], prob["yl"], prob["xh"], prob["yh"]
+    zlo, zhi = depth_range(prob)
+    w = np.maximum(prob["w_bot"], prob["w_top"])
+    h = np.maximum(prob["h_bot"], prob["h_top"])
+    if kind == "uniform":
+        x = xl + w / 2 + rng.random(n) * np.maximum(xh - xl - w, 0.0)
+        y = yl + h / 2 + rng.random(n) * np.maximum(yh - yl - h, 0.0)
+        z = zlo + rng.random(n) * (zhi - zlo)
+    elif kind == "center":
+        x = np.clip(rng.normal(0.5 * (xl + xh), 0.1 * (xh - xl), n), xl, xh)
+        y = np.clip(rng.normal(0.5 * (yl + yh), 0.1 * (yh - yl), n), yl, yh)
+        z = np.clip(rng.normal(0.5 * (zlo + zhi), 0.2 * (zhi - zlo), n), zlo, zhi)
+    else:
+        raise ValueError(kind)
+    zf = prob["z_fixed"].astype(bool)
+    if zf.any():  # z-fixed fillers sit at the centre depth of their die
+        idx = np.nonzero(zf)[0]
+        z[idx[0::2]] = zlo
+        z[idx[1::2]] = zhi
+    return x, y, z
