@@ -1,0 +1,200 @@
+/*
+ * place3d: one evaluation of the 3D die-to-die placement objective and its
+ * gradient on a GB300 GPU (sm_103a), after "Analytical Heterogeneous
+ * Die-to-Die 3D Placement with Macros" (arXiv 2403.09070).
+ *
+ * The objective (eq. analytical-placement with the wirelength of eq.
+ * wl-model) is
+ *
+ *     f(x, y, z) = sum_e W^_e,Bi + alpha sum_e p^_e(z) + lambda U^
+ *
+ * - W^_e,Bi: bistratal weighted-average wirelength, eq. wl-obj with every
+ *   partial HPWL p() smoothed by eq. wa-model-approx (Sec. III-A);
+ * - p^_e(z): the WA depth span that models the HBT cost (eq. wl-model);
+ * - U^: eDensity3D energy (Sec. III-A), density by eq. density-map-accum
+ *   (cells) and Theorem 1 (macros), potential and field by eqs. density-coef,
+ *   poisson-sol-potential and possion-sol-force.
+ *
+ * The gradient returned is (d/dx, d/dy, g + alpha d p^(z)/dz) of the
+ * wirelength (eq. fda-normalize, with g the normalised FD depth gradient of
+ * eq. fda-grad) plus lambda times the density force (field gather).
+ *
+ * Conventions for every entry point:
+ * - Return value: PLACE3D_OK (0) or a negative PLACE3D_ERR_* code; the
+ *   message is available from place3d_last_error().
+ * - A handle is not thread-safe; use one handle per host thread.  All GPU
+ *   work of a handle is enqueued on the stream given at creation.
+ * - Device pointers passed in are used in place on that stream (no copy);
+ *   host pointers are copied.  The caller owns every buffer it passes.
+ */
+#ifndef PLACE3D_H
+#define PLACE3D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define PLACE3D_OK 0
+#define PLACE3D_ERR_INVALID_ARG (-1) /* NULL pointer, bad size, bad enum */
+#define PLACE3D_ERR_BAD_CSR (-2)     /* net_start/pin_inst inconsistent */
+#define PLACE3D_ERR_OUT_OF_RANGE (-3) /* value outside its domain (checks) */
+#define PLACE3D_ERR_CUDA (-4)        /* a CUDA runtime call failed */
+#define PLACE3D_ERR_OOM (-5)         /* device allocation failed */
+#define PLACE3D_ERR_UNSUPPORTED (-7) /* mode not available on this device */
+
+/* ---- precision modes (place3d_problem.precision) ---- */
+#define PLACE3D_FP64 0    /* every step in FP64 (the plain path) */
+#define PLACE3D_FP32 1    /* FP32 steps, FP32 CUDA-core transforms, FP64 scalars */
+#define PLACE3D_FP32_TC 2 /* FP32 steps, split-BF16 tcgen05 transforms */
+
+/* ---- flags (place3d_problem.flags) ---- */
+#define PLACE3D_FLAG_CHECKS 1 /* validate positions on every set_positions */
+
+/* ---- dtype and memory kind of caller buffers ---- */
+#define PLACE3D_F64 0
+#define PLACE3D_F32 1
+#define PLACE3D_MEM_HOST 0
+#define PLACE3D_MEM_DEVICE 1
+
+/*
+ * Problem statement (Sec. II-B "Problem Formulation", Sec. III-A, Sec. V-A).
+ * All arrays are HOST arrays, read during place3d_create() only (deep copy).
+ *
+ * Instances i in [0, n_inst): std cells, macros and fillers.  Sizes are per
+ * die: (w_bot, h_bot) on the bottom die, (w_top, h_top) on the top die
+ * (eq. std-size-tech for cells; eq. macro-size-tech interpolates macros).
+ * Fillers are instances without pins; z_fixed marks instances whose
+ * z-gradient is forced to 0 (Sec. III-A z-fixed fillers).
+ *
+ * Netlist: CSR over nets; net e owns pins [net_start[e], net_start[e+1]),
+ * pin p sits on instance pin_inst[p] at offset (pin_off_bot_x/y) from its
+ * centre on the bottom die and (pin_off_top_x/y) on the top die (offsets
+ * follow the partition, Sec. III-A).  An instance may hold at most one pin
+ * of a net.  Nets with fewer than 2 pins contribute nothing.
+ *
+ * Region and bins: Omega = [xl,xh] x [yl,yh] x [0,d_z] with N_x x N_y x N_z
+ * bins, w_b = (xh-xl)/N_x, h_b = (yh-yl)/N_y, d_b = (w_b+h_b)/2 and
+ * d_z = N_z d_b (Sec. V-A).  Instance depth is d_z/2, movable
+ * z in [d_z/4, 3 d_z/4] (Sec. III-A).
+ *
+ * gamma: WA smoothing of x and y; gamma_z: of z (<= 0 means gamma).
+ * alpha: HBT weight of eq. wl-model (place3d_alpha() gives the paper's
+ * default); lambda: density weight of eq. analytical-placement.
+ */
+typedef struct place3d_problem {
+  int32_t n_inst;
+  const uint8_t *is_macro; /* [n_inst] 1 = macro */
+  const uint8_t *z_fixed;  /* [n_inst] 1 = z-gradient forced to 0; may be NULL */
+  const double *w_bot, *h_bot, *w_top, *h_top; /* [n_inst] */
+  int32_t n_net, n_pin;
+  const int32_t *net_start; /* [n_net+1], net_start[0]=0, nondecreasing, last=n_pin */
+  const int32_t *pin_inst;  /* [n_pin], values in [0, n_inst) */
+  const double *pin_off_bot_x, *pin_off_bot_y; /* [n_pin] offsets on the bottom die */
+  const double *pin_off_top_x, *pin_off_top_y; /* [n_pin] offsets on the top die */
+  double xl, yl, xh, yh;
+  int32_t nx, ny, nz;
+  double gamma, gamma_z;
+  double alpha, lambda;
+  int32_t precision; /* PLACE3D_FP64 | PLACE3D_FP32 | PLACE3D_FP32_TC */
+  int32_t flags;     /* PLACE3D_FLAG_* */
+} place3d_problem;
+
+/* Scalars of one evaluation (FP64). */
+typedef struct place3d_result {
+  double obj;      /* f = wl_bi + alpha wl_z + lambda energy */
+  double wl_bi;    /* sum_e W^_e,Bi (eq. wl-obj on WA-smoothed spans) */
+  double wl_z;     /* sum_e p^_e(z) (eq. wl-model, unscaled) */
+  double energy;   /* U^ = 1/2 vol(b) sum_b rho_b phi_b */
+  double hpwl_d2d; /* exact D2D HPWL, sum_e W_ex + W_ey (eq. wl-obj) */
+  double n_cross;  /* #crossing nets = sum_e C_e (Sec. II-B), i.e. #HBTs */
+  double g_scale;  /* (S_x + S_y) / (2 S_z) of eq. fda-normalize (0 if S_z = 0) */
+  double s_x, s_y, s_z; /* L1 norms of the WL gradient in x, y and of eq. fda-grad */
+} place3d_result;
+
+typedef struct place3d_handle place3d_handle;
+
+/* Validate and deep-copy the problem, allocate every device buffer on
+ * `device`, build the net-degree buckets and the transform matrices.
+ * cuda_stream: a cudaStream_t of that device, or NULL for the default
+ * stream.  On success *out owns all device memory (freed by destroy).
+ * Errors: INVALID_ARG, BAD_CSR, OOM, CUDA, UNSUPPORTED (FP32_TC needs an
+ * sm_103 device and N_x, N_y multiples of 128). */
+int place3d_create(const place3d_problem *prob, int device, void *cuda_stream,
+                   place3d_handle **out);
+
+/* out[6] = {w_b, h_b, d_b, d_x, d_y, d_z} (Sec. V-A). */
+int place3d_geometry(const place3d_handle *h, double out[6]);
+
+/* HBT penalty factor of Sec. V-A: alpha0 (d_x eta^2 / d_z) log(90 beta eta - 1)
+ * with alpha0 = 3.5e-3 and eta = 2 w_hbt / (rh_top + rh_bot). */
+double place3d_alpha(double dx, double dz, double beta, double w_hbt,
+                     double rh_top, double rh_bot);
+
+/* Set instance centres x, y, z ([n_inst] each, dtype PLACE3D_F32/F64, mem
+ * HOST or DEVICE).  Device buffers must stay valid until the next
+ * evaluation has been enqueued; they are read on the handle's stream.
+ * z is expected in [d_z/4, 3 d_z/4]; with PLACE3D_FLAG_CHECKS a value
+ * outside, or a non-finite coordinate, returns OUT_OF_RANGE (after a sync). */
+int place3d_set_positions(place3d_handle *h, const void *x, const void *y,
+                          const void *z, int dtype, int mem);
+
+/* Enqueue one evaluation of f and its gradient at the current positions.
+ * gx, gy, gz: [n_inst] outputs (dtype, mem) or all NULL (gradient kept on
+ * the device only).  If out != NULL the call synchronises the stream and
+ * fills *out; with out == NULL it returns right after enqueueing and
+ * place3d_get_result() fetches the scalars later.  Host gradient buffers
+ * imply a synchronisation. */
+int place3d_eval_objective_and_grad(place3d_handle *h, place3d_result *out,
+                                    void *gx, void *gy, void *gz, int dtype,
+                                    int mem);
+
+/* Synchronise the handle's stream and return the scalars of the last
+ * evaluation. */
+int place3d_get_result(place3d_handle *h, place3d_result *out);
+
+/* Read an intermediate map of the last evaluation into dst (host or device,
+ * [N_z][N_y][N_x] with x fastest):
+ *   PLACE3D_MAP_RHO_FIXED: int64 density counts of 2^-36 (the fixed-point
+ *     density of eq. density-map-accum + Theorem 1), 8 bytes per bin;
+ *   PLACE3D_MAP_EX/EY/EZ: the field of eq. possion-sol-force at bin centres,
+ *     in the handle's precision (8 bytes per bin for FP64, else 4).
+ * Errors: INVALID_ARG for an unknown map or NULL dst. */
+#define PLACE3D_MAP_RHO_FIXED 0
+#define PLACE3D_MAP_EX 1
+#define PLACE3D_MAP_EY 2
+#define PLACE3D_MAP_EZ 3
+int place3d_copy_map(place3d_handle *h, int which, void *dst, int mem);
+
+/* Read the per-instance wirelength gradient parts of the last evaluation as
+ * FP64 host arrays [n_inst] (any may be NULL): d sum W^_Bi / dx, / dy, the FD
+ * depth gradient of eq. fda-grad, and d sum p^_e(z) / dz. */
+int place3d_copy_wl_parts(place3d_handle *h, double *gx, double *gy,
+                          double *gfd, double *gwaz);
+
+/* Per-stage GPU timing.  With profiling on, every evaluation records CUDA
+ * events around its stages on the stream they run on; place3d_stage_times()
+ * returns the accumulated milliseconds and launch counts per stage since the
+ * last reset (arrays of length place3d_num_stages()), and the stage names. */
+int place3d_set_profiling(place3d_handle *h, int on);
+int place3d_num_stages(void);
+const char *place3d_stage_name(int stage);
+int place3d_stage_times(place3d_handle *h, double *ms, int64_t *launches,
+                        int64_t *evals, int reset);
+
+/* Number of kernel launches one evaluation enqueues with this handle. */
+int place3d_launches_per_eval(const place3d_handle *h);
+
+/* Last error message of the handle, or of the calling thread when h is NULL
+ * (creation errors).  Never NULL. */
+const char *place3d_last_error(const place3d_handle *h);
+
+/* Free every resource of the handle (synchronises its stream). */
+void place3d_destroy(place3d_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PLACE3D_H */

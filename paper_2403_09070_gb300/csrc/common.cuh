@@ -1,0 +1,111 @@
+// Shared device helpers of the place3d kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace p3d {
+
+template <typename T> struct V4;
+template <> struct alignas(16) V4<float> { float x, y, z, w; };
+template <> struct alignas(32) V4<double> { double x, y, z, w; };
+
+// One IEEE-rounded operation each; never contracted into an FMA.  The
+// fixed-point density contract (quantised contributions) is defined on these.
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float rn_div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double rn_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float r_floor(float a) { return floorf(a); }
+__device__ __forceinline__ double r_floor(double a) { return floor(a); }
+__device__ __forceinline__ float r_ceil(float a) { return ceilf(a); }
+__device__ __forceinline__ double r_ceil(double a) { return ceil(a); }
+__device__ __forceinline__ long long r_rint(float a) { return __float2ll_rn(a); }
+__device__ __forceinline__ long long r_rint(double a) { return __double2ll_rn(a); }
+__device__ __forceinline__ float r_exp(float a) { return expf(a); }
+__device__ __forceinline__ double r_exp(double a) { return exp(a); }
+
+template <typename T> __device__ __forceinline__ T big();
+template <> __device__ __forceinline__ float big<float>() { return 3.0e38f; }
+template <> __device__ __forceinline__ double big<double>() { return 1.0e300; }
+
+__device__ __forceinline__ float shfl_xor(float v, int m, int w) {
+  return __shfl_xor_sync(0xffffffffu, v, m, w);
+}
+__device__ __forceinline__ double shfl_xor(double v, int m, int w) {
+  return __shfl_xor_sync(0xffffffffu, v, m, w);
+}
+__device__ __forceinline__ int shfl_xor(int v, int m, int w) {
+  return __shfl_xor_sync(0xffffffffu, v, m, w);
+}
+__device__ __forceinline__ long long shfl_up_ll(long long v, int d) {
+  return __shfl_up_sync(0xffffffffu, v, d);
+}
+
+__device__ __forceinline__ void atomic_add_i64(long long *p, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
+}
+
+// Per-instance gradient accumulators (gx, gy, fd, waz).
+__device__ __forceinline__ void acc_add(V4<float> *p, float a, float b, float c, float d) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+               "f"(d)
+               : "memory");
+#else
+  atomicAdd(&p->x, a);
+  atomicAdd(&p->y, b);
+  atomicAdd(&p->z, c);
+  atomicAdd(&p->w, d);
+#endif
+}
+__device__ __forceinline__ void acc_add(V4<double> *p, double a, double b, double c, double d) {
+  atomicAdd(&p->x, a);
+  atomicAdd(&p->y, b);
+  atomicAdd(&p->z, c);
+  atomicAdd(&p->w, d);
+}
+
+// Block-wide sum of up to 4 doubles into global accumulators (one atomic per
+// block and value).  All threads of the block must call it.
+template <int NV>
+__device__ __forceinline__ void block_sum_atomic(double (&v)[NV], double *dst) {
+  __shared__ double red[32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = v[k];
+#pragma unroll
+    for (int m = 16; m; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    if (lane == 0) red[warp][k] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = lane < nw ? red[lane][k] : 0.0;
+#pragma unroll
+      for (int m = 16; m; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+      if (lane == 0 && s != 0.0) atomicAdd(dst + k, s);
+    }
+  }
+}
+
+// Indices of the device scalar accumulators.
+enum Scalar {
+  S_WL_BI = 0,
+  S_WL_Z,
+  S_HPWL,
+  S_NCROSS,
+  S_ESUM,  // sum c_j c_k c_l a^2 / w^2 (energy before the 1/2 vol(b) N factor)
+  S_SX,
+  S_SY,
+  S_SZ,
+  S_COUNT
+};
+
+}  // namespace p3d

@@ -1,0 +1,345 @@
+// Density kernels: fixed-point charge scatter (eq. density-map-accum for
+// cells, Theorem 1 corners + 3D integer prefix sum for macros), conversion to
+// the transform's input, suffix sums of the field for the macro gather, and
+// the field gather fused with the wirelength-gradient add.
+#pragma once
+#include "common.cuh"
+
+namespace p3d {
+
+// Density constants, computed in double on the host and rounded once to T.
+template <typename T> struct DensC {
+  T x0, y0;          // region origin
+  T iwb, ihb, idb;   // 1/w_b, 1/h_b, 1/d_b
+  T cw, ch;          // sqrt(2) w_b, sqrt(2) h_b: local-smoothness thresholds
+  T zmid, qz, tz;    // d_z/2, d_z/4, 2/d_z
+  T fnx, fny, fnz;   // N_x, N_y, N_z as T
+  int nx, ny, nz;
+};
+
+constexpr double kFixedScale = 68719476736.0;  // 2^36 counts per unit density
+
+template <typename T> struct Box {
+  T lo[3], hi[3];  // stretched cuboid in bin units (x, y, z), unclipped
+  T om;            // local-smoothness weight omega
+};
+
+// Instance cuboid D_i (Sec. IV-A) with the partition-dependent size (eq.
+// std-size-tech for cells, eq. macro-size-tech for macros, clamped to the
+// movable range) and local smoothness (omega, stretched footprint).  Every
+// step is one IEEE-rounded operation in the order the fixed-point contract
+// states, so that quantised contributions are reproducible bit for bit.
+template <typename T>
+__device__ __forceinline__ Box<T> inst_box(const DensC<T> &c, T X, T Y, T Z, const V4<T> &sz,
+                                           bool macro) {
+  const bool top = Z > c.zmid;
+  T w, h;
+  if (macro) {
+    T t = rn_sub(rn_mul(Z, c.tz), T(0.5));
+    if (t < T(0)) t = T(0);
+    if (t > T(1)) t = T(1);
+    const T u = rn_sub(T(1), t);
+    w = rn_add(rn_mul(t, sz.z), rn_mul(u, sz.x));
+    h = rn_add(rn_mul(t, sz.w), rn_mul(u, sz.y));
+  } else {
+    w = top ? sz.z : sz.x;
+    h = top ? sz.w : sz.y;
+  }
+  const T sw = w > c.cw ? w : c.cw;
+  const T sh = h > c.ch ? h : c.ch;
+  Box<T> b;
+  b.om = rn_div(rn_mul(w, h), rn_mul(sw, sh));
+  const T hw = rn_mul(T(0.5), sw), hh = rn_mul(T(0.5), sh);
+  const T dx = rn_sub(X, c.x0), dy = rn_sub(Y, c.y0);
+  b.lo[0] = rn_mul(rn_sub(dx, hw), c.iwb);
+  b.hi[0] = rn_mul(rn_add(dx, hw), c.iwb);
+  b.lo[1] = rn_mul(rn_sub(dy, hh), c.ihb);
+  b.hi[1] = rn_mul(rn_add(dy, hh), c.ihb);
+  b.lo[2] = rn_mul(rn_sub(Z, c.qz), c.idb);
+  b.hi[2] = rn_mul(rn_add(Z, c.qz), c.idb);
+  return b;
+}
+
+// Clip [lo, hi] to [0, N] and return the bin index range; false if empty.
+template <typename T>
+__device__ __forceinline__ bool clip_axis(T lo, T hi, T fN, int n, T &cl, T &chh, int &b0, int &b1) {
+  cl = lo > T(0) ? lo : T(0);
+  chh = hi < fN ? hi : fN;
+  if (!(cl < chh)) return false;
+  b0 = (int)r_floor(cl);
+  b1 = (int)r_ceil(chh) - 1;
+  if (b1 > n - 1) b1 = n - 1;
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T ov_axis(T cl, T chh, int b) {
+  const T lo = (T)b, hi = (T)(b + 1);
+  return rn_sub(chh < hi ? chh : hi, cl > lo ? cl : lo);
+}
+
+// ---- a2: std-cell scatter, one thread per instance (macros skipped) ----
+// Each (cell, bin) contribution c = ((omega*ovx)*ovy)*ovz is quantised to
+// rint(c * 2^36) and added with a 64-bit integer atomic: the map is exact
+// and independent of the order of the additions.
+template <typename T>
+__global__ void __launch_bounds__(256) k_scatter_cells(int n, const V4<T> *__restrict__ pos,
+                                                       const V4<T> *__restrict__ size,
+                                                       const uint8_t *__restrict__ flags,
+                                                       DensC<T> c, long long *__restrict__ q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint8_t f = flags[i];
+  if (f & 1) return;  // macro: Theorem 1 path
+  const V4<T> p = pos[i];
+  const Box<T> b = inst_box(c, p.x, p.y, p.z, size[i], false);
+  T cl[3], chh[3];
+  int b0[3], b1[3];
+  if (!clip_axis(b.lo[0], b.hi[0], c.fnx, c.nx, cl[0], chh[0], b0[0], b1[0])) return;
+  if (!clip_axis(b.lo[1], b.hi[1], c.fny, c.ny, cl[1], chh[1], b0[1], b1[1])) return;
+  if (!clip_axis(b.lo[2], b.hi[2], c.fnz, c.nz, cl[2], chh[2], b0[2], b1[2])) return;
+  const T scale = (T)kFixedScale;
+  for (int k = b0[2]; k <= b1[2]; ++k) {
+    const T oz = ov_axis(cl[2], chh[2], k);
+    for (int j = b0[1]; j <= b1[1]; ++j) {
+      const T oy = ov_axis(cl[1], chh[1], j);
+      long long *row = q + ((size_t)k * c.ny + j) * c.nx;
+      for (int ii = b0[0]; ii <= b1[0]; ++ii) {
+        const T ox = ov_axis(cl[0], chh[0], ii);
+        const T v = rn_mul(rn_mul(rn_mul(b.om, ox), oy), oz);
+        atomic_add_i64(row + ii, r_rint(rn_mul(v, scale)));
+      }
+    }
+  }
+}
+
+// Corner s (bit a set = upper face on axis a) of a macro's cuboid in bin
+// units, clamped to [0, N]: base index and the two weights g(i - c).
+template <typename T>
+__device__ __forceinline__ void corner_axis(T c, T fN, int &base, T &w0, T &w1) {
+  if (c < T(0)) c = T(0);
+  if (c > fN) c = fN;
+  base = (int)r_floor(c);
+  const T f = rn_sub(c, (T)base);
+  w0 = rn_sub(T(1), f);
+  w1 = f;
+}
+
+// ---- a3: macro corner map (Theorem 1), one thread per (macro, corner) ----
+// Entries e = ((omega*gx)*gy)*gz with sign -sx*sy*sz, quantised like cell
+// contributions, accumulated into the corner map A (int64).
+template <typename T>
+__global__ void k_macro_corners(int nm, const int *__restrict__ macro_ids,
+                                const V4<T> *__restrict__ pos, const V4<T> *__restrict__ size,
+                                DensC<T> c, long long *__restrict__ A) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nm * 8) return;
+  const int i = macro_ids[t >> 3], s = t & 7;
+  const V4<T> p = pos[i];
+  const Box<T> b = inst_box(c, p.x, p.y, p.z, size[i], true);
+  const T fN[3] = {c.fnx, c.fny, c.fnz};
+  const int nn[3] = {c.nx, c.ny, c.nz};
+  int base[3];
+  T wg[3][2];
+  int sign = -1;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const bool up = (s >> a) & 1;
+    corner_axis(up ? b.hi[a] : b.lo[a], fN[a], base[a], wg[a][0], wg[a][1]);
+    sign *= up ? 1 : -1;
+  }
+  const T scale = (T)kFixedScale;
+#pragma unroll
+  for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) {
+        const int ii = base[0] + cx, j = base[1] + cy, k = base[2] + cz;
+        if (ii >= nn[0] || j >= nn[1] || k >= nn[2]) continue;
+        const T e = rn_mul(rn_mul(rn_mul(b.om, wg[0][cx]), wg[1][cy]), wg[2][cz]);
+        const long long qe = r_rint(rn_mul(e, scale));
+        if (qe) atomic_add_i64(A + ((size_t)k * c.ny + j) * c.nx + ii, sign > 0 ? qe : -qe);
+      }
+}
+
+// ---- eq. def-prefix-sum-3d: inclusive scan along x (one warp per row) ----
+// REV = true scans from the high end (suffix sums).  In/out may alias.
+template <typename TI, typename TO, bool REV>
+__global__ void __launch_bounds__(256) k_scan_rows(int rows, int nx, const TI *in, TO *out) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= rows) return;
+  const size_t off = (size_t)row * nx;
+  TO carry = 0;
+  for (int base = 0; base < nx; base += 32) {
+    const int t = base + lane;
+    const int i = REV ? nx - 1 - t : t;
+    TO v = t < nx ? (TO)in[off + i] : (TO)0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const TO u = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d) v += u;
+    }
+    v += carry;
+    if (t < nx) out[off + i] = v;
+    carry = __shfl_sync(0xffffffffu, v, 31);
+  }
+}
+
+// ---- inclusive scan along y, in place; block = 32 columns x W warps ----
+// Each warp scans a chunk of rows per column (lane = column), chunk totals
+// are combined through shared memory.  grid = (ceil(nx/32), nz).
+template <typename TA, bool REV>
+__global__ void __launch_bounds__(1024) k_scan_cols(int nx, int ny, TA *a) {
+  __shared__ TA tot[32][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int x = blockIdx.x * 32 + lane;
+  const size_t slab = (size_t)blockIdx.y * ny * nx;
+  const int chunk = (ny + nw - 1) / nw;
+  const int r0 = warp * chunk, r1 = min(ny, r0 + chunk);
+  TA s = 0;
+  if (x < nx)
+    for (int r = r0; r < r1; ++r) s += a[slab + (size_t)(REV ? ny - 1 - r : r) * nx + x];
+  tot[warp][lane] = s;
+  __syncthreads();
+  TA run = 0;
+  for (int w = 0; w < warp; ++w) run += tot[w][lane];
+  if (x < nx)
+    for (int r = r0; r < r1; ++r) {
+      const size_t id = slab + (size_t)(REV ? ny - 1 - r : r) * nx + x;
+      run += a[id];
+      a[id] = run;
+    }
+}
+
+// ---- density -> transform input: z prefix of the macro map + cell map ----
+// rho[z][y][x] = (q[z][y][x] + sum_{z' <= z} A[z'][y][x]) * 2^-36.
+// A may be NULL (no macros).  One thread per (y, x) column.
+template <typename T>
+__global__ void __launch_bounds__(256) k_densify(int nxy, int nz, const long long *__restrict__ q,
+                                                 const long long *__restrict__ A, T *__restrict__ rho) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nxy) return;
+  long long acc = 0;
+  for (int z = 0; z < nz; ++z) {
+    const size_t id = (size_t)z * nxy + t;
+    if (A) acc += A[id];
+    rho[id] = (T)(q[id] + acc) * (T)(1.0 / kFixedScale);
+  }
+}
+
+// ---- a10 (macros): Theorem 1's adjoint, one thread per (macro, corner) ----
+// S holds the x- and y-suffix sums of E_x, E_y, E_z (double, 3 maps); the
+// z-suffix is summed here.  out[m][3] accumulates sum_entries sign*e*S.
+template <typename T>
+__global__ void k_macro_gather(int nm, const int *__restrict__ macro_ids,
+                               const V4<T> *__restrict__ pos, const V4<T> *__restrict__ size,
+                               DensC<T> c, const double *__restrict__ S, size_t nb,
+                               double *__restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nm * 8) return;
+  const int m = t >> 3, s = t & 7, i = macro_ids[m];
+  const V4<T> p = pos[i];
+  const Box<T> b = inst_box(c, p.x, p.y, p.z, size[i], true);
+  const T fN[3] = {c.fnx, c.fny, c.fnz};
+  int base[3];
+  T wg[3][2];
+  int sign = -1;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const bool up = (s >> a) & 1;
+    corner_axis(up ? b.hi[a] : b.lo[a], fN[a], base[a], wg[a][0], wg[a][1]);
+    sign *= up ? 1 : -1;
+  }
+  double acc[3] = {0, 0, 0};
+  for (int cz = 0; cz < 2; ++cz)
+    for (int cy = 0; cy < 2; ++cy)
+      for (int cx = 0; cx < 2; ++cx) {
+        const int ii = base[0] + cx, j = base[1] + cy, k = base[2] + cz;
+        if (ii >= c.nx || j >= c.ny || k >= c.nz) continue;
+        const double e = (double)(b.om * wg[0][cx] * wg[1][cy] * wg[2][cz]);
+        if (e == 0.0) continue;
+        for (int kk = k; kk < c.nz; ++kk) {
+          const size_t id = ((size_t)kk * c.ny + j) * c.nx + ii;
+#pragma unroll
+          for (int comp = 0; comp < 3; ++comp) acc[comp] += e * S[comp * nb + id];
+        }
+      }
+#pragma unroll
+  for (int comp = 0; comp < 3; ++comp)
+    if (acc[comp] != 0.0) atomicAdd(out + m * 3 + comp, sign > 0 ? acc[comp] : -acc[comp]);
+}
+
+// Final assembly constants.
+template <typename T> struct FinalC {
+  T lam, alpha, volb;
+  const double *scal;  // device scalars (S_x, S_y, S_z for g)
+};
+
+__device__ __forceinline__ double g_scale_of(const double *scal) {
+  const double sz = scal[S_SZ];
+  return sz > 0.0 ? (scal[S_SX] + scal[S_SY]) / (2.0 * sz) : 0.0;
+}
+
+// ---- a10 + a9 + a11 per instance: cell field gather fused with the WL add ----
+// g = acc_wl + lambda * (-omega sum_b vol(D cap b) E_b); gz uses the
+// normalised FD gradient.  Macros take their density part from mgrad.
+template <typename T, typename TO>
+__global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ pos,
+                                               const V4<T> *__restrict__ size,
+                                               const uint8_t *__restrict__ flags,
+                                               const int *__restrict__ macro_slot, DensC<T> c,
+                                               const T *__restrict__ ex, const T *__restrict__ ey,
+                                               const T *__restrict__ ez,
+                                               const double *__restrict__ mgrad,
+                                               const V4<T> *__restrict__ acc, FinalC<T> fc,
+                                               TO *__restrict__ gx, TO *__restrict__ gy,
+                                               TO *__restrict__ gz) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint8_t f = flags[i];
+  T dgx = 0, dgy = 0, dgz = 0;
+  if (f & 1) {
+    const int m = macro_slot[i];
+    dgx = (T)(-(double)fc.volb * mgrad[m * 3 + 0]);
+    dgy = (T)(-(double)fc.volb * mgrad[m * 3 + 1]);
+    dgz = (T)(-(double)fc.volb * mgrad[m * 3 + 2]);
+  } else {
+    const V4<T> p = pos[i];
+    const Box<T> b = inst_box(c, p.x, p.y, p.z, size[i], false);
+    T cl[3], chh[3];
+    int b0[3], b1[3];
+    if (clip_axis(b.lo[0], b.hi[0], c.fnx, c.nx, cl[0], chh[0], b0[0], b1[0]) &&
+        clip_axis(b.lo[1], b.hi[1], c.fny, c.ny, cl[1], chh[1], b0[1], b1[1]) &&
+        clip_axis(b.lo[2], b.hi[2], c.fnz, c.nz, cl[2], chh[2], b0[2], b1[2])) {
+      T sx = 0, sy = 0, sz = 0;
+      for (int k = b0[2]; k <= b1[2]; ++k) {
+        const T oz = ov_axis(cl[2], chh[2], k);
+        for (int j = b0[1]; j <= b1[1]; ++j) {
+          const T oyz = ov_axis(cl[1], chh[1], j) * oz;
+          const size_t row = ((size_t)k * c.ny + j) * c.nx;
+          for (int ii = b0[0]; ii <= b1[0]; ++ii) {
+            const T v = ov_axis(cl[0], chh[0], ii) * oyz;
+            sx += v * ex[row + ii];
+            sy += v * ey[row + ii];
+            sz += v * ez[row + ii];
+          }
+        }
+      }
+      const T k = -b.om * fc.volb;
+      dgx = k * sx;
+      dgy = k * sy;
+      dgz = k * sz;
+    }
+  }
+  const V4<T> a = acc[i];
+  const T g = (T)g_scale_of(fc.scal);
+  T ozg = g * a.z + fc.alpha * a.w + fc.lam * dgz;
+  if (f & 2) ozg = T(0);
+  gx[i] = (TO)(a.x + fc.lam * dgx);
+  gy[i] = (TO)(a.y + fc.lam * dgy);
+  gz[i] = (TO)ozg;
+}
+
+}  // namespace p3d

@@ -1,0 +1,911 @@
+// place3d C ABI: problem validation and upload, net-degree buckets, transform
+// matrices, and the evaluation schedule (density path on the caller's stream,
+// wirelength path on a second stream, joined before the final assembly).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/place3d.h"
+#include "common.cuh"
+#include "density.cuh"
+#include "tc_gemm.h"
+#include "transform.cuh"
+#include "wirelength.cuh"
+
+using namespace p3d;
+
+namespace {
+
+thread_local std::string g_thread_err = "";
+
+// Profiling stages.
+enum Stage {
+  ST_PREP = 0,
+  ST_SCATTER,
+  ST_PREFIX,
+  ST_FWD,
+  ST_ZSTAGE,
+  ST_INV,
+  ST_MACRO_GATHER,
+  ST_WIRELENGTH,
+  ST_NORMS,
+  ST_FINAL,
+  ST_COUNT
+};
+const char *kStageNames[ST_COUNT] = {"prep",         "scatter",    "prefix_densify", "transform_fwd",
+                                     "zstage",       "transform_inv", "macro_gather", "wirelength",
+                                     "norms",        "final"};
+
+struct Bucket {
+  int first, count;  // net range in the reordered CSR
+  int kind;          // 0..5 group kernels, 6 block kernel
+};
+
+struct StageEv {
+  cudaEvent_t a, b;
+  int stage;
+  cudaStream_t s;
+};
+
+}  // namespace
+
+struct place3d_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr, side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int precision = 0, flags = 0;
+  int n = 0, nm = 0, nnet = 0, npin = 0;
+  int nx = 0, ny = 0, nz = 0;
+  size_t nb = 0;
+  double wb = 0, hb = 0, db = 0, dx = 0, dy = 0, dz = 0;
+  double xl = 0, yl = 0;  // region origin
+  double gamma = 0, gamma_z = 0, alpha = 0, lambda = 0;
+  size_t esz = 8;  // bytes per real
+  // device buffers
+  void *pos = nullptr, *size = nullptr, *off = nullptr, *acc = nullptr;
+  uint8_t *flags_d = nullptr;
+  int *macro_ids = nullptr, *macro_slot = nullptr, *net_start = nullptr, *pin_inst = nullptr;
+  long long *q = nullptr, *corner = nullptr;
+  void *rho = nullptr, *t1 = nullptr, *t2 = nullptr, *czpsi = nullptr, *szpsi = nullptr;
+  void *xinv = nullptr, *x2 = nullptr, *ex = nullptr, *ey = nullptr, *ez = nullptr;
+  void *mats = nullptr;
+  size_t mat_off[5] = {0, 0, 0, 0, 0};  // Fx, Fy, Bx(=[Sx;Cx]), Cy, Sy (elements)
+  double *suffix = nullptr, *mgrad = nullptr, *scal = nullptr;
+  ZStageC *zc = nullptr;
+  void *gout = nullptr;  // internal gradient output [3][n] (handle precision)
+  void *stage_in = nullptr;  // staging for host positions [3][n] doubles
+  int *check_flag = nullptr;
+  std::vector<Bucket> buckets;
+  // tensor-core transform state (FP32_TC)
+  p3d_tc::TcPlan *tc = nullptr;
+  // results
+  double host_scal[S_COUNT];
+  bool have_result = false;
+  std::string err;
+  int launches = 0;
+  // profiling
+  bool profiling = false;
+  std::vector<StageEv> ev_pool, ev_live;
+  double stage_ms[ST_COUNT];
+  long long stage_launch[ST_COUNT];
+  long long prof_evals = 0;
+};
+
+namespace {
+
+int fail(place3d_handle *h, int code, const std::string &msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_thread_err = msg;
+  return code;
+}
+
+int cuda_fail(place3d_handle *h, cudaError_t e, const char *what) {
+  return fail(h, e == cudaErrorMemoryAllocation ? PLACE3D_ERR_OOM : PLACE3D_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define P3D_CUDA(h, call)                                 \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+template <typename T> T *as(void *p) { return static_cast<T *>(p); }
+
+// Stage timing helpers (events drawn from a pool, resolved on query).
+struct StageScope {
+  place3d_handle *h;
+  int stage;
+  cudaStream_t s;
+  StageEv ev{};
+  StageScope(place3d_handle *h_, int st, cudaStream_t s_) : h(h_), stage(st), s(s_) {
+    if (!h->profiling) return;
+    if (h->ev_pool.empty()) {
+      cudaEventCreate(&ev.a);
+      cudaEventCreate(&ev.b);
+    } else {
+      ev = h->ev_pool.back();
+      h->ev_pool.pop_back();
+    }
+    ev.stage = st;
+    ev.s = s;
+    cudaEventRecord(ev.a, s);
+  }
+  ~StageScope() {
+    if (!h->profiling) return;
+    cudaEventRecord(ev.b, s);
+    h->ev_live.push_back(ev);
+  }
+};
+
+void count_launch(place3d_handle *h, int stage) {
+  h->launches++;
+  if (h->profiling) h->stage_launch[stage]++;
+}
+
+int grid_for(long long n, int block) { return (int)((n + block - 1) / block); }
+
+// ---- position packing (and optional range checks) ----
+template <typename TI, typename T>
+__global__ void k_pack(int n, const TI *__restrict__ x, const TI *__restrict__ y, const TI *__restrict__ z,
+                       V4<T> *__restrict__ pos, double zlo, double zhi, int *__restrict__ bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  V4<T> p;
+  p.x = (T)x[i];
+  p.y = (T)y[i];
+  p.z = (T)z[i];
+  p.w = T(0);
+  pos[i] = p;
+  if (bad) {
+    const double zz = (double)z[i];
+    if (!isfinite((double)x[i]) || !isfinite((double)y[i]) || !(zz >= zlo && zz <= zhi)) atomicOr(bad, 1);
+  }
+}
+
+template <typename T>
+void host_mats(int n, double d, std::vector<T> &F, std::vector<T> &C, std::vector<T> &S) {
+  // F[j][i] = cos(pi j (i+1/2)/n); C[i][j] = cos(...); S[i][j] = (j pi/d) sin(...)
+  F.resize((size_t)n * n);
+  C.resize((size_t)n * n);
+  S.resize((size_t)n * n);
+  const double pi = 3.14159265358979323846;
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) {
+      const double arg = pi * j * (i + 0.5) / n;
+      F[(size_t)j * n + i] = (T)std::cos(arg);
+      C[(size_t)i * n + j] = (T)std::cos(arg);
+      S[(size_t)i * n + j] = (T)((j * pi / d) * std::sin(arg));
+    }
+}
+
+template <typename T> DensC<T> dens_consts(const place3d_handle *h, double xl, double yl) {
+  DensC<T> c;
+  c.x0 = (T)xl;
+  c.y0 = (T)yl;
+  c.iwb = (T)(1.0 / h->wb);
+  c.ihb = (T)(1.0 / h->hb);
+  c.idb = (T)(1.0 / h->db);
+  c.cw = (T)(std::sqrt(2.0) * h->wb);
+  c.ch = (T)(std::sqrt(2.0) * h->hb);
+  c.zmid = (T)(0.5 * h->dz);
+  c.qz = (T)(0.25 * h->dz);
+  c.tz = (T)(2.0 / h->dz);
+  c.fnx = (T)h->nx;
+  c.fny = (T)h->ny;
+  c.fnz = (T)h->nz;
+  c.nx = h->nx;
+  c.ny = h->ny;
+  c.nz = h->nz;
+  return c;
+}
+
+}  // namespace
+
+namespace {
+
+template <typename T>
+GemmProb<T> gp(const void *A, const void *W, void *out, long long abs, long long obs, int batches, int M,
+               int N, int K) {
+  GemmProb<T> p;
+  p.A = static_cast<const T *>(A);
+  p.W = static_cast<const T *>(W);
+  p.out = static_cast<T *>(out);
+  p.a_bstride = abs;
+  p.o_bstride = obs;
+  p.batches = batches;
+  p.M = M;
+  p.N = N;
+  p.K = K;
+  p.tiles_m = (M + kBM - 1) / kBM;
+  p.tiles_n = (N + kBN - 1) / kBN;
+  return p;
+}
+
+template <typename T>
+void launch_gemm(place3d_handle *h, cudaStream_t s, std::initializer_list<GemmProb<T>> probs, int stage) {
+  GemmGroup<T> g;
+  g.count = 0;
+  int tiles = 0;
+  for (const auto &p : probs) {
+    g.p[g.count] = p;
+    g.tile_start[g.count] = tiles;
+    tiles += p.batches * p.tiles_m * p.tiles_n;
+    g.count++;
+  }
+  g.tile_start[g.count] = tiles;
+  k_gemm_simt<T><<<tiles, 256, 0, s>>>(g);
+  count_launch(h, stage);
+}
+
+// The spectral solve: rho -> E_x, E_y, E_z (and the energy sum).
+template <typename T> void run_transforms(place3d_handle *h, cudaStream_t s) {
+  const int nx = h->nx, ny = h->ny, nz = h->nz;
+  const long long pl = (long long)nx * ny;
+  const T *M = as<T>(h->mats);
+  const T *Fx = M + h->mat_off[0], *Fy = M + h->mat_off[1], *Bx = M + h->mat_off[2];
+  const T *Cy = M + h->mat_off[3], *Sy = M + h->mat_off[4];
+  {
+    StageScope sc(h, ST_FWD, s);
+    launch_gemm<T>(h, s, {gp<T>(h->rho, Fx, h->t1, pl, pl, nz, ny, nx, nx)}, ST_FWD);
+    launch_gemm<T>(h, s, {gp<T>(h->t1, Fy, h->t2, pl, pl, nz, nx, ny, ny)}, ST_FWD);
+  }
+  {
+    StageScope sc(h, ST_ZSTAGE, s);
+    k_zstage<T><<<grid_for(pl, 256), 256, 0, s>>>(h->zc, as<T>(h->t2), as<T>(h->czpsi), as<T>(h->szpsi),
+                                                   h->scal + S_ESUM);
+    count_launch(h, ST_ZSTAGE);
+  }
+  {
+    StageScope sc(h, ST_INV, s);
+    launch_gemm<T>(h, s,
+                   {gp<T>(h->czpsi, Bx, h->xinv, pl, 2 * pl, nz, ny, 2 * nx, nx),
+                    gp<T>(h->szpsi, Bx + (size_t)nx * nx, h->x2, pl, pl, nz, ny, nx, nx)},
+                   ST_INV);
+    launch_gemm<T>(h, s,
+                   {gp<T>(h->xinv, Cy, h->ex, 2 * pl, pl, nz, nx, ny, ny),
+                    gp<T>(as<T>(h->xinv) + pl, Sy, h->ey, 2 * pl, pl, nz, nx, ny, ny),
+                    gp<T>(h->x2, Cy, h->ez, pl, pl, nz, nx, ny, ny)},
+                   ST_INV);
+  }
+}
+
+// The same solve on the tensor cores (split-BF16 tcgen05 products).
+void run_transforms_tc(place3d_handle *h, cudaStream_t s) {
+  {
+    StageScope sc(h, ST_FWD, s);
+    const int k = p3d_tc::forward(h->tc, s);
+    for (int i = 0; i < k; ++i) count_launch(h, ST_FWD);
+  }
+  {
+    StageScope sc(h, ST_ZSTAGE, s);
+    const int k = p3d_tc::zstage(h->tc, s, h->scal + S_ESUM);
+    for (int i = 0; i < k; ++i) count_launch(h, ST_ZSTAGE);
+  }
+  {
+    StageScope sc(h, ST_INV, s);
+    const int k = p3d_tc::inverse(h->tc, s);
+    for (int i = 0; i < k; ++i) count_launch(h, ST_INV);
+  }
+}
+
+template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void *gz, int dtype, int mem) {
+  cudaStream_t s = h->stream, w = h->side;
+  const int n = h->n;
+  const DensC<T> dc = dens_consts<T>(h, h->xl, h->yl);
+  h->launches = 0;
+  P3D_CUDA(h, cudaMemsetAsync(h->scal, 0, sizeof(double) * S_COUNT, s));
+  P3D_CUDA(h, cudaEventRecord(h->ev_fork, s));
+  // ---------------- wirelength path (side stream) ----------------
+  P3D_CUDA(h, cudaStreamWaitEvent(w, h->ev_fork, 0));
+  {
+    StageScope sc(h, ST_WIRELENGTH, w);
+    P3D_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(V4<T>) * (size_t)std::max(n, 1), w));
+    WlC<T> c;
+    c.zmid = (T)(0.5 * h->dz);
+    c.inv_g = (T)(1.0 / h->gamma);
+    c.inv_gz = (T)(1.0 / (h->gamma_z > 0 ? h->gamma_z : h->gamma));
+    c.fd_scale = (T)(4.0 / h->dz);
+    V4<T> *acc = as<V4<T>>(h->acc);
+    const V4<T> *pos = as<V4<T>>(h->pos), *off = as<V4<T>>(h->off);
+    for (const Bucket &b : h->buckets) {
+      const int G = b.kind == 0 ? 4 : b.kind == 1 ? 8 : b.kind == 2 ? 16 : 32;
+      const int blocks = grid_for((long long)b.count * G, 256);
+      switch (b.kind) {
+        case 0: k_wl_group<T, 4, 1><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
+        case 1: k_wl_group<T, 8, 1><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
+        case 2: k_wl_group<T, 16, 1><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
+        case 3: k_wl_group<T, 32, 1><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
+        case 4: k_wl_group<T, 32, 2><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
+        case 5: k_wl_group<T, 32, 4><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
+        default: k_wl_block<T><<<b.count, 256, 0, w>>>(b.first, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
+      }
+      count_launch(h, ST_WIRELENGTH);
+    }
+  }
+  {
+    StageScope sc(h, ST_NORMS, w);
+    k_norms<T><<<std::min(grid_for(std::max(n, 1), 256), 1216), 256, 0, w>>>(n, as<V4<T>>(h->acc), h->scal);
+    count_launch(h, ST_NORMS);
+  }
+  P3D_CUDA(h, cudaEventRecord(h->ev_join, w));
+  // ---------------- density path (caller's stream) ----------------
+  {
+    StageScope sc(h, ST_SCATTER, s);
+    P3D_CUDA(h, cudaMemsetAsync(h->q, 0, sizeof(long long) * h->nb, s));
+    if (n > 0) {
+      k_scatter_cells<T><<<grid_for(n, 256), 256, 0, s>>>(n, as<V4<T>>(h->pos), as<V4<T>>(h->size), h->flags_d,
+                                                          dc, h->q);
+      count_launch(h, ST_SCATTER);
+    }
+    if (h->nm > 0) {
+      P3D_CUDA(h, cudaMemsetAsync(h->corner, 0, sizeof(long long) * h->nb, s));
+      k_macro_corners<T><<<grid_for(h->nm * 8, 128), 128, 0, s>>>(h->nm, h->macro_ids, as<V4<T>>(h->pos),
+                                                                  as<V4<T>>(h->size), dc, h->corner);
+      count_launch(h, ST_SCATTER);
+    }
+  }
+  {
+    StageScope sc(h, ST_PREFIX, s);
+    const int rows = h->ny * h->nz;
+    if (h->nm > 0) {
+      k_scan_rows<long long, long long, false><<<grid_for(rows, 8), 256, 0, s>>>(rows, h->nx, h->corner, h->corner);
+      count_launch(h, ST_PREFIX);
+      k_scan_cols<long long, false><<<dim3(grid_for(h->nx, 32), h->nz), 1024, 0, s>>>(h->nx, h->ny, h->corner);
+      count_launch(h, ST_PREFIX);
+    }
+    if (h->tc) {
+      p3d_tc::densify(h->tc, s, h->nx * h->ny, h->nz, h->q, h->nm > 0 ? h->corner : nullptr);
+    } else {
+      k_densify<T><<<grid_for((long long)h->nx * h->ny, 256), 256, 0, s>>>(h->nx * h->ny, h->nz, h->q,
+                                                                           h->nm > 0 ? h->corner : nullptr, as<T>(h->rho));
+    }
+    count_launch(h, ST_PREFIX);
+  }
+  if (h->tc)
+    run_transforms_tc(h, s);
+  else
+    run_transforms<T>(h, s);
+  if (h->nm > 0) {
+    StageScope sc(h, ST_MACRO_GATHER, s);
+    const int rows = h->ny * h->nz;
+    for (int comp = 0; comp < 3; ++comp) {
+      const T *E = as<T>(comp == 0 ? h->ex : comp == 1 ? h->ey : h->ez);
+      k_scan_rows<T, double, true><<<grid_for(rows, 8), 256, 0, s>>>(rows, h->nx, E, h->suffix + comp * h->nb);
+      count_launch(h, ST_MACRO_GATHER);
+    }
+    k_scan_cols<double, true><<<dim3(grid_for(h->nx, 32), h->nz * 3), 1024, 0, s>>>(h->nx, h->ny, h->suffix);
+    count_launch(h, ST_MACRO_GATHER);
+    P3D_CUDA(h, cudaMemsetAsync(h->mgrad, 0, sizeof(double) * 3 * h->nm, s));
+    k_macro_gather<T><<<grid_for(h->nm * 8, 128), 128, 0, s>>>(h->nm, h->macro_ids, as<V4<T>>(h->pos),
+                                                               as<V4<T>>(h->size), dc, h->suffix, h->nb, h->mgrad);
+    count_launch(h, ST_MACRO_GATHER);
+  }
+  // ---------------- join + final assembly ----------------
+  P3D_CUDA(h, cudaStreamWaitEvent(s, h->ev_join, 0));
+  {
+    StageScope sc(h, ST_FINAL, s);
+    FinalC<T> fc;
+    fc.lam = (T)h->lambda;
+    fc.alpha = (T)h->alpha;
+    fc.volb = (T)(h->wb * h->hb * h->db);
+    fc.scal = h->scal;
+    const bool direct = mem == PLACE3D_MEM_DEVICE && gx && gy && gz;
+    const int odt = direct ? dtype : (sizeof(T) == 8 ? PLACE3D_F64 : PLACE3D_F32);
+    void *ox = direct ? gx : h->gout;
+    void *oy = direct ? gy : (char *)h->gout + (size_t)n * sizeof(T);
+    void *oz = direct ? gz : (char *)h->gout + (size_t)2 * n * sizeof(T);
+    if (n > 0) {
+      if (odt == PLACE3D_F64)
+        k_final<T, double><<<grid_for(n, 256), 256, 0, s>>>(n, as<V4<T>>(h->pos), as<V4<T>>(h->size), h->flags_d,
+                                                            h->macro_slot, dc, as<T>(h->ex), as<T>(h->ey), as<T>(h->ez),
+                                                            h->mgrad, as<V4<T>>(h->acc), fc, (double *)ox, (double *)oy,
+                                                            (double *)oz);
+      else
+        k_final<T, float><<<grid_for(n, 256), 256, 0, s>>>(n, as<V4<T>>(h->pos), as<V4<T>>(h->size), h->flags_d,
+                                                           h->macro_slot, dc, as<T>(h->ex), as<T>(h->ey), as<T>(h->ez),
+                                                           h->mgrad, as<V4<T>>(h->acc), fc, (float *)ox, (float *)oy,
+                                                           (float *)oz);
+      count_launch(h, ST_FINAL);
+    }
+    if (!direct && gx && gy && gz && n > 0) {
+      // host outputs (or device outputs of another dtype): copy / convert
+      const size_t tb = sizeof(T);
+      const size_t ob = dtype == PLACE3D_F64 ? 8 : 4;
+      if (ob != tb) return fail(h, PLACE3D_ERR_INVALID_ARG, "host gradient dtype must match the handle precision");
+      cudaMemcpyKind k = mem == PLACE3D_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+      P3D_CUDA(h, cudaMemcpyAsync(gx, ox, (size_t)n * tb, k, s));
+      P3D_CUDA(h, cudaMemcpyAsync(gy, oy, (size_t)n * tb, k, s));
+      P3D_CUDA(h, cudaMemcpyAsync(gz, oz, (size_t)n * tb, k, s));
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+  if (h->profiling) h->prof_evals++;
+  return PLACE3D_OK;
+}
+
+void fill_result(const place3d_handle *h, place3d_result *r) {
+  const double *s = h->host_scal;
+  const double volb = h->wb * h->hb * h->db;
+  r->wl_bi = s[S_WL_BI];
+  r->wl_z = s[S_WL_Z];
+  r->hpwl_d2d = s[S_HPWL];
+  r->n_cross = s[S_NCROSS];
+  r->energy = 0.5 * volb * (double)h->nb * s[S_ESUM];
+  r->s_x = s[S_SX];
+  r->s_y = s[S_SY];
+  r->s_z = s[S_SZ];
+  r->g_scale = s[S_SZ] > 0 ? (s[S_SX] + s[S_SY]) / (2.0 * s[S_SZ]) : 0.0;
+  r->obj = r->wl_bi + h->alpha * r->wl_z + h->lambda * r->energy;
+}
+
+void free_all(place3d_handle *h) {
+  void *bufs[] = {h->pos,   h->size,  h->off,   h->acc,   h->flags_d, h->macro_ids, h->macro_slot,
+                  h->net_start, h->pin_inst, h->q, h->corner, h->rho, h->t1, h->t2, h->czpsi,
+                  h->szpsi, h->xinv, h->x2, h->ex, h->ey, h->ez, h->mats, h->suffix, h->mgrad,
+                  h->scal, h->zc, h->gout, h->stage_in, h->check_flag};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  if (h->tc) p3d_tc::destroy(h->tc);
+  for (auto &e : h->ev_pool) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  for (auto &e : h->ev_live) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
+}
+
+template <typename T>
+int upload_typed(place3d_handle *h, const place3d_problem *p, const std::vector<int> &order,
+                 const std::vector<int> &new_start) {
+  const int n = h->n;
+  // instance sizes (w_bot, h_bot, w_top, h_top)
+  std::vector<V4<T>> sz(std::max(n, 1));
+  for (int i = 0; i < n; ++i) {
+    sz[i].x = (T)p->w_bot[i];
+    sz[i].y = (T)p->h_bot[i];
+    sz[i].z = (T)p->w_top[i];
+    sz[i].w = (T)p->h_top[i];
+  }
+  P3D_CUDA(h, cudaMemcpy(h->size, sz.data(), sizeof(V4<T>) * n, cudaMemcpyHostToDevice));
+  // pins in bucket order
+  std::vector<V4<T>> off(std::max(h->npin, 1));
+  std::vector<int> pin(std::max(h->npin, 1));
+  size_t k = 0;
+  for (int e : order) {
+    for (int q = p->net_start[e]; q < p->net_start[e + 1]; ++q, ++k) {
+      pin[k] = p->pin_inst[q];
+      off[k].x = (T)p->pin_off_bot_x[q];
+      off[k].y = (T)p->pin_off_bot_y[q];
+      off[k].z = (T)p->pin_off_top_x[q];
+      off[k].w = (T)p->pin_off_top_y[q];
+    }
+  }
+  P3D_CUDA(h, cudaMemcpy(h->off, off.data(), sizeof(V4<T>) * k, cudaMemcpyHostToDevice));
+  P3D_CUDA(h, cudaMemcpy(h->pin_inst, pin.data(), sizeof(int) * k, cudaMemcpyHostToDevice));
+  P3D_CUDA(h, cudaMemcpy(h->net_start, new_start.data(), sizeof(int) * new_start.size(), cudaMemcpyHostToDevice));
+  // transform matrices
+  std::vector<T> Fx, Cx, Sx, Fy, Cy, Sy;
+  host_mats<T>(h->nx, h->dx, Fx, Cx, Sx);
+  host_mats<T>(h->ny, h->dy, Fy, Cy, Sy);
+  const size_t nx2 = (size_t)h->nx * h->nx, ny2 = (size_t)h->ny * h->ny;
+  h->mat_off[0] = 0;
+  h->mat_off[1] = nx2;
+  h->mat_off[2] = nx2 + ny2;
+  h->mat_off[3] = 3 * nx2 + ny2;
+  h->mat_off[4] = 3 * nx2 + 2 * ny2;
+  std::vector<T> all(3 * nx2 + 3 * ny2);
+  std::copy(Fx.begin(), Fx.end(), all.begin());
+  std::copy(Fy.begin(), Fy.end(), all.begin() + h->mat_off[1]);
+  std::copy(Sx.begin(), Sx.end(), all.begin() + h->mat_off[2]);
+  std::copy(Cx.begin(), Cx.end(), all.begin() + h->mat_off[2] + nx2);
+  std::copy(Cy.begin(), Cy.end(), all.begin() + h->mat_off[3]);
+  std::copy(Sy.begin(), Sy.end(), all.begin() + h->mat_off[4]);
+  P3D_CUDA(h, cudaMalloc(&h->mats, sizeof(T) * all.size()));
+  P3D_CUDA(h, cudaMemcpy(h->mats, all.data(), sizeof(T) * all.size(), cudaMemcpyHostToDevice));
+  return PLACE3D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+double place3d_alpha(double dx, double dz, double beta, double w_hbt, double rh_top, double rh_bot) {
+  const double eta = 2.0 * w_hbt / (rh_top + rh_bot);
+  return 3.5e-3 * (dx * eta * eta / dz) * std::log(90.0 * beta * eta - 1.0);
+}
+
+int place3d_create(const place3d_problem *p, int device, void *cuda_stream, place3d_handle **out) {
+  if (!p || !out) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL problem or output handle pointer");
+  *out = nullptr;
+  if (p->n_inst < 0 || p->n_net < 0 || p->n_pin < 0)
+    return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "negative instance, net or pin count");
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->nz > kMaxNz)
+    return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "bin grid must have nx, ny >= 1 and 1 <= nz <= 16");
+  if (!(p->xh > p->xl) || !(p->yh > p->yl) || !std::isfinite(p->xl) || !std::isfinite(p->yl) ||
+      !std::isfinite(p->xh) || !std::isfinite(p->yh))
+    return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "region must satisfy xh > xl and yh > yl (finite)");
+  if (!(p->gamma > 0) || !std::isfinite(p->gamma) || !std::isfinite(p->alpha) || !std::isfinite(p->lambda))
+    return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "gamma must be > 0; alpha, lambda finite");
+  if (p->precision != PLACE3D_FP64 && p->precision != PLACE3D_FP32 && p->precision != PLACE3D_FP32_TC)
+    return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "unknown precision mode");
+  const int n = p->n_inst;
+  if (n > 0 && (!p->is_macro || !p->w_bot || !p->h_bot || !p->w_top || !p->h_top))
+    return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL instance array");
+  for (int i = 0; i < n; ++i)
+    if (!(p->w_bot[i] >= 0) || !(p->h_bot[i] >= 0) || !(p->w_top[i] >= 0) || !(p->h_top[i] >= 0) ||
+        !std::isfinite(p->w_bot[i] + p->h_bot[i] + p->w_top[i] + p->h_top[i]))
+      return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "instance sizes must be finite and >= 0");
+  if (!p->net_start) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL net_start");
+  if (p->net_start[0] != 0 || p->net_start[p->n_net] != p->n_pin)
+    return fail(nullptr, PLACE3D_ERR_BAD_CSR, "net_start[0] must be 0 and net_start[n_net] == n_pin");
+  if (p->n_pin > 0 && (!p->pin_inst || !p->pin_off_bot_x || !p->pin_off_bot_y || !p->pin_off_top_x ||
+                       !p->pin_off_top_y))
+    return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL pin array");
+  std::vector<int> stamp(std::max(n, 1), -1);
+  for (int e = 0; e < p->n_net; ++e) {
+    if (p->net_start[e + 1] < p->net_start[e]) return fail(nullptr, PLACE3D_ERR_BAD_CSR, "net_start decreases");
+    for (int q = p->net_start[e]; q < p->net_start[e + 1]; ++q) {
+      const int i = p->pin_inst[q];
+      if (i < 0 || i >= n) return fail(nullptr, PLACE3D_ERR_BAD_CSR, "pin_inst out of range");
+      if (stamp[i] == e)
+        return fail(nullptr, PLACE3D_ERR_BAD_CSR, "an instance holds two pins of one net (net " + std::to_string(e) + ")");
+      stamp[i] = e;
+      if (!std::isfinite(p->pin_off_bot_x[q] + p->pin_off_bot_y[q] + p->pin_off_top_x[q] + p->pin_off_top_y[q]))
+        return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "pin offsets must be finite");
+    }
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return fail(nullptr, PLACE3D_ERR_CUDA, "no such CUDA device");
+  if (cudaSetDevice(device) != cudaSuccess) return fail(nullptr, PLACE3D_ERR_CUDA, "cudaSetDevice failed");
+
+  place3d_handle *h = new place3d_handle();
+  h->device = device;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->precision = p->precision;
+  h->flags = p->flags;
+  h->n = n;
+  h->nx = p->nx;
+  h->ny = p->ny;
+  h->nz = p->nz;
+  h->nb = (size_t)p->nx * p->ny * p->nz;
+  h->dx = p->xh - p->xl;
+  h->dy = p->yh - p->yl;
+  h->wb = h->dx / p->nx;
+  h->hb = h->dy / p->ny;
+  h->db = 0.5 * (h->wb + h->hb);
+  h->dz = p->nz * h->db;
+  h->gamma = p->gamma;
+  h->gamma_z = p->gamma_z;
+  h->alpha = p->alpha;
+  h->lambda = p->lambda;
+  h->esz = p->precision == PLACE3D_FP64 ? 8 : 4;
+  std::memset(h->stage_ms, 0, sizeof(h->stage_ms));
+  std::memset(h->stage_launch, 0, sizeof(h->stage_launch));
+  h->xl = p->xl;
+  h->yl = p->yl;
+  auto bail = [&](int code) {
+    free_all(h);
+    g_thread_err = h->err;
+    delete h;
+    return code;
+  };
+
+  // net-degree buckets: nets of degree < 2 are dropped (they contribute 0)
+  std::vector<std::vector<int>> cls(7);
+  for (int e = 0; e < p->n_net; ++e) {
+    const int d = p->net_start[e + 1] - p->net_start[e];
+    if (d < 2) continue;
+    const int k = d <= 4 ? 0 : d <= 8 ? 1 : d <= 16 ? 2 : d <= 32 ? 3 : d <= 64 ? 4 : d <= 128 ? 5 : 6;
+    cls[k].push_back(e);
+  }
+  std::vector<int> order, new_start(1, 0);
+  for (int k = 0; k < 7; ++k) {
+    if (cls[k].empty()) continue;
+    h->buckets.push_back({(int)order.size(), (int)cls[k].size(), k});
+    for (int e : cls[k]) {
+      order.push_back(e);
+      new_start.push_back(new_start.back() + (p->net_start[e + 1] - p->net_start[e]));
+    }
+  }
+  h->nnet = (int)order.size();
+  h->npin = new_start.back();
+  // macros
+  std::vector<int> mids, mslot(std::max(n, 1), -1);
+  std::vector<uint8_t> fl(std::max(n, 1), 0);
+  for (int i = 0; i < n; ++i) {
+    if (p->is_macro[i]) {
+      mslot[i] = (int)mids.size();
+      mids.push_back(i);
+      fl[i] |= 1;
+    }
+    if (p->z_fixed && p->z_fixed[i]) fl[i] |= 2;
+  }
+  h->nm = (int)mids.size();
+
+  // device allocation
+  const size_t es = h->esz, nb = h->nb, nn = std::max(n, 1);
+  const size_t v4 = es * 4;
+  struct A {
+    void **p;
+    size_t bytes;
+  } allocs[] = {
+      {&h->pos, v4 * nn}, {&h->size, v4 * nn}, {&h->off, v4 * (size_t)std::max(h->npin, 1)}, {&h->acc, v4 * nn},
+      {(void **)&h->flags_d, nn}, {(void **)&h->macro_ids, sizeof(int) * (size_t)std::max(h->nm, 1)},
+      {(void **)&h->macro_slot, sizeof(int) * nn}, {(void **)&h->net_start, sizeof(int) * (size_t)(h->nnet + 1)},
+      {(void **)&h->pin_inst, sizeof(int) * (size_t)std::max(h->npin, 1)}, {(void **)&h->q, 8 * nb},
+      {(void **)&h->corner, h->nm ? 8 * nb : (size_t)8}, {&h->rho, es * nb}, {&h->t1, es * nb}, {&h->t2, es * nb},
+      {&h->czpsi, es * nb}, {&h->szpsi, es * nb}, {&h->xinv, 2 * es * nb}, {&h->x2, es * nb},
+      {&h->ex, es * nb}, {&h->ey, es * nb}, {&h->ez, es * nb},
+      {(void **)&h->suffix, h->nm ? 3 * 8 * nb : (size_t)8}, {(void **)&h->mgrad, (size_t)24 * std::max(h->nm, 1)},
+      {(void **)&h->scal, sizeof(double) * S_COUNT}, {(void **)&h->zc, sizeof(ZStageC)},
+      {&h->gout, 3 * es * nn}, {(void **)&h->check_flag, sizeof(int)}};
+  for (auto &a : allocs) {
+    cudaError_t e = cudaMalloc(a.p, a.bytes);
+    if (e != cudaSuccess) {
+      cuda_fail(h, e, "cudaMalloc");
+      return bail(e == cudaErrorMemoryAllocation ? PLACE3D_ERR_OOM : PLACE3D_ERR_CUDA);
+    }
+  }
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    fail(h, PLACE3D_ERR_CUDA, "stream/event creation failed");
+    return bail(PLACE3D_ERR_CUDA);
+  }
+  int rc = h->precision == PLACE3D_FP64 ? upload_typed<double>(h, p, order, new_start)
+                                        : upload_typed<float>(h, p, order, new_start);
+  if (rc != PLACE3D_OK) return bail(rc);
+  if (cudaMemcpy(h->flags_d, fl.data(), nn, cudaMemcpyHostToDevice) != cudaSuccess ||
+      (h->nm && cudaMemcpy(h->macro_ids, mids.data(), sizeof(int) * h->nm, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(h->macro_slot, mslot.data(), sizeof(int) * nn, cudaMemcpyHostToDevice) != cudaSuccess) {
+    fail(h, PLACE3D_ERR_CUDA, "upload failed");
+    return bail(PLACE3D_ERR_CUDA);
+  }
+  ZStageC zc;
+  std::memset(&zc, 0, sizeof(zc));
+  zc.nx = h->nx;
+  zc.ny = h->ny;
+  zc.nz = h->nz;
+  const double pi = 3.14159265358979323846;
+  zc.pi_dx = pi / h->dx;
+  zc.pi_dy = pi / h->dy;
+  zc.pi_dz = pi / h->dz;
+  zc.inv_n = 1.0 / (double)h->nb;
+  for (int l = 0; l < h->nz; ++l)
+    for (int z = 0; z < h->nz; ++z) {
+      const double arg = pi * l * (z + 0.5) / h->nz;
+      zc.cz[l * kMaxNz + z] = std::cos(arg);
+      zc.sz[l * kMaxNz + z] = (l * pi / h->dz) * std::sin(arg);
+    }
+  if (cudaMemcpy(h->zc, &zc, sizeof(zc), cudaMemcpyHostToDevice) != cudaSuccess) {
+    fail(h, PLACE3D_ERR_CUDA, "upload failed");
+    return bail(PLACE3D_ERR_CUDA);
+  }
+  if (h->precision == PLACE3D_FP32_TC) {
+    std::string why;
+    h->tc = p3d_tc::create(h->device, h->nx, h->ny, h->nz, h->dx, h->dy, h->dz, h->ex, h->ey, h->ez,
+                           h->zc, &why);
+    if (!h->tc) {
+      fail(h, PLACE3D_ERR_UNSUPPORTED, "FP32_TC: " + why);
+      return bail(PLACE3D_ERR_UNSUPPORTED);
+    }
+  }
+  *out = h;
+  return PLACE3D_OK;
+}
+
+int place3d_geometry(const place3d_handle *h, double out[6]) {
+  if (!h || !out) return PLACE3D_ERR_INVALID_ARG;
+  out[0] = h->wb;
+  out[1] = h->hb;
+  out[2] = h->db;
+  out[3] = h->dx;
+  out[4] = h->dy;
+  out[5] = h->dz;
+  return PLACE3D_OK;
+}
+
+int place3d_set_positions(place3d_handle *h, const void *x, const void *y, const void *z, int dtype, int mem) {
+  if (!h) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL handle");
+  if (h->n == 0) return PLACE3D_OK;
+  if (!x || !y || !z) return fail(h, PLACE3D_ERR_INVALID_ARG, "NULL position array");
+  if ((dtype != PLACE3D_F64 && dtype != PLACE3D_F32) || (mem != PLACE3D_MEM_HOST && mem != PLACE3D_MEM_DEVICE))
+    return fail(h, PLACE3D_ERR_INVALID_ARG, "bad dtype or memory kind");
+  P3D_CUDA(h, cudaSetDevice(h->device));
+  cudaStream_t s = h->stream;
+  const int n = h->n;
+  const size_t eb = dtype == PLACE3D_F64 ? 8 : 4;
+  const void *px = x, *py = y, *pz = z;
+  StageScope sc(h, ST_PREP, s);
+  if (mem == PLACE3D_MEM_HOST) {
+    if (!h->stage_in) P3D_CUDA(h, cudaMalloc(&h->stage_in, 3 * 8 * (size_t)n));
+    char *st = static_cast<char *>(h->stage_in);
+    P3D_CUDA(h, cudaMemcpyAsync(st, x, eb * n, cudaMemcpyHostToDevice, s));
+    P3D_CUDA(h, cudaMemcpyAsync(st + eb * n, y, eb * n, cudaMemcpyHostToDevice, s));
+    P3D_CUDA(h, cudaMemcpyAsync(st + 2 * eb * n, z, eb * n, cudaMemcpyHostToDevice, s));
+    px = st;
+    py = st + eb * n;
+    pz = st + 2 * eb * n;
+  }
+  const bool check = h->flags & PLACE3D_FLAG_CHECKS;
+  int *bad = check ? h->check_flag : nullptr;
+  if (check) P3D_CUDA(h, cudaMemsetAsync(h->check_flag, 0, sizeof(int), s));
+  const double zlo = 0.25 * h->dz, zhi = 0.75 * h->dz;
+  const int g = grid_for(n, 256);
+  if (h->precision == PLACE3D_FP64) {
+    if (dtype == PLACE3D_F64)
+      k_pack<double, double><<<g, 256, 0, s>>>(n, (const double *)px, (const double *)py, (const double *)pz,
+                                               as<V4<double>>(h->pos), zlo, zhi, bad);
+    else
+      k_pack<float, double><<<g, 256, 0, s>>>(n, (const float *)px, (const float *)py, (const float *)pz,
+                                              as<V4<double>>(h->pos), zlo, zhi, bad);
+  } else {
+    if (dtype == PLACE3D_F64)
+      k_pack<double, float><<<g, 256, 0, s>>>(n, (const double *)px, (const double *)py, (const double *)pz,
+                                              as<V4<float>>(h->pos), zlo, zhi, bad);
+    else
+      k_pack<float, float><<<g, 256, 0, s>>>(n, (const float *)px, (const float *)py, (const float *)pz,
+                                             as<V4<float>>(h->pos), zlo, zhi, bad);
+  }
+  count_launch(h, ST_PREP);
+  P3D_CUDA(h, cudaGetLastError());
+  if (check) {
+    int flag = 0;
+    P3D_CUDA(h, cudaMemcpyAsync(&flag, h->check_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    P3D_CUDA(h, cudaStreamSynchronize(s));
+    if (flag) return fail(h, PLACE3D_ERR_OUT_OF_RANGE, "a position is non-finite or z is outside [d_z/4, 3 d_z/4]");
+  }
+  return PLACE3D_OK;
+}
+
+int place3d_eval_objective_and_grad(place3d_handle *h, place3d_result *out, void *gx, void *gy, void *gz,
+                                    int dtype, int mem) {
+  if (!h) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL handle");
+  const int ng = (gx != nullptr) + (gy != nullptr) + (gz != nullptr);
+  if (ng != 0 && ng != 3) return fail(h, PLACE3D_ERR_INVALID_ARG, "pass all three gradient arrays or none");
+  if (ng && ((dtype != PLACE3D_F64 && dtype != PLACE3D_F32) || (mem != PLACE3D_MEM_HOST && mem != PLACE3D_MEM_DEVICE)))
+    return fail(h, PLACE3D_ERR_INVALID_ARG, "bad dtype or memory kind");
+  P3D_CUDA(h, cudaSetDevice(h->device));
+  const int rc = h->precision == PLACE3D_FP64 ? eval_impl<double>(h, gx, gy, gz, dtype, mem)
+                                              : eval_impl<float>(h, gx, gy, gz, dtype, mem);
+  if (rc != PLACE3D_OK) return rc;
+  P3D_CUDA(h, cudaMemcpyAsync(h->host_scal, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, h->stream));
+  h->have_result = true;
+  if (out || (ng && mem == PLACE3D_MEM_HOST)) {
+    P3D_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (out) fill_result(h, out);
+  }
+  return PLACE3D_OK;
+}
+
+int place3d_get_result(place3d_handle *h, place3d_result *out) {
+  if (!h || !out) return fail(h, PLACE3D_ERR_INVALID_ARG, "NULL argument");
+  if (!h->have_result) return fail(h, PLACE3D_ERR_INVALID_ARG, "no evaluation has been enqueued");
+  P3D_CUDA(h, cudaSetDevice(h->device));
+  P3D_CUDA(h, cudaStreamSynchronize(h->stream));
+  fill_result(h, out);
+  return PLACE3D_OK;
+}
+
+int place3d_copy_map(place3d_handle *h, int which, void *dst, int mem) {
+  if (!h || !dst) return fail(h, PLACE3D_ERR_INVALID_ARG, "NULL argument");
+  P3D_CUDA(h, cudaSetDevice(h->device));
+  const void *src = nullptr;
+  size_t bytes = 0;
+  switch (which) {
+    case PLACE3D_MAP_RHO_FIXED: src = h->q; bytes = 8 * h->nb; break;
+    case PLACE3D_MAP_EX: src = h->ex; bytes = h->esz * h->nb; break;
+    case PLACE3D_MAP_EY: src = h->ey; bytes = h->esz * h->nb; break;
+    case PLACE3D_MAP_EZ: src = h->ez; bytes = h->esz * h->nb; break;
+    default: return fail(h, PLACE3D_ERR_INVALID_ARG, "unknown map");
+  }
+  if (which == PLACE3D_MAP_RHO_FIXED) {
+    // the fixed-point map of the last evaluation = cell counts + prefix-summed macro corners
+    std::vector<long long> a(h->nb), c;
+    P3D_CUDA(h, cudaStreamSynchronize(h->stream));
+    P3D_CUDA(h, cudaMemcpy(a.data(), h->q, bytes, cudaMemcpyDeviceToHost));
+    if (h->nm > 0) {
+      c.resize(h->nb);
+      P3D_CUDA(h, cudaMemcpy(c.data(), h->corner, bytes, cudaMemcpyDeviceToHost));
+      // corner holds x/y-scanned corners; finish the z prefix here (integers, exact)
+      const size_t pl = (size_t)h->nx * h->ny;
+      for (size_t t = 0; t < pl; ++t) {
+        long long acc = 0;
+        for (int z = 0; z < h->nz; ++z) {
+          acc += c[z * pl + t];
+          a[z * pl + t] += acc;
+        }
+      }
+    }
+    if (mem == PLACE3D_MEM_HOST)
+      std::memcpy(dst, a.data(), bytes);
+    else
+      P3D_CUDA(h, cudaMemcpy(dst, a.data(), bytes, cudaMemcpyHostToDevice));
+    return PLACE3D_OK;
+  }
+  P3D_CUDA(h, cudaStreamSynchronize(h->stream));
+  P3D_CUDA(h, cudaMemcpy(dst, src, bytes, mem == PLACE3D_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice));
+  return PLACE3D_OK;
+}
+
+int place3d_copy_wl_parts(place3d_handle *h, double *gx, double *gy, double *gfd, double *gwaz) {
+  if (!h) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL handle");
+  P3D_CUDA(h, cudaSetDevice(h->device));
+  P3D_CUDA(h, cudaStreamSynchronize(h->stream));
+  const int n = h->n;
+  std::vector<double> v(4 * (size_t)n);
+  if (h->precision == PLACE3D_FP64) {
+    P3D_CUDA(h, cudaMemcpy(v.data(), h->acc, 32 * (size_t)n, cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float> f(4 * (size_t)n);
+    P3D_CUDA(h, cudaMemcpy(f.data(), h->acc, 16 * (size_t)n, cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < f.size(); ++k) v[k] = f[k];
+  }
+  for (int i = 0; i < n; ++i) {
+    if (gx) gx[i] = v[4 * i + 0];
+    if (gy) gy[i] = v[4 * i + 1];
+    if (gfd) gfd[i] = v[4 * i + 2];
+    if (gwaz) gwaz[i] = v[4 * i + 3];
+  }
+  return PLACE3D_OK;
+}
+
+int place3d_set_profiling(place3d_handle *h, int on) {
+  if (!h) return PLACE3D_ERR_INVALID_ARG;
+  h->profiling = on != 0;
+  return PLACE3D_OK;
+}
+
+int place3d_num_stages(void) { return ST_COUNT; }
+
+const char *place3d_stage_name(int stage) {
+  return (stage >= 0 && stage < ST_COUNT) ? kStageNames[stage] : "";
+}
+
+int place3d_stage_times(place3d_handle *h, double *ms, int64_t *launches, int64_t *evals, int reset) {
+  if (!h) return PLACE3D_ERR_INVALID_ARG;
+  P3D_CUDA(h, cudaSetDevice(h->device));
+  for (auto &e : h->ev_live) {
+    P3D_CUDA(h, cudaEventSynchronize(e.b));
+    float t = 0;
+    P3D_CUDA(h, cudaEventElapsedTime(&t, e.a, e.b));
+    h->stage_ms[e.stage] += t;
+    h->ev_pool.push_back(e);
+  }
+  h->ev_live.clear();
+  for (int k = 0; k < ST_COUNT; ++k) {
+    if (ms) ms[k] = h->stage_ms[k];
+    if (launches) launches[k] = h->stage_launch[k];
+  }
+  if (evals) *evals = h->prof_evals;
+  if (reset) {
+    std::memset(h->stage_ms, 0, sizeof(h->stage_ms));
+    std::memset(h->stage_launch, 0, sizeof(h->stage_launch));
+    h->prof_evals = 0;
+  }
+  return PLACE3D_OK;
+}
+
+int place3d_launches_per_eval(const place3d_handle *h) { return h ? h->launches : 0; }
+
+const char *place3d_last_error(const place3d_handle *h) { return h ? h->err.c_str() : g_thread_err.c_str(); }
+
+void place3d_destroy(place3d_handle *h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  if (h->side) cudaStreamSynchronize(h->side);
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,146 @@
+// Spectral Poisson solve (eqs. density-coef, poisson-sol-potential,
+// possion-sol-force) as per-axis dense matrix products, CUDA-core form
+// (FP64 plain path and FP32 path), plus the z-axis stage that applies the
+// N_z-point transforms, the spectral scaling and the energy sum.
+#pragma once
+#include "common.cuh"
+
+namespace p3d {
+
+// One batched product out[b][n][m] = sum_k A[b][m][k] * W[n][k]: rows of A
+// are contracted with rows of W (both K-contiguous) and the result is
+// stored transposed, so that the next axis becomes the contiguous one.
+template <typename T> struct GemmProb {
+  const T *A;
+  const T *W;
+  T *out;
+  long long a_bstride, o_bstride;  // elements between batches
+  int batches, M, N, K;
+  int tiles_m, tiles_n;            // filled by the launcher
+};
+
+template <typename T> struct GemmGroup {
+  GemmProb<T> p[3];
+  int count;
+  int tile_start[4];
+};
+
+constexpr int kBM = 64, kBN = 64, kBK = 16;
+
+// 256 threads, 64x64 tile, each thread 4 (m) x 4 (n) outputs.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_simt(GemmGroup<T> g) {
+  __shared__ T As[kBK][kBM + 4];
+  __shared__ T Ws[kBK][kBN + 4];
+  int tile = blockIdx.x, pi = 0;
+  while (pi + 1 < g.count && tile >= g.tile_start[pi + 1]) ++pi;
+  const GemmProb<T> &P = g.p[pi];
+  tile -= g.tile_start[pi];
+  const int per_batch = P.tiles_m * P.tiles_n;
+  const int b = tile / per_batch;
+  const int r = tile - b * per_batch;
+  const int m0 = (r % P.tiles_m) * kBM, n0 = (r / P.tiles_m) * kBN;
+  const T *A = P.A + (long long)b * P.a_bstride;
+  T *O = P.out + (long long)b * P.o_bstride;
+  const int t = threadIdx.x;
+  const int tm = t & 15, tn = t >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  // loader mapping: 64 rows x 16 k, 4 consecutive k per thread
+  const int lr = t >> 2, lk = (t & 3) * 4;
+  for (int k0 = 0; k0 < P.K; k0 += kBK) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int kk = k0 + lk + u;
+      const int am = m0 + lr, wn = n0 + lr;
+      As[lk + u][lr] = (am < P.M && kk < P.K) ? A[(long long)am * P.K + kk] : T(0);
+      Ws[lk + u][lr] = (wn < P.N && kk < P.K) ? P.W[(long long)wn * P.K + kk] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; ++kk) {
+      T a[4], w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tm * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[j] = Ws[kk][tn * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * w[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int n = n0 + tn * 4 + j;
+    if (n >= P.N) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int m = m0 + tm * 4 + i;
+      if (m < P.M) O[(long long)n * P.M + m] = acc[i][j];
+    }
+  }
+}
+
+// z-stage constants.
+constexpr int kMaxNz = 16;
+struct ZStageC {
+  int nx, ny, nz;
+  double pi_dx, pi_dy, pi_dz;  // pi/d_x, pi/d_y, pi/d_z
+  double inv_n;                // 1/N
+  double cz[kMaxNz * kMaxNz];  // cos(pi l (z+1/2)/N_z), [l][z]
+  double sz[kMaxNz * kMaxNz];  // w_l sin(pi l (z+1/2)/N_z), [l][z]
+};
+
+// Input T2[z][k][j] (x and y already transformed, j fastest).  For each
+// (k, j): a_l = (1/N) sum_z T2[z] cos(...), psi = c_j c_k c_l a/|w|^2 (psi_000
+// = 0), energy sum += c c c a^2/|w|^2, then Czpsi[z] = sum_l psi_l cos(...)
+// and Szpsi[z] = sum_l psi_l w_l sin(...).  One thread per (k, j).
+template <typename T>
+__global__ void __launch_bounds__(256) k_zstage(const ZStageC *__restrict__ zc, const T *__restrict__ in,
+                                                T *__restrict__ czpsi, T *__restrict__ szpsi,
+                                                double *__restrict__ esum) {
+  const int nx = zc->nx, ny = zc->ny, nz = zc->nz;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0;
+  if (t < nx * ny) {
+    const int j = t % nx, k = t / nx;
+    const size_t plane = (size_t)nx * ny;
+    T v[kMaxNz];
+    for (int z = 0; z < nz; ++z) v[z] = in[z * plane + t];
+    const double wj = j * zc->pi_dx, wk = k * zc->pi_dy;
+    const double cjk = (j ? 2.0 : 1.0) * (k ? 2.0 : 1.0);
+    T psi[kMaxNz];
+    for (int l = 0; l < nz; ++l) {
+      T a = 0;
+      for (int z = 0; z < nz; ++z) a += v[z] * (T)zc->cz[l * kMaxNz + z];
+      a *= (T)zc->inv_n;
+      const double wl = l * zc->pi_dz;
+      const double w2 = wj * wj + wk * wk + wl * wl;
+      if (j == 0 && k == 0 && l == 0) {
+        psi[l] = 0;
+      } else {
+        const double cc = cjk * (l ? 2.0 : 1.0);
+        psi[l] = (T)(cc / w2) * a;
+        e += cc * (double)a * (double)a / w2;
+      }
+    }
+    for (int z = 0; z < nz; ++z) {
+      T sc = 0, ss = 0;
+      for (int l = 0; l < nz; ++l) {
+        sc += psi[l] * (T)zc->cz[l * kMaxNz + z];
+        ss += psi[l] * (T)zc->sz[l * kMaxNz + z];
+      }
+      czpsi[z * plane + t] = sc;
+      szpsi[z * plane + t] = ss;
+    }
+  }
+  double v1[1] = {e};
+  block_sum_atomic<1>(v1, esum);
+}
+
+}  // namespace p3d

@@ -1,0 +1,452 @@
+// Bistratal weighted-average wirelength (eqs. wa-model-approx, wl-obj,
+// wl-model), its gradient and the incremental FD depth gradient (eq.
+// fda-grad, Sec. IV-B), per net with segmented reductions.
+//
+// Each net is reduced by a group of G lanes (G = 4, 8, 16, 32; PPL pins per
+// lane held in registers), or by a whole block for high-fanout nets.  Per
+// net: the 1st and 2nd extremes of the top and bottom pins in x and y, the
+// WA sums of the top and bottom pins (each shifted by its own extreme, so no
+// exponential can overflow and none of a sub-net's terms underflows because
+// of the other die), and the depth span.  The whole-net WA sums are derived
+// from the two sides' sums by one rescale per net.  The per-pin gradient is
+// then pushed to the instance accumulators (gx, gy, fd, waz).
+#pragma once
+#include "common.cuh"
+
+namespace p3d {
+
+template <typename T> struct WlC {
+  T zmid;      // d_z/2 (partition threshold, Sec. II-B)
+  T inv_g;     // 1/gamma
+  T inv_gz;    // 1/gamma_z
+  T fd_scale;  // 4/d_z (eq. fda-grad)
+};
+
+template <typename T> struct Pin {
+  int inst, slot;
+  bool top;
+  T px, py, pz;  // pin on its current die
+  T qx, qy;      // the same pin if its instance were on the other die
+};
+
+template <typename T>
+__device__ __forceinline__ Pin<T> load_pin(int p, int slot, const int *__restrict__ pin_inst,
+                                           const V4<T> *__restrict__ off,
+                                           const V4<T> *__restrict__ pos, const WlC<T> &c) {
+  Pin<T> q;
+  q.inst = __ldg(pin_inst + p);
+  q.slot = slot;
+  const V4<T> o = off[p];  // (bot x, bot y, top x, top y)
+  const V4<T> s = pos[q.inst];
+  q.top = s.z > c.zmid;
+  q.px = s.x + (q.top ? o.z : o.x);
+  q.py = s.y + (q.top ? o.w : o.y);
+  q.qx = s.x + (q.top ? o.x : o.z);
+  q.qy = s.y + (q.top ? o.y : o.w);
+  q.pz = s.z;
+  return q;
+}
+
+// 1st/2nd extremes of one side on one axis (the 1st and 2nd outermost boxes).
+template <typename T> struct Ext {
+  T mx1, mx2, mn1, mn2;
+  int amx, amn;
+  __device__ __forceinline__ void init() {
+    mx1 = mx2 = -big<T>();
+    mn1 = mn2 = big<T>();
+    amx = amn = -1;
+  }
+  __device__ __forceinline__ void add(T v, int k) {
+    if (v > mx1) { mx2 = mx1; mx1 = v; amx = k; } else if (v > mx2) { mx2 = v; }
+    if (v < mn1) { mn2 = mn1; mn1 = v; amn = k; } else if (v < mn2) { mn2 = v; }
+  }
+  __device__ __forceinline__ void merge(T bmx1, T bmx2, int bamx, T bmn1, T bmn2, int bamn) {
+    if (bmx1 > mx1) { mx2 = mx1 > bmx2 ? mx1 : bmx2; mx1 = bmx1; amx = bamx; }
+    else { mx2 = mx2 > bmx1 ? mx2 : bmx1; }
+    if (bmn1 < mn1) { mn2 = mn1 < bmn2 ? mn1 : bmn2; mn1 = bmn1; amn = bamn; }
+    else { mn2 = mn2 < bmn1 ? mn2 : bmn1; }
+  }
+  template <int W> __device__ __forceinline__ void shfl_reduce() {
+#pragma unroll
+    for (int m = W / 2; m; m >>= 1) {
+      const T a = shfl_xor(mx1, m, W), b = shfl_xor(mx2, m, W);
+      const T c = shfl_xor(mn1, m, W), d = shfl_xor(mn2, m, W);
+      const int ia = shfl_xor(amx, m, W), ic = shfl_xor(amn, m, W);
+      merge(a, b, ia, c, d, ic);
+    }
+  }
+};
+
+template <typename T> struct NetExt {
+  Ext<T> e[2][2];  // [axis x/y][side bottom/top]
+  int ntop, n;
+  T zmx, zmn;
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int s = 0; s < 2; ++s) e[a][s].init();
+    ntop = n = 0;
+    zmx = -big<T>();
+    zmn = big<T>();
+  }
+  __device__ __forceinline__ void add(const Pin<T> &p) {
+    const int s = p.top;
+    e[0][s].add(p.px, p.slot);
+    e[1][s].add(p.py, p.slot);
+    ntop += s;
+    n += 1;
+    zmx = p.pz > zmx ? p.pz : zmx;
+    zmn = p.pz < zmn ? p.pz : zmn;
+  }
+  __device__ __forceinline__ void merge(const NetExt &b) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const Ext<T> &x = b.e[a][s];
+        e[a][s].merge(x.mx1, x.mx2, x.amx, x.mn1, x.mn2, x.amn);
+      }
+    ntop += b.ntop;
+    n += b.n;
+    zmx = b.zmx > zmx ? b.zmx : zmx;
+    zmn = b.zmn < zmn ? b.zmn : zmn;
+  }
+  template <int W> __device__ __forceinline__ void shfl_reduce() {
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int s = 0; s < 2; ++s) e[a][s].template shfl_reduce<W>();
+#pragma unroll
+    for (int m = W / 2; m; m >>= 1) {
+      ntop += shfl_xor(ntop, m, W);
+      n += shfl_xor(n, m, W);
+      const T a = shfl_xor(zmx, m, W), b = shfl_xor(zmn, m, W);
+      zmx = a > zmx ? a : zmx;
+      zmn = b < zmn ? b : zmn;
+    }
+  }
+};
+
+// WA sums per [axis][side]: sum e+, sum v e+, sum e-, sum v e-; and for z.
+template <typename T> struct Sums {
+  T v[2][2][4];
+  T z[4];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[a][s][k] = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) z[k] = 0;
+  }
+  __device__ __forceinline__ void merge(const Sums &b) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[a][s][k] += b.v[a][s][k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) z[k] += b.z[k];
+  }
+  template <int W> __device__ __forceinline__ void shfl_reduce() {
+#pragma unroll
+    for (int m = W / 2; m; m >>= 1) {
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) v[a][s][k] += shfl_xor(v[a][s][k], m, W);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) z[k] += shfl_xor(z[k], m, W);
+    }
+  }
+};
+
+// Exponentials of one pin: x+, x-, y+, y-, z+, z- (shifted by its side's
+// extremes in x, y and by the net's extremes in z).
+template <typename T>
+__device__ __forceinline__ void pin_exps(const Pin<T> &p, const NetExt<T> &X, const WlC<T> &c,
+                                         T (&ex)[6]) {
+  const int s = p.top;
+  ex[0] = r_exp((p.px - X.e[0][s].mx1) * c.inv_g);
+  ex[1] = r_exp((X.e[0][s].mn1 - p.px) * c.inv_g);
+  ex[2] = r_exp((p.py - X.e[1][s].mx1) * c.inv_g);
+  ex[3] = r_exp((X.e[1][s].mn1 - p.py) * c.inv_g);
+  ex[4] = r_exp((p.pz - X.zmx) * c.inv_gz);
+  ex[5] = r_exp((X.zmn - p.pz) * c.inv_gz);
+}
+
+template <typename T>
+__device__ __forceinline__ void sums_add(Sums<T> &S, const Pin<T> &p, const T (&ex)[6]) {
+  const int s = p.top;
+  S.v[0][s][0] += ex[0];
+  S.v[0][s][1] += p.px * ex[0];
+  S.v[0][s][2] += ex[1];
+  S.v[0][s][3] += p.px * ex[1];
+  S.v[1][s][0] += ex[2];
+  S.v[1][s][1] += p.py * ex[2];
+  S.v[1][s][2] += ex[3];
+  S.v[1][s][3] += p.py * ex[3];
+  S.z[0] += ex[4];
+  S.z[1] += p.pz * ex[4];
+  S.z[2] += ex[5];
+  S.z[3] += p.pz * ex[5];
+}
+
+// Per-net results of one axis.
+template <typename T> struct AxisNet {
+  bool all;          // active branch of max{p^_e, p^_e+ + p^_e-} (ties -> whole net)
+  T f[2], h[2];      // rescale of each side's + and - sums to the whole net's shifts
+  T SP, SM, M, m;    // whole-net WA sums and the two weighted averages
+  T Ms[2], ms[2];    // per side weighted averages
+  T what;            // W^_e on this axis
+  T wexact;          // eq. wl-obj on this axis, exact extremes
+};
+
+template <typename T>
+__device__ __forceinline__ AxisNet<T> axis_net(int a, const NetExt<T> &X, const Sums<T> &S,
+                                               const WlC<T> &c) {
+  AxisNet<T> r;
+  const int nt = X.ntop, nb = X.n - X.ntop;
+  const bool has[2] = {nb > 0, nt > 0};
+  T mxA = -big<T>(), mnA = big<T>();
+  T p[2] = {T(0), T(0)}, hp[2] = {T(0), T(0)};
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    r.Ms[s] = r.ms[s] = T(0);
+    if (has[s]) {
+      const Ext<T> &e = X.e[a][s];
+      mxA = e.mx1 > mxA ? e.mx1 : mxA;
+      mnA = e.mn1 < mnA ? e.mn1 : mnA;
+      r.Ms[s] = S.v[a][s][1] / S.v[a][s][0];
+      r.ms[s] = S.v[a][s][3] / S.v[a][s][2];
+      p[s] = r.Ms[s] - r.ms[s];
+      hp[s] = e.mx1 - e.mn1;
+    }
+  }
+  T SP = 0, NP = 0, SM = 0, NM = 0;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    r.f[s] = r.h[s] = T(0);
+    if (has[s]) {
+      r.f[s] = r_exp((X.e[a][s].mx1 - mxA) * c.inv_g);
+      r.h[s] = r_exp((mnA - X.e[a][s].mn1) * c.inv_g);
+      SP += S.v[a][s][0] * r.f[s];
+      NP += S.v[a][s][1] * r.f[s];
+      SM += S.v[a][s][2] * r.h[s];
+      NM += S.v[a][s][3] * r.h[s];
+    }
+  }
+  r.SP = SP;
+  r.SM = SM;
+  r.M = NP / SP;
+  r.m = NM / SM;
+  const T pall = r.M - r.m;
+  r.all = pall >= p[0] + p[1];
+  r.what = r.all ? pall : p[0] + p[1];
+  const T hall = mxA - mnA;
+  r.wexact = hall > hp[0] + hp[1] ? hall : hp[0] + hp[1];
+  return r;
+}
+
+// W_e,x after pin `slot` leaves side s for the other side at coordinate v.
+template <typename T>
+__device__ __forceinline__ T moved_axis(const Ext<T> &es, const Ext<T> &eo, int ns, int no, int slot,
+                                        T v) {
+  const int ns1 = ns - 1;
+  T smax = 0, smin = 0, ps = 0;
+  if (ns1 > 0) {
+    smax = slot == es.amx ? es.mx2 : es.mx1;
+    smin = slot == es.amn ? es.mn2 : es.mn1;
+    ps = smax - smin;
+  }
+  const T omax = no ? (eo.mx1 > v ? eo.mx1 : v) : v;
+  const T omin = no ? (eo.mn1 < v ? eo.mn1 : v) : v;
+  const T po = omax - omin;
+  const T amax = ns1 > 0 ? (smax > omax ? smax : omax) : omax;
+  const T amin = ns1 > 0 ? (smin < omin ? smin : omin) : omin;
+  const T hall = amax - amin;
+  return hall > ps + po ? hall : ps + po;
+}
+
+template <typename T> struct NetScal {
+  AxisNet<T> ax[2];
+  T zM, zm, zS1, zS2, pz;
+  T wcur;  // exact W_Bi
+};
+
+template <typename T>
+__device__ __forceinline__ NetScal<T> net_scalars(const NetExt<T> &X, const Sums<T> &S,
+                                                  const WlC<T> &c) {
+  NetScal<T> r;
+  r.ax[0] = axis_net(0, X, S, c);
+  r.ax[1] = axis_net(1, X, S, c);
+  r.zS1 = S.z[0];
+  r.zS2 = S.z[2];
+  r.zM = S.z[1] / S.z[0];
+  r.zm = S.z[3] / S.z[2];
+  r.pz = r.zM - r.zm;
+  r.wcur = r.ax[0].wexact + r.ax[1].wexact;
+  return r;
+}
+
+// Gradient of one WA average pair at v given the exponentials (eq.
+// wa-model-approx differentiated): (e+/S+)(1 + (v-M)/g) - (e-/S-)(1 - (v-m)/g).
+template <typename T>
+__device__ __forceinline__ T wa_grad(T v, T ep, T SP, T M, T em, T SM, T m, T inv_g) {
+  return (ep / SP) * (T(1) + (v - M) * inv_g) - (em / SM) * (T(1) - (v - m) * inv_g);
+}
+
+// Per-pin outputs (gx, gy, fd, waz) -> instance accumulators.
+template <typename T>
+__device__ __forceinline__ void pin_outputs(const Pin<T> &p, const T (&ex)[6], const NetExt<T> &X,
+                                            const Sums<T> &S, const NetScal<T> &N,
+                                            const WlC<T> &c, V4<T> *__restrict__ acc) {
+  const int s = p.top;
+  T g[2];
+  const T v[2] = {p.px, p.py};
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const AxisNet<T> &A = N.ax[a];
+    if (A.all)
+      g[a] = wa_grad(v[a], ex[2 * a] * A.f[s], A.SP, A.M, ex[2 * a + 1] * A.h[s], A.SM, A.m, c.inv_g);
+    else
+      g[a] = wa_grad(v[a], ex[2 * a], S.v[a][s][0], A.Ms[s], ex[2 * a + 1], S.v[a][s][2], A.ms[s],
+                     c.inv_g);
+  }
+  const T gz = wa_grad(p.pz, ex[4], N.zS1, N.zM, ex[5], N.zS2, N.zm, c.inv_gz);
+  const int ns = s ? X.ntop : X.n - X.ntop, no = X.n - ns;
+  const T wm = moved_axis(X.e[0][s], X.e[0][1 - s], ns, no, p.slot, p.qx) +
+               moved_axis(X.e[1][s], X.e[1][1 - s], ns, no, p.slot, p.qy);
+  const T fd = c.fd_scale * (s ? (N.wcur - wm) : (wm - N.wcur));
+  acc_add(acc + p.inst, g[0], g[1], fd, gz);
+}
+
+// ---- nets of degree <= G*PPL, one group of G lanes per net ----
+template <typename T, int G, int PPL>
+__global__ void __launch_bounds__(256) k_wl_group(int net0, int nnets, const int *__restrict__ net_start,
+                                                  const int *__restrict__ pin_inst,
+                                                  const V4<T> *__restrict__ off,
+                                                  const V4<T> *__restrict__ pos, WlC<T> c,
+                                                  V4<T> *__restrict__ acc, double *__restrict__ scal) {
+  const int lane = threadIdx.x & (G - 1);
+  const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const bool valid = gid < nnets;
+  int s0 = 0, d = 0;
+  if (valid) {
+    s0 = __ldg(net_start + net0 + gid);
+    d = __ldg(net_start + net0 + gid + 1) - s0;
+  }
+  Pin<T> pin[PPL];
+  bool has[PPL];
+  NetExt<T> X;
+  X.init();
+#pragma unroll
+  for (int r = 0; r < PPL; ++r) {
+    const int k = lane + r * G;
+    has[r] = k < d;
+    if (has[r]) {
+      pin[r] = load_pin(s0 + k, k, pin_inst, off, pos, c);
+      X.add(pin[r]);
+    }
+  }
+  X.template shfl_reduce<G>();
+  Sums<T> S;
+  S.init();
+  T ex[PPL][6];
+#pragma unroll
+  for (int r = 0; r < PPL; ++r)
+    if (has[r]) {
+      pin_exps(pin[r], X, c, ex[r]);
+      sums_add(S, pin[r], ex[r]);
+    }
+  S.template shfl_reduce<G>();
+  double vals[4] = {0, 0, 0, 0};
+  if (d >= 2) {
+    const NetScal<T> N = net_scalars(X, S, c);
+#pragma unroll
+    for (int r = 0; r < PPL; ++r)
+      if (has[r]) pin_outputs(pin[r], ex[r], X, S, N, c, acc);
+    if (lane == 0) {
+      vals[0] = (double)N.ax[0].what + (double)N.ax[1].what;
+      vals[1] = (double)N.pz;
+      vals[2] = (double)N.wcur;
+      vals[3] = (X.ntop > 0 && X.ntop < X.n) ? 1.0 : 0.0;
+    }
+  }
+  block_sum_atomic<4>(vals, scal + S_WL_BI);
+}
+
+// ---- high-fanout nets: one block (256 threads) per net, three passes ----
+template <typename T>
+__global__ void __launch_bounds__(256) k_wl_block(int net0, const int *__restrict__ net_start,
+                                                  const int *__restrict__ pin_inst,
+                                                  const V4<T> *__restrict__ off,
+                                                  const V4<T> *__restrict__ pos, WlC<T> c,
+                                                  V4<T> *__restrict__ acc, double *__restrict__ scal) {
+  __shared__ NetExt<T> sx[8];
+  __shared__ Sums<T> ss[8];
+  const int e = net0 + blockIdx.x;
+  const int s0 = net_start[e], d = net_start[e + 1] - s0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  NetExt<T> X;
+  X.init();
+  for (int k = tid; k < d; k += blockDim.x) X.add(load_pin(s0 + k, k, pin_inst, off, pos, c));
+  X.template shfl_reduce<32>();
+  if (lane == 0) sx[warp] = X;
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) sx[0].merge(sx[w]);
+  }
+  __syncthreads();
+  X = sx[0];
+  Sums<T> S;
+  S.init();
+  for (int k = tid; k < d; k += blockDim.x) {
+    const Pin<T> p = load_pin(s0 + k, k, pin_inst, off, pos, c);
+    T ex[6];
+    pin_exps(p, X, c, ex);
+    sums_add(S, p, ex);
+  }
+  S.template shfl_reduce<32>();
+  if (lane == 0) ss[warp] = S;
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) ss[0].merge(ss[w]);
+  }
+  __syncthreads();
+  S = ss[0];
+  const NetScal<T> N = net_scalars(X, S, c);
+  for (int k = tid; k < d; k += blockDim.x) {
+    const Pin<T> p = load_pin(s0 + k, k, pin_inst, off, pos, c);
+    T ex[6];
+    pin_exps(p, X, c, ex);
+    pin_outputs(p, ex, X, S, N, c, acc);
+  }
+  if (tid == 0) {
+    atomicAdd(scal + S_WL_BI, (double)N.ax[0].what + (double)N.ax[1].what);
+    atomicAdd(scal + S_WL_Z, (double)N.pz);
+    atomicAdd(scal + S_HPWL, (double)N.wcur);
+    if (X.ntop > 0 && X.ntop < X.n) atomicAdd(scal + S_NCROSS, 1.0);
+  }
+}
+
+// ---- a9: L1 norms S_x, S_y, S_z of the wirelength gradient (FP64) ----
+template <typename T>
+__global__ void __launch_bounds__(256) k_norms(int n, const V4<T> *__restrict__ acc, double *__restrict__ scal) {
+  double v[3] = {0, 0, 0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const V4<T> a = acc[i];
+    v[0] += fabs((double)a.x);
+    v[1] += fabs((double)a.y);
+    v[2] += fabs((double)a.z);
+  }
+  block_sum_atomic<3>(v, scal + S_SX);
+}
+
+}  // namespace p3d

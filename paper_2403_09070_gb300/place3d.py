@@ -1,0 +1,264 @@
+"""Thin Python binding of the place3d C ABI (include/place3d.h).
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+kernels of libplace3d.so.  There is no CPU fallback: if the library cannot be
+loaded the constructor raises.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA
+memory; CUDA tensors are used in place on the handle's stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FP64, FP32, FP32_TC = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_tc": FP32_TC}
+F64, F32 = 0, 1
+MEM_HOST, MEM_DEVICE = 0, 1
+FLAG_CHECKS = 1
+MAP_RHO_FIXED, MAP_EX, MAP_EY, MAP_EZ = 0, 1, 2, 3
+ERRORS = {-1: "INVALID_ARG", -2: "BAD_CSR", -3: "OUT_OF_RANGE", -4: "CUDA", -5: "OOM", -7: "UNSUPPORTED"}
+
+
+class Place3DError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"place3d error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("n_inst", C.c_int32), ("is_macro", C.c_void_p), ("z_fixed", C.c_void_p),
+        ("w_bot", C.c_void_p), ("h_bot", C.c_void_p), ("w_top", C.c_void_p), ("h_top", C.c_void_p),
+        ("n_net", C.c_int32), ("n_pin", C.c_int32), ("net_start", C.c_void_p), ("pin_inst", C.c_void_p),
+        ("pin_off_bot_x", C.c_void_p), ("pin_off_bot_y", C.c_void_p),
+        ("pin_off_top_x", C.c_void_p), ("pin_off_top_y", C.c_void_p),
+        ("xl", C.c_double), ("yl", C.c_double), ("xh", C.c_double), ("yh", C.c_double),
+        ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+        ("gamma", C.c_double), ("gamma_z", C.c_double), ("alpha", C.c_double), ("lam", C.c_double),
+        ("precision", C.c_int32), ("flags", C.c_int32),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("obj", "wl_bi", "wl_z", "energy", "hpwl_d2d", "n_cross",
+                                           "g_scale", "s_x", "s_y", "s_z")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ("place3d_create", "place3d_geometry", "place3d_alpha", "place3d_set_positions",
+           "place3d_eval_objective_and_grad", "place3d_get_result", "place3d_copy_map",
+           "place3d_copy_wl_parts", "place3d_set_profiling", "place3d_num_stages", "place3d_stage_name",
+           "place3d_stage_times", "place3d_launches_per_eval", "place3d_last_error", "place3d_destroy")
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.SO
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libplace3d.so (building it with nvcc first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.SO
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError(f"{path} is missing; run paper_2403_09070_gb300.build.build()")
+        _build.build()
+    L = C.CDLL(path)
+    vp, i32, d = C.c_void_p, C.c_int, C.c_double
+    L.place3d_create.argtypes = [C.POINTER(_Problem), i32, vp, C.POINTER(vp)]
+    L.place3d_geometry.argtypes = [vp, vp]
+    L.place3d_alpha.argtypes = [d] * 6
+    L.place3d_alpha.restype = d
+    L.place3d_set_positions.argtypes = [vp, vp, vp, vp, i32, i32]
+    L.place3d_eval_objective_and_grad.argtypes = [vp, C.POINTER(Result), vp, vp, vp, i32, i32]
+    L.place3d_get_result.argtypes = [vp, C.POINTER(Result)]
+    L.place3d_copy_map.argtypes = [vp, i32, vp, i32]
+    L.place3d_copy_wl_parts.argtypes = [vp, vp, vp, vp, vp]
+    L.place3d_set_profiling.argtypes = [vp, i32]
+    L.place3d_num_stages.argtypes = []
+    L.place3d_stage_name.argtypes = [i32]
+    L.place3d_stage_name.restype = C.c_char_p
+    L.place3d_stage_times.argtypes = [vp, vp, vp, vp, i32]
+    L.place3d_launches_per_eval.argtypes = [vp]
+    L.place3d_last_error.argtypes = [vp]
+    L.place3d_last_error.restype = C.c_char_p
+    L.place3d_destroy.argtypes = [vp]
+    L.place3d_destroy.restype = None
+    _lib = L
+    return L
+
+
+def alpha(dx, dz, beta=10.0, w_hbt=1.0, rh_top=0.8, rh_bot=1.0) -> float:
+    """HBT penalty factor of Sec. V-A (computed by the library)."""
+    return float(load_library().place3d_alpha(dx, dz, beta, w_hbt, rh_top, rh_bot))
+
+
+def _is_torch(a):
+    return hasattr(a, "data_ptr") and hasattr(a, "is_cuda")
+
+
+def _buf(a):
+    """(pointer, dtype code, mem kind, keepalive) of a numpy array / torch tensor."""
+    if _is_torch(a):
+        import torch
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        dt = {torch.float64: F64, torch.float32: F32}.get(a.dtype)
+        if dt is None:
+            raise ValueError(f"unsupported dtype {a.dtype}")
+        return a.data_ptr(), dt, (MEM_DEVICE if a.is_cuda else MEM_HOST), a
+    a = np.ascontiguousarray(a)
+    dt = {np.dtype(np.float64): F64, np.dtype(np.float32): F32}.get(a.dtype)
+    if dt is None:
+        raise ValueError(f"unsupported dtype {a.dtype}")
+    return a.ctypes.data, dt, MEM_HOST, a
+
+
+class Place3D:
+    """One placement problem on one GPU (owns a place3d handle)."""
+
+    def __init__(self, prob: dict, precision: str | int = "fp32", device: int = 0, stream=None,
+                 alpha: float | None = None, flags: int = 0):
+        L = load_library()
+        self._L = L
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        self.precision = precision
+        keep = {}
+
+        def arr(k, dt):
+            a = np.ascontiguousarray(prob[k], dtype=dt)
+            keep[k] = a
+            return a.ctypes.data
+
+        n = int(prob["n_inst"])
+        zf = prob.get("z_fixed")
+        p = _Problem()
+        p.n_inst = n
+        p.is_macro = arr("is_macro", np.uint8)
+        p.z_fixed = arr("z_fixed", np.uint8) if zf is not None else None
+        p.w_bot, p.h_bot = arr("w_bot", np.float64), arr("h_bot", np.float64)
+        p.w_top, p.h_top = arr("w_top", np.float64), arr("h_top", np.float64)
+        p.n_net, p.n_pin = int(prob["n_net"]), int(prob["n_pin"])
+        p.net_start, p.pin_inst = arr("net_start", np.int32), arr("pin_inst", np.int32)
+        p.pin_off_bot_x, p.pin_off_bot_y = arr("off_bx", np.float64), arr("off_by", np.float64)
+        p.pin_off_top_x, p.pin_off_top_y = arr("off_tx", np.float64), arr("off_ty", np.float64)
+        p.xl, p.yl, p.xh, p.yh = (float(prob[k]) for k in ("xl", "yl", "xh", "yh"))
+        p.nx, p.ny, p.nz = int(prob["nx"]), int(prob["ny"]), int(prob["nz"])
+        p.gamma, p.gamma_z = float(prob["gamma"]), float(prob.get("gamma_z", 0.0))
+        if alpha is None and p.nx > 0 and p.ny > 0:
+            wb = (p.xh - p.xl) / p.nx
+            hb = (p.yh - p.yl) / p.ny
+            dz = p.nz * 0.5 * (wb + hb)
+            alpha = L.place3d_alpha(p.xh - p.xl, dz, prob.get("beta", 10.0), prob.get("w_hbt", 1.0),
+                                    prob.get("rh_top", 0.8), prob.get("rh_bot", 1.0))
+        p.alpha = float(alpha) if alpha is not None else 0.0
+        p.lam = float(prob["lam"])
+        p.precision = int(precision)
+        p.flags = int(flags)
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        h = C.c_void_p()
+        rc = L.place3d_create(C.byref(p), int(device), C.c_void_p(stream or 0), C.byref(h))
+        if rc != 0:
+            raise Place3DError(rc, L.place3d_last_error(None).decode())
+        self._h = h
+        self.n = n
+        self.alpha = p.alpha
+        self.nb = p.nx * p.ny * p.nz
+        self.shape = (p.nz, p.ny, p.nx)
+        self._keep = None
+
+    # -- plumbing --
+    def _check(self, rc):
+        if rc != 0:
+            raise Place3DError(rc, self._L.place3d_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.place3d_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- API --
+    def geometry(self) -> dict:
+        out = np.zeros(6)
+        self._check(self._L.place3d_geometry(self._h, out.ctypes.data))
+        return dict(wb=out[0], hb=out[1], db=out[2], dx=out[3], dy=out[4], dz=out[5])
+
+    def set_positions(self, x, y, z):
+        bx, by, bz = _buf(x), _buf(y), _buf(z)
+        if len({bx[1], by[1], bz[1]}) != 1 or len({bx[2], by[2], bz[2]}) != 1:
+            raise ValueError("x, y, z must share dtype and memory kind")
+        self._keep = (bx[3], by[3], bz[3])
+        self._check(self._L.place3d_set_positions(self._h, bx[0], by[0], bz[0], bx[1], bx[2]))
+
+    def eval(self, gx=None, gy=None, gz=None, sync: bool = True):
+        """Enqueue one evaluation; with sync return the scalars as a dict."""
+        res = Result()
+        if gx is None:
+            ptrs, dt, mem = (None, None, None), F64, MEM_HOST
+        else:
+            b = [_buf(a) for a in (gx, gy, gz)]
+            ptrs, dt, mem = tuple(v[0] for v in b), b[0][1], b[0][2]
+            self._gkeep = [v[3] for v in b]
+        self._check(self._L.place3d_eval_objective_and_grad(
+            self._h, C.byref(res) if sync else None, *ptrs, dt, mem))
+        return res.as_dict() if sync else None
+
+    def get_result(self) -> dict:
+        res = Result()
+        self._check(self._L.place3d_get_result(self._h, C.byref(res)))
+        return res.as_dict()
+
+    def copy_map(self, which: int) -> np.ndarray:
+        if which == MAP_RHO_FIXED:
+            out = np.zeros(self.shape, np.int64)
+        else:
+            out = np.zeros(self.shape, np.float64 if self.precision == FP64 else np.float32)
+        self._check(self._L.place3d_copy_map(self._h, which, out.ctypes.data, MEM_HOST))
+        return out
+
+    def wl_parts(self) -> dict:
+        g = [np.zeros(self.n) for _ in range(4)]
+        self._check(self._L.place3d_copy_wl_parts(self._h, *[a.ctypes.data for a in g]))
+        return dict(gx=g[0], gy=g[1], gfd=g[2], gwaz=g[3])
+
+    def set_profiling(self, on: bool):
+        self._check(self._L.place3d_set_profiling(self._h, int(bool(on))))
+
+    def stage_times(self, reset: bool = False) -> dict:
+        ns = self._L.place3d_num_stages()
+        ms = np.zeros(ns)
+        ln = np.zeros(ns, np.int64)
+        ev = np.zeros(1, np.int64)
+        self._check(self._L.place3d_stage_times(self._h, ms.ctypes.data, ln.ctypes.data, ev.ctypes.data,
+                                                int(reset)))
+        names = [self._L.place3d_stage_name(k).decode() for k in range(ns)]
+        return dict(evals=int(ev[0]), stages={nm: (float(ms[k]), int(ln[k])) for k, nm in enumerate(names)})
+
+    def launches_per_eval(self) -> int:
+        return int(self._L.place3d_launches_per_eval(self._h))

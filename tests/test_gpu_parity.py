@@ -1,0 +1,162 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle on the same
+seeded inputs.  Bars: bit-exact fixed-point density map; FP64 path within
+1e-9 relative; FP32 paths within 2e-5 relative on the objective and 1e-4
+relative on the gradient L2 norm."""
+import numpy as np
+import pytest
+
+from gpu_harness import Q, rel_l2, rel_max, run_gpu, run_oracle
+from helpers import dz_of, problem
+from paper_2403_09070_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-9
+
+
+def _check_fp64(prob, x, y, z, maps=True):
+    g = run_gpu(prob, x, y, z, "fp64", maps=maps)
+    o, r = run_oracle(prob, x, y, z, g["alpha"], density_mode=1)
+    if maps:
+        q = o.density_fixed(x, y, z, use_float=False)
+        assert np.array_equal(g["q"], q), "fixed-point density map differs"
+        pe = o.poisson(q * Q)
+        for k in ("ex", "ey", "ez"):
+            assert rel_max(g[k], pe[k]) < TOL64, k
+        w = o.wirelength(x, y, z)
+        for k in ("gx", "gy", "gwaz", "gfd"):
+            assert rel_max(g["wl"][k], w[k]) < TOL64, k
+    res = g["res"]
+    for k, kr in (("obj", "obj"), ("wl_bi", "wl_bi"), ("wl_z", "wl_z"), ("energy", "energy"),
+                  ("hpwl_d2d", "hpwl_d2d"), ("g_scale", "g_scale"), ("s_x", "Sx"), ("s_y", "Sy"),
+                  ("s_z", "Sz")):
+        assert res[k] == pytest.approx(r[kr], rel=TOL64, abs=1e-300), k
+    assert res["n_cross"] == r["n_cross"]
+    for k in ("gx", "gy", "gz"):
+        assert rel_max(g[k], r[k]) < TOL64, k
+    return g, r
+
+
+def _check_fp32(prob, x, y, z, precision="fp32"):
+    x32, y32, z32 = (np.asarray(a, np.float32).astype(np.float64) for a in (x, y, z))
+    g = run_gpu(prob, x32, y32, z32, precision)
+    o, r = run_oracle(prob, x32, y32, z32, g["alpha"], density_mode=0)
+    q = o.density_fixed(x32, y32, z32, use_float=True)
+    assert np.array_equal(g["q"], q), "fixed-point density map (float contract) differs"
+    res = g["res"]
+    assert res["obj"] == pytest.approx(r["obj"], rel=2e-5)
+    assert res["n_cross"] == r["n_cross"]
+    for k in ("gx", "gy", "gz"):
+        assert rel_l2(g[k], r[k]) < 1e-4, (k, rel_l2(g[k], r[k]))
+    return g, r
+
+
+@pytest.mark.parametrize("positions,origin", [("uniform", (0.0, 0.0)), ("center", (0.0, 0.0)),
+                                              ("uniform", (137.0, -42.5))])
+def test_fp64_cells_2k(positions, origin):
+    p = synth.make_problem("cells_2k", positions=positions, origin=origin)
+    _check_fp64(p, p["x"], p["y"], p["z"])
+
+
+@pytest.mark.parametrize("positions", ["uniform", "center"])
+def test_fp32_cells_2k(positions):
+    p = synth.make_problem("cells_2k", positions=positions)
+    _check_fp32(p, p["x"], p["y"], p["z"])
+
+
+def test_fp64_cells_200k():
+    p = synth.make_problem("cells_200k")
+    _check_fp64(p, p["x"], p["y"], p["z"])
+
+
+def test_fp32_cells_200k():
+    p = synth.make_problem("cells_200k")
+    _check_fp32(p, p["x"], p["y"], p["z"])
+
+
+# ---------------- edge cases ----------------
+
+def _edge(kind):
+    rng = np.random.default_rng(hash(kind) % 2 ** 32)
+    die = (3.0, -7.0, 3.0 + 74.0, -7.0 + 46.0)
+    grid = (37, 23, 3)
+    n = 120
+    sizes = [(float(rng.integers(1, 9)), 1.0, 0.0, 0.0) for _ in range(n)]
+    sizes = [(w, h, 0.8 * w, 0.8 * h) for (w, h, _, _) in sizes]
+    macros = []
+    nets = [list(rng.choice(n, size=int(rng.integers(2, 9)), replace=False)) for _ in range(150)]
+    zf = []
+    if kind in ("default", "outside", "zmid", "zfixed", "hifanout"):
+        sizes += [(12.0, 9.0, 9.6, 7.2), (6.0, 6.0, 4.8, 4.8)]
+        macros = [n, n + 1]
+        nets += [[n, 3, 5, 7], [n + 1, n, 11]]
+    if kind == "nonets":
+        nets = []
+    if kind == "hifanout":
+        nets += [list(rng.choice(n, size=100, replace=False)),
+                 list(range(n)) + [n, n + 1],  # 122 pins
+                 [4], [9, 10]]
+        grid = (40, 24, 2)
+    if kind == "single":
+        sizes, nets, macros = sizes[:1], [], []
+    if kind == "nz1":
+        grid = (16, 16, 1)
+    if kind == "zfixed":
+        zf = list(range(0, n, 5))
+    ni = len(sizes)
+    P_ = sum(len(e) for e in nets)
+    off = np.zeros((P_, 4))
+    off[:, 0] = rng.uniform(-0.5, 0.5, P_)
+    off[:, 1] = rng.uniform(-0.5, 0.5, P_)
+    off[:, 2] = 0.8 * off[:, 0]
+    off[:, 3] = 0.8 * off[:, 1]
+    p = problem(sizes, nets=nets, offsets=off, die=die, grid=grid, macros=macros, z_fixed=zf,
+                gamma=4.0 * 74.0 / grid[0])
+    dz = dz_of(p)
+    x = rng.uniform(die[0] + 5, die[2] - 5, ni)
+    y = rng.uniform(die[1] + 5, die[3] - 5, ni)
+    z = rng.uniform(dz / 4, 3 * dz / 4, ni)
+    if kind == "alltop":
+        z[:] = 0.75 * dz
+    if kind == "allbottom":
+        z[:] = 0.25 * dz
+    if kind == "zmid":
+        z[::3] = dz / 2
+    if kind == "outside":
+        x[:10] = die[0] - 1.0
+        x[10:20] = die[2] + 0.5
+        x[n] = die[0] + 1.0  # macro hanging out of the region
+    return p, x, y, z
+
+
+EDGE = ["default", "nonets", "single", "alltop", "allbottom", "zmid", "outside", "hifanout", "nz1",
+        "zfixed"]
+
+
+@pytest.mark.parametrize("kind", EDGE)
+def test_fp64_edge_cases(kind):
+    p, x, y, z = _edge(kind)
+    _check_fp64(p, x, y, z)
+
+
+@pytest.mark.parametrize("kind", EDGE)
+def test_fp32_edge_cases(kind):
+    p, x, y, z = _edge(kind)
+    _check_fp32(p, x, y, z)
+
+
+def test_positions_from_device_tensors_and_device_gradients():
+    """Device (torch CUDA) positions and gradients give the host results."""
+    torch = pytest.importorskip("torch")
+    from paper_2403_09070_gb300 import place3d as P
+    p = synth.make_problem("cells_2k")
+    ref = run_gpu(p, p["x"], p["y"], p["z"], "fp64", maps=False)
+    with P.Place3D(p, precision="fp64", stream=torch.cuda.current_stream()) as h:
+        xs = [torch.tensor(p[k], device="cuda", dtype=torch.float64) for k in ("x", "y", "z")]
+        h.set_positions(*xs)
+        gs = [torch.empty(p["n_inst"], device="cuda", dtype=torch.float64) for _ in range(3)]
+        r = h.eval(*gs)
+    # the wirelength sums use floating-point atomics: equal up to summation order
+    assert r["obj"] == pytest.approx(ref["res"]["obj"], rel=1e-12)
+    for t, k in zip(gs, ("gx", "gy", "gz")):
+        np.testing.assert_allclose(t.cpu().numpy(), ref[k], rtol=1e-12, atol=1e-12 * np.abs(ref[k]).max())
