@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Throughput of one evaluation of the 3D placement objective and gradient.
+
+A step is one full pass of the hot path over the synthetic workload: pack the
+device-resident positions, then the bistratal WA wirelength with the FD depth
+gradient, the fixed-point density scatter (cells + Theorem 1 macros), the
+spectral Poisson solve, the field gather and the final gradient assembly.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank evaluates its own
+copy of the workload (independent placement problems, weak scaling, no
+collective on the data path); the timed region is bracketed by barriers and
+the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grad evals/s (WA WL + 3D density fwd+bwd) at 1M cells; % of HBM roofline"
+UNIT = "grad evals/s"
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="place3d", choices=["place3d", "reference"])
+    ap.add_argument("--workload", default="cells_1m")
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32_tc", "fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- algorithmic bytes / flops
+def algorithmic(prob: dict, precision: str) -> dict:
+    """Per-evaluation algorithmic traffic of each stage: every input read once,
+    every output written once (FP32 fast path; FP64 doubles the real terms)."""
+    n, P, E = prob["n_inst"], prob["n_pin"], prob["n_net"]
+    B = prob["nx"] * prob["ny"] * prob["nz"]
+    r = 8 if precision == "fp64" else 4
+    s = r // 4
+    wl = 12 * s * n + (4 + 16 * s) * P + 4 * E + 12 * s * n
+    scatter = 28 * s * n + 8 * B
+    fwd = 2 * 2 * r * B
+    zst = 3 * r * B
+    inv = 11 * r * B
+    gather = 28 * s * n + 12 * s * B + 12 * s * n
+    prefix = 16 * B + r * B
+    flops_pass = 2 * B * max(prob["nx"], prob["ny"])  # one x- or y-axis product
+    tc_mult = 3 if precision == "fp32_tc" else 1        # split hi/lo: 3 products
+    return dict(
+        bytes=dict(wirelength=wl, scatter=scatter, prefix_densify=prefix, transform_fwd=fwd,
+                   zstage=zst, transform_inv=inv, final=gather, macro_gather=0, norms=16 * s * n, prep=28 * s * n),
+        flops=dict(transform_fwd=2 * flops_pass * tc_mult, transform_inv=6 * flops_pass * tc_mult))
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi samples (SM clock, throttle reasons) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.p = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.t.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle legs (CPU)
+def _oracle_worker(args):
+    """Generate the workload once, then time `count` full oracle evaluations."""
+    workload, count = args
+    from oracle import Oracle
+    from paper_2403_09070_gb300 import synth
+    p = synth.make_problem(workload)
+    o = Oracle(p)
+    times = []
+    for _ in range(count):
+        t0 = time.perf_counter()
+        o.eval(p["x"], p["y"], p["z"], density_mode=0, fd_mode=1)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def oracle_throughput(workload: str, evals: int, workers: int) -> dict:
+    """`evals` full oracle evaluations split over `workers` spawned processes
+    (each evaluation single-threaded).  evals/s = evals / the largest
+    per-worker evaluation time (problem generation is not timed)."""
+    import oracle
+    oracle.build()
+    workers = max(1, min(workers, evals))
+    chunks = [evals // workers + (1 if k < evals % workers else 0) for k in range(workers)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        per = pool.map(_oracle_worker, [(workload, c) for c in chunks])
+    busiest = max(sum(t) for t in per)
+    flat = [t for ts in per for t in ts]
+    return {"value": evals / busiest, "busiest_s": busiest, "per_eval_s": float(np.median(flat)),
+            "evals": evals, "workers": workers}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(a):
+    """The oracle (FP64 CPU, as it stands) on the host cores, same workload,
+    metric and unit.  Each step is one full evaluation; steps run
+    concurrently on the host cores (one per worker process)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cores = host_cores()
+    oracle_throughput(a.workload, min(cores, max(a.warmup, 1)), min(cores, max(a.warmup, 1)))  # warm-up
+    r = oracle_throughput(a.workload, a.steps, cores)
+    ms = 1000.0 / r["value"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": _workload_desc(a.workload), "impl": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": r["value"], "unit": UNIT, "cores": r["workers"], "kind": "oracle",
+                         "sample": f"{a.steps} full evaluations of {a.workload} split over {r['workers']} "
+                                   f"worker processes (single-threaded each); median "
+                                   f"{r['per_eval_s']:.2f} s per evaluation"},
+        "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _workload_desc(name):
+    from paper_2403_09070_gb300 import synth
+    w = synth.WORKLOADS[name]
+    return (f"{name}: {w.n_std} std cells + {w.n_macro} macros, {w.n_net} nets (+{w.n_hifanout} high-fanout), "
+            f"{w.die:g}x{w.die:g} dies, {w.nx}x{w.ny}x{w.nz} bins")
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cores = host_cores()
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        # before the first GPU call (the pool is spawned, but keep it simple)
+        cpu = oracle_throughput(a.workload, min(cores, 16), min(cores, 16))  # one evaluation per core
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2403_09070_gb300 import place3d as P
+    from paper_2403_09070_gb300 import synth
+
+    prob = synth.make_problem(a.workload)
+    n = prob["n_inst"]
+    precision = a.precision
+    if precision == "auto":
+        precision = "fp32_tc"
+        try:
+            P.Place3D(synth.make_problem("cells_2k", n_std=64, n_net=16) | {"nx": 128, "ny": 128},
+                      precision="fp32_tc", device=local).close()
+        except P.Place3DError:
+            precision = "fp32"
+    stream = torch.cuda.current_stream()
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    h = P.Place3D(prob, precision=precision, device=local, stream=stream)
+    xyz = [torch.tensor(prob[k], device="cuda", dtype=dt) for k in ("x", "y", "z")]
+    grads = [torch.empty(n, device="cuda", dtype=dt) for _ in range(3)]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def step():
+        h.set_positions(*xyz)
+        h.eval(*grads, sync=False)
+
+    for _ in range(a.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    h.stage_times(reset=True)
+    h.set_profiling(True)
+    clk = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    for k in range(a.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the event pair)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    h.set_profiling(False)
+    res = h.get_result()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = h.stage_times(reset=True)
+    launches = h.launches_per_eval() + 1  # + the position-packing kernel
+    value = world * a.steps / (total_ms / 1000.0)
+
+    # roofline of the dominant stage (per-stage CUDA events on the launching stream)
+    alg = algorithmic(prob, precision)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    evals = max(st["evals"], 1)
+    stages = {}
+    for name, (ms, nl) in st["stages"].items():
+        if nl == 0:
+            continue
+        t_eval = ms / evals
+        b = alg["bytes"].get(name, 0)
+        stages[name] = {"ms_per_eval": t_eval, "launches_per_eval": nl / evals,
+                        "alg_bytes": b, "gbs": b / (t_eval * 1e6) if t_eval > 0 and b else None}
+        if name in alg["flops"]:
+            stages[name]["tflops"] = alg["flops"][name] / (t_eval * 1e9) if t_eval > 0 else None
+    dom = max(stages, key=lambda k: stages[k]["ms_per_eval"])
+    prof_traffic = _profiled_traffic(dom, a.workload, precision)
+    if dom in ("transform_fwd", "transform_inv") and precision == "fp32_tc":
+        ach = stages[dom]["tflops"]
+        roof = {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
+                "frac": ach / bf16_peak, "traffic": prof_traffic, "peak_source": "measured (bf16 sustained)"}
+    else:
+        ach = stages[dom]["gbs"]
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak if ach else None, "traffic": prof_traffic,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
+
+    # end to end through the C ABI with pinned host buffers
+    hx = [torch.tensor(prob[k], dtype=dt).pin_memory() for k in ("x", "y", "z")]
+    hg = [torch.empty(n, dtype=dt).pin_memory() for _ in range(3)]
+    for _ in range(2):
+        h.set_positions(*hx)
+        h.eval(*hg, sync=True)
+    e2e_s = 0.0
+    for _ in range(a.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.set_positions(*hx)
+        r2 = h.eval(*hg, sync=True)
+        e2e_s += time.perf_counter() - t0
+    e2e_ms = e2e_s * 1000.0
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h.close()
+
+    fp64 = None
+    if not a.no_fp64 and precision != "fp64" and rank == 0 and world == 1:
+        fp64 = _fp64_plain(prob, torch, P)
+
+    if rank == 0:
+        esz = 8 if precision == "fp64" else 4
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32_tc": "f32 (transforms bf16x3 split on tensor cores, f64 scalars)",
+                      "fp32": "f32 (f64 scalars)", "fp64": "f64"}[precision],
+            "data": "synthetic",
+            "config": {"workload": _workload_desc(a.workload), "precision": precision,
+                       "n_inst": n, "n_pin": prob["n_pin"], "n_net": prob["n_net"],
+                       "l2": "flushed between timed steps (256 MiB write, outside the step's event pair)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": world * a.steps / (e2e_ms / 1000.0), "unit": UNIT,
+                    "h2d_bytes_per_step": 3 * n * esz, "d2h_bytes_per_step": 3 * n * esz + 80},
+            "gpu_launches": launches * a.steps,
+            "roofline": roof,
+            "stages": stages,
+            "clocks": clocks,
+            "objective": res["obj"],
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": cpu["workers"], "kind": "oracle",
+                                    "sample": f"{cpu['evals']} full evaluations of {a.workload} on "
+                                              f"{cpu['workers']} worker processes, one single-threaded "
+                                              f"evaluation each; median {cpu['per_eval_s']:.2f} s per evaluation"}
+        if fp64 is not None:
+            line["fp64_plain"] = fp64
+            line["speedup_vs_fp64_plain"] = value / fp64["value"]
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def _fp64_plain(prob, torch, P, steps=5, warmup=2):
+    """The plain FP64 GPU path on the same workload (context for the fast path)."""
+    n = prob["n_inst"]
+    h = P.Place3D(prob, precision="fp64", stream=torch.cuda.current_stream())
+    xyz = [torch.tensor(prob[k], device="cuda", dtype=torch.float64) for k in ("x", "y", "z")]
+    g = [torch.empty(n, device="cuda", dtype=torch.float64) for _ in range(3)]
+    for _ in range(warmup):
+        h.set_positions(*xyz)
+        h.eval(*g, sync=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        h.set_positions(*xyz)
+        h.eval(*g, sync=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    h.close()
+    return {"value": 1000.0 / ms, "unit": UNIT, "ms_per_step": ms, "steps": steps}
+
+
+def _profiled_traffic(stage, workload, precision):
+    """DRAM bytes per evaluation of a stage from the committed ncu summary of
+    the current kernels, if one exists (profiles/traffic.json), else None."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        return t[workload][precision][stage]
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+if __name__ == "__main__":
+    sys.exit(main())
