@@ -56,7 +56,9 @@ class Result(C.Structure):
 EXPORTS = ("place3d_create", "place3d_geometry", "place3d_alpha", "place3d_set_positions",
            "place3d_eval_objective_and_grad", "place3d_get_result", "place3d_copy_map",
            "place3d_copy_wl_parts", "place3d_set_profiling", "place3d_num_stages", "place3d_stage_name",
-           "place3d_stage_times", "place3d_launches_per_eval", "place3d_last_error", "place3d_destroy")
+           "place3d_stage_times", "place3d_launches_per_eval", "place3d_last_error", "place3d_destroy",
+           "place3d_density_map_noalloc")
+NOALLOC_MAX_BINS = 262144
 
 _lib = None
 
@@ -96,6 +98,7 @@ def load_library(build_if_missing: bool = True):
     L.place3d_last_error.restype = C.c_char_p
     L.place3d_destroy.argtypes = [vp]
     L.place3d_destroy.restype = None
+    L.place3d_density_map_noalloc.argtypes = [i32] + [vp] * 8 + [d] * 4 + [i32] * 3 + [vp, vp]
     _lib = L
     return L
 
@@ -262,3 +265,24 @@ class Place3D:
 
     def launches_per_eval(self) -> int:
         return int(self._L.place3d_launches_per_eval(self._h))
+
+
+def density_map_noalloc(x, y, z, w_bot, h_bot, w_top, h_top, is_macro, region, grid, rho, stream=None):
+    """Allocation-free fixed-point density map (place3d_density_map_noalloc).
+
+    All arrays are CUDA tensors on the current device (float64, is_macro
+    uint8); rho ([nz, ny, nx] float64) is written on `stream` (asynchronous).
+    For callers that cannot allocate device memory at this point; the
+    library's scratch for it is a fixed array shared by all calls on a
+    device, so calls must not overlap on the GPU."""
+    L = load_library()
+    n = int(x.numel())
+    xl, yl, xh, yh = (float(v) for v in region)
+    nx, ny, nz = (int(v) for v in grid)
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    rc = L.place3d_density_map_noalloc(n, *[t.data_ptr() for t in (x, y, z, w_bot, h_bot, w_top, h_top,
+                                                                     is_macro)],
+                                       xl, yl, xh, yh, nx, ny, nz, rho.data_ptr(), C.c_void_p(stream or 0))
+    if rc != 0:
+        raise Place3DError(rc, "place3d_density_map_noalloc failed")
