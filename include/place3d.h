@@ -43,6 +43,7 @@ extern "C" {
 #define PLACE3D_ERR_OUT_OF_RANGE (-3) /* value outside its domain (checks) */
 #define PLACE3D_ERR_CUDA (-4)        /* a CUDA runtime call failed */
 #define PLACE3D_ERR_OOM (-5)         /* device allocation failed */
+#define PLACE3D_ERR_TIMEOUT (-6)     /* a bounded device-side wait gave up */
 #define PLACE3D_ERR_UNSUPPORTED (-7) /* mode not available on this device */
 
 /* ---- precision modes (place3d_problem.precision) ---- */
@@ -227,6 +228,20 @@ int place3d_density_map_noalloc(int n_inst, const double *x, const double *y,
                                 double xl, double yl, double xh, double yh,
                                 int nx, int ny, int nz, double *rho,
                                 void *cuda_stream);
+
+/*
+ * Self-test of the tensor-core product used by PLACE3D_FP32_TC: out[b][n][m]
+ * = sum_k A[b][m][k] W[n][k] with both operands split into BF16 hi/lo planes
+ * and FP32 accumulation (the split-precision form of the per-axis transforms
+ * of eqs. density-coef .. possion-sol-force).  A: [batches][M][K], W: [N][K],
+ * out: [batches][N][M], all HOST FP32 row-major; M a multiple of 128, N and K
+ * multiples of 64.  Runs on the current device (sm_103 only) and
+ * synchronises it.  *wait_error (may be NULL) receives the kernel's error
+ * code (0 = none; 1..3 = a bounded mbarrier wait expired).  Errors:
+ * INVALID_ARG, UNSUPPORTED (not an sm_103 device), CUDA, TIMEOUT.
+ */
+int place3d_tc_selftest(int M, int N, int K, int batches, const float *A,
+                        const float *W, float *out, int *wait_error);
 
 /* Last error message of the handle, or of the calling thread when h is NULL
  * (creation errors).  Never NULL. */

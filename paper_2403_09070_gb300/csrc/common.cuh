@@ -1,5 +1,6 @@
 // Shared device helpers of the place3d kernels (sm_103a).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -94,6 +95,23 @@ __device__ __forceinline__ void block_sum_atomic(double (&v)[NV], double *dst) {
     }
   }
 }
+
+// Map writers: plain values, or an FP32 value split into two BF16 planes
+// (hi = bf16(v), lo = bf16(v - hi); lo plane `plane` elements after hi) for
+// the tensor-core products.
+template <typename T> struct OutPlain {
+  T *p;
+  __device__ __forceinline__ void put(size_t i, T v) const { p[i] = v; }
+};
+struct OutSplit {
+  __nv_bfloat16 *hi;
+  long long plane;
+  __device__ __forceinline__ void put(size_t i, float v) const {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    hi[i + plane] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+};
 
 // Indices of the device scalar accumulators.
 enum Scalar {

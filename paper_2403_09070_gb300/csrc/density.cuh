@@ -216,16 +216,16 @@ __global__ void __launch_bounds__(1024) k_scan_cols(int nx, int ny, TA *a) {
 // ---- density -> transform input: z prefix of the macro map + cell map ----
 // rho[z][y][x] = (q[z][y][x] + sum_{z' <= z} A[z'][y][x]) * 2^-36.
 // A may be NULL (no macros).  One thread per (y, x) column.
-template <typename T>
+template <typename T, typename Out>
 __global__ void __launch_bounds__(256) k_densify(int nxy, int nz, const long long *__restrict__ q,
-                                                 const long long *__restrict__ A, T *__restrict__ rho) {
+                                                 const long long *__restrict__ A, Out rho) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nxy) return;
   long long acc = 0;
   for (int z = 0; z < nz; ++z) {
     const size_t id = (size_t)z * nxy + t;
     if (A) acc += A[id];
-    rho[id] = (T)(q[id] + acc) * (T)(1.0 / kFixedScale);
+    rho.put(id, (T)(q[id] + acc) * (T)(1.0 / kFixedScale));
   }
 }
 

@@ -43,7 +43,7 @@ const char *kStageNames[ST_COUNT] = {"prep",         "scatter",    "prefix_densi
 
 struct Bucket {
   int first, count;  // net range in the reordered CSR
-  int kind;          // 0..5 group kernels, 6 block kernel
+  int kind;          // 7: 2 lanes, 0..5: 4..32 lanes x 1..4 pins, 6: block kernel
 };
 
 struct StageEv {
@@ -259,8 +259,18 @@ template <typename T> void run_transforms(place3d_handle *h, cudaStream_t s) {
   }
   {
     StageScope sc(h, ST_ZSTAGE, s);
-    k_zstage<T><<<grid_for(pl, 256), 256, 0, s>>>(h->zc, as<T>(h->t2), as<T>(h->czpsi), as<T>(h->szpsi),
-                                                   h->scal + S_ESUM);
+    const int g = grid_for(pl, 256);
+    const T *t2 = as<T>(h->t2);
+    const OutPlain<T> cz{as<T>(h->czpsi)}, sz{as<T>(h->szpsi)};
+    double *es = h->scal + S_ESUM;
+    if (nz <= 2)
+      k_zstage<T, 2><<<g, 256, 0, s>>>(h->zc, t2, cz, sz, es);
+    else if (nz <= 4)
+      k_zstage<T, 4><<<g, 256, 0, s>>>(h->zc, t2, cz, sz, es);
+    else if (nz <= 8)
+      k_zstage<T, 8><<<g, 256, 0, s>>>(h->zc, t2, cz, sz, es);
+    else
+      k_zstage<T, 16><<<g, 256, 0, s>>>(h->zc, t2, cz, sz, es);
     count_launch(h, ST_ZSTAGE);
   }
   {
@@ -316,9 +326,10 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     V4<T> *acc = as<V4<T>>(h->acc);
     const V4<T> *pos = as<V4<T>>(h->pos), *off = as<V4<T>>(h->off);
     for (const Bucket &b : h->buckets) {
-      const int G = b.kind == 0 ? 4 : b.kind == 1 ? 8 : b.kind == 2 ? 16 : 32;
+      const int G = b.kind == 7 ? 2 : b.kind == 0 ? 4 : b.kind == 1 ? 8 : b.kind == 2 ? 16 : 32;
       const int blocks = grid_for((long long)b.count * G, 256);
       switch (b.kind) {
+        case 7: k_wl_group<T, 2, 1><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
         case 0: k_wl_group<T, 4, 1><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
         case 1: k_wl_group<T, 8, 1><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
         case 2: k_wl_group<T, 16, 1><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
@@ -364,8 +375,8 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     if (h->tc) {
       p3d_tc::densify(h->tc, s, h->nx * h->ny, h->nz, h->q, h->nm > 0 ? h->corner : nullptr);
     } else {
-      k_densify<T><<<grid_for((long long)h->nx * h->ny, 256), 256, 0, s>>>(h->nx * h->ny, h->nz, h->q,
-                                                                           h->nm > 0 ? h->corner : nullptr, as<T>(h->rho));
+      k_densify<T><<<grid_for((long long)h->nx * h->ny, 256), 256, 0, s>>>(
+          h->nx * h->ny, h->nz, h->q, h->nm > 0 ? h->corner : nullptr, OutPlain<T>{as<T>(h->rho)});
     }
     count_launch(h, ST_PREFIX);
   }
@@ -600,15 +611,15 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
   };
 
   // net-degree buckets: nets of degree < 2 are dropped (they contribute 0)
-  std::vector<std::vector<int>> cls(7);
+  std::vector<std::vector<int>> cls(8);
   for (int e = 0; e < p->n_net; ++e) {
     const int d = p->net_start[e + 1] - p->net_start[e];
     if (d < 2) continue;
-    const int k = d <= 4 ? 0 : d <= 8 ? 1 : d <= 16 ? 2 : d <= 32 ? 3 : d <= 64 ? 4 : d <= 128 ? 5 : 6;
+    const int k = d == 2 ? 7 : d <= 4 ? 0 : d <= 8 ? 1 : d <= 16 ? 2 : d <= 32 ? 3 : d <= 64 ? 4 : d <= 128 ? 5 : 6;
     cls[k].push_back(e);
   }
   std::vector<int> order, new_start(1, 0);
-  for (int k = 0; k < 7; ++k) {
+  for (int k : {7, 0, 1, 2, 3, 4, 5, 6}) {
     if (cls[k].empty()) continue;
     h->buckets.push_back({(int)order.size(), (int)cls[k].size(), k});
     for (int e : cls[k]) {
@@ -782,6 +793,8 @@ int place3d_eval_objective_and_grad(place3d_handle *h, place3d_result *out, void
   h->have_result = true;
   if (out || (ng && mem == PLACE3D_MEM_HOST)) {
     P3D_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->tc && p3d_tc::error_code(h->tc) != 0)
+      return fail(h, PLACE3D_ERR_TIMEOUT, "a tensor-core transform wait expired");
     if (out) fill_result(h, out);
   }
   return PLACE3D_OK;
@@ -792,6 +805,8 @@ int place3d_get_result(place3d_handle *h, place3d_result *out) {
   if (!h->have_result) return fail(h, PLACE3D_ERR_INVALID_ARG, "no evaluation has been enqueued");
   P3D_CUDA(h, cudaSetDevice(h->device));
   P3D_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->tc && p3d_tc::error_code(h->tc) != 0)
+    return fail(h, PLACE3D_ERR_TIMEOUT, "a tensor-core transform wait expired");
   fill_result(h, out);
   return PLACE3D_OK;
 }

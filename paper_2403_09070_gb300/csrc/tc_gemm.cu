@@ -1,16 +1,610 @@
-// Tensor-core spectral solve (placeholder until the tcgen05 kernels land).
+// Tensor-core form of the spectral solve (eqs. density-coef,
+// poisson-sol-potential, possion-sol-force) on sm_103a.
+//
+// Each axis transform is a batched product out[b][n][m] = sum_k A[b][m][k]
+// W[n][k] (W = cosine or sine matrix), computed with tcgen05.mma (kind::f16,
+// BF16 operands, FP32 accumulation in tensor memory).  FP32 accuracy is won
+// back by splitting every operand into two BF16 planes, v = hi + lo, and
+// accumulating hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding).
+// Operand tiles are staged by TMA (128-byte swizzle) through a 4-deep
+// mbarrier pipeline: one thread issues the TMA loads, one thread issues the
+// MMAs, four warps drain the accumulator from tensor memory and store it
+// transposed (the next axis becomes the contiguous one), either as FP32 or
+// again as split-BF16 planes for the next product.
+//
+// Every wait on an mbarrier is bounded by a clock budget; on expiry the CTA
+// records an error code, stops issuing work, waits (bounded) for its own TMA
+// copies, frees its tensor memory and exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/place3d.h"
+#include "common.cuh"
+#include "density.cuh"
 #include "tc_gemm.h"
+#include "transform.cuh"
 
 namespace p3d_tc {
-struct TcPlan {};
-TcPlan *create(int, int, int, int, double, double, double, void *, void *, void *, const p3d::ZStageC *,
-               std::string *why) {
-  if (why) *why = "tensor-core transforms are not built in this library";
-  return nullptr;
+using namespace p3d;
+
+constexpr int BM = 128, BN = 64, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;                    // one BF16 plane of an A tile (16 KiB)
+constexpr int W_BYTES = BN * BK * 2;                    // one BF16 plane of a W tile (8 KiB)
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * W_BYTES;  // 48 KiB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr int TMEM_COLS = BN;                           // FP32 accumulator columns
+constexpr long long kWaitCycles = 4000000000LL;         // about 2 s at 2 GHz
+
+enum { OUT_F32 = 0, OUT_SPLIT = 1 };
+enum { ERR_FULL = 1, ERR_EMPTY = 2, ERR_ACC = 3 };
+
+struct Prob {
+  void *out;          // float* (OUT_F32) or bf16* hi plane (OUT_SPLIT)
+  long long plane;    // elements from the hi plane to the lo plane
+  long long o_bstride;
+  int M, N, K, batches, tiles_m, tiles_n, kind;
+};
+
+struct Group {
+  CUtensorMap amap[3];  // A: dims {K, M, batch, plane}
+  CUtensorMap wmap[3];  // W: dims {K, N, plane}
+  Prob p[3];
+  int count;
+  int tile_start[4];
+  int *err;
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-void densify(TcPlan *, cudaStream_t, int, int, const long long *, const long long *) {}
-int forward(TcPlan *, cudaStream_t) { return 0; }
-int zstage(TcPlan *, cudaStream_t, double *) { return 0; }
-int inverse(TcPlan *, cudaStream_t) { return 0; }
-void destroy(TcPlan *) {}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_4d(const CUtensorMap *map, uint32_t dst, uint32_t bar, int c0, int c1,
+                                            int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(const CUtensorMap *map, uint32_t dst, uint32_t bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, BF16 x BF16 -> FP32.
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
+// rows of 128 B, 8-row groups 1024 B apart (stride byte offset), descriptor
+// version 1, swizzle mode 2 (128 B).  The tile base is 1024-byte aligned; a
+// step of 16 K-elements inside the swizzle row advances the start by 32 B.
+__device__ __forceinline__ uint64_t desc_k_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: D FP32, A and B BF16, both K-major, M = BM, N = BN.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                             int *err, int code) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      atomicExch(err, code);
+      return false;
+    }
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------ kernel
+__global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Group g) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2 * STAGES + 1];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  int tile = blockIdx.x, pi = 0;
+  while (pi + 1 < g.count && tile >= g.tile_start[pi + 1]) ++pi;
+  const Prob &P = g.p[pi];
+  tile -= g.tile_start[pi];
+  const int per_b = P.tiles_m * P.tiles_n;
+  const int b = tile / per_b, r = tile - (tile / per_b) * per_b;
+  const int m0 = (r % P.tiles_m) * BM, n0 = (r / P.tiles_m) * BN;
+  const int nk = P.K / BK;
+
+  const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[STAGES]), accf = smem_u32(&bars[2 * STAGES]);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(accf, 1);
+    abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(smem_u32(&tmem_slot), TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  volatile int *abort_p = &abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer ----
+      const CUtensorMap *am = &g.amap[pi], *wm = &g.wmap[pi];
+      int issued = 0;
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES, round = kb / STAGES;
+        if (kb >= STAGES && !wait_bounded(empty0 + 8 * s, (round - 1) & 1, abort_p, g.err, ERR_EMPTY)) break;
+        const uint32_t st = smem_u32(smem + s * STAGE_BYTES), fb = full0 + 8 * s;
+        mbar_expect_tx(fb, STAGE_BYTES);
+        tma_load_4d(am, st, fb, kb * BK, m0, b, 0);
+        tma_load_4d(am, st + A_BYTES, fb, kb * BK, m0, b, 1);
+        tma_load_3d(wm, st + 2 * A_BYTES, fb, kb * BK, n0, 0);
+        tma_load_3d(wm, st + 2 * A_BYTES + W_BYTES, fb, kb * BK, n0, 1);
+        issued = kb + 1;
+      }
+      // every armed stage's last copy must have landed before the CTA exits
+      for (int s = 0; s < STAGES && s < issued; ++s) {
+        const int last = s + ((issued - 1 - s) / STAGES) * STAGES;
+        const long long t0 = clock64();
+        while (!mbar_try_wait(full0 + 8 * s, (last / STAGES) & 1) && clock64() - t0 < kWaitCycles) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES, round = kb / STAGES;
+        if (!wait_bounded(full0 + 8 * s, round & 1, abort_p, g.err, ERR_FULL)) break;
+        tc_fence_after();
+        const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES), a_lo = a_hi + A_BYTES;
+        const uint32_t w_hi = a_hi + 2 * A_BYTES, w_lo = w_hi + W_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint64_t dah = desc_k_sw128(a_hi + kk * 32), dal = desc_k_sw128(a_lo + kk * 32);
+          const uint64_t dwh = desc_k_sw128(w_hi + kk * 32), dwl = desc_k_sw128(w_lo + kk * 32);
+          mma_bf16(tmem, dah, dwh, kIdesc, (kb | kk) != 0);
+          mma_bf16(tmem, dah, dwl, kIdesc, 1u);
+          mma_bf16(tmem, dal, dwh, kIdesc, 1u);
+        }
+        mma_commit(empty0 + 8 * s);  // frees the stage once these MMAs have read it
+      }
+      mma_commit(accf);  // accumulator complete (also after an abort, so nobody waits forever)
+    }
+  } else {
+    // ---- epilogue: TMEM -> registers -> global, transposed ----
+    const bool ok = wait_bounded(accf, 0, abort_p, g.err, ERR_ACC);
+    tc_fence_after();
+    const int q = warp & 3;  // this warp's TMEM lane quarter
+    const int m = m0 + q * 32 + lane;
+    const long long base = (long long)b * P.o_bstride + m;
+#pragma unroll
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t v[16];
+      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+      if (!ok || *abort_p) continue;
+      if (P.kind == OUT_F32) {
+        float *o = static_cast<float *>(P.out);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) o[base + (long long)(n0 + c0 + j) * P.M] = __uint_as_float(v[j]);
+      } else {
+        __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(P.out);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float f = __uint_as_float(v[j]);
+          const __nv_bfloat16 h = __float2bfloat16_rn(f);
+          const long long id = base + (long long)(n0 + c0 + j) * P.M;
+          o[id] = h;
+          o[id + P.plane] = __float2bfloat16_rn(f - __bfloat162float(h));
+        }
+      }
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn(std::string *why) {
+  static EncodeTiledFn fn = nullptr;
+  if (fn) return fn;
+  void *p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !p) {
+    if (why) *why = "cuTensorMapEncodeTiled is not available from the driver";
+    return nullptr;
+  }
+  fn = reinterpret_cast<EncodeTiledFn>(p);
+  return fn;
+}
+
+// A operand: BF16 planes [plane][batch][M][K] with the given strides (elements).
+static bool map_a(CUtensorMap *m, const void *base, int K, int M, int batches, long long bstride,
+                  long long plane, std::string *why) {
+  EncodeTiledFn f = encode_fn(why);
+  if (!f) return false;
+  cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)M, (cuuint64_t)batches, 2};
+  cuuint64_t strides[3] = {(cuuint64_t)K * 2, (cuuint64_t)bstride * 2, (cuuint64_t)plane * 2};
+  cuuint32_t box[4] = {BK, BM, 1, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides, box, es,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    if (why) *why = "cuTensorMapEncodeTiled failed for an A operand (code " + std::to_string((int)r) + ")";
+    return false;
+  }
+  return true;
+}
+
+// W operand: BF16 planes [plane][N][K].
+static bool map_w(CUtensorMap *m, const void *base, int K, int N, long long plane, std::string *why) {
+  EncodeTiledFn f = encode_fn(why);
+  if (!f) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)N, 2};
+  cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)plane * 2};
+  cuuint32_t box[3] = {BK, BN, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, es,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    if (why) *why = "cuTensorMapEncodeTiled failed for a W operand (code " + std::to_string((int)r) + ")";
+    return false;
+  }
+  return true;
+}
+
+// One product of a group: A planes (base, batch stride, plane stride), W
+// planes (base, plane stride), output.
+struct ProbSpec {
+  const __nv_bfloat16 *A;
+  long long a_bstride, a_plane;
+  const __nv_bfloat16 *W;
+  long long w_plane;
+  void *out;
+  long long o_bstride, o_plane;
+  int kind, batches, M, N, K;
+};
+
+static bool make_group(Group *g, std::initializer_list<ProbSpec> specs, int *err, std::string *why) {
+  std::memset(g, 0, sizeof(Group));
+  g->err = err;
+  int tiles = 0;
+  for (const ProbSpec &s : specs) {
+    if (s.M % BM || s.N % BN || s.K % BK) {
+      if (why) *why = "product sizes must be multiples of 128 (M) and 64 (N, K)";
+      return false;
+    }
+    const int i = g->count;
+    if (!map_a(&g->amap[i], s.A, s.K, s.M, s.batches, s.a_bstride, s.a_plane, why)) return false;
+    if (!map_w(&g->wmap[i], s.W, s.K, s.N, s.w_plane, why)) return false;
+    Prob &p = g->p[i];
+    p.out = s.out;
+    p.plane = s.o_plane;
+    p.o_bstride = s.o_bstride;
+    p.M = s.M;
+    p.N = s.N;
+    p.K = s.K;
+    p.batches = s.batches;
+    p.tiles_m = s.M / BM;
+    p.tiles_n = s.N / BN;
+    p.kind = s.kind;
+    g->tile_start[i] = tiles;
+    tiles += s.batches * p.tiles_m * p.tiles_n;
+    g->count++;
+  }
+  g->tile_start[g->count] = tiles;
+  return true;
+}
+
+static int group_tiles(const Group &g) { return g.tile_start[g.count]; }
+
+static void launch(const Group &g, cudaStream_t s) {
+  k_tc_gemm<<<group_tiles(g), 192, SMEM_BYTES, s>>>(g);
+}
+
+// Round-to-nearest-even FP32 -> BF16 on the host.
+static uint16_t host_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+static float host_f32(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+// Split v into hi/lo planes: dst[i] = bf16(v), dst[plane + i] = bf16(v - hi).
+static void host_split(const std::vector<double> &v, std::vector<uint16_t> &dst) {
+  dst.resize(2 * v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    const uint16_t h = host_bf16((float)v[i]);
+    dst[i] = h;
+    dst[v.size() + i] = host_bf16((float)(v[i] - (double)host_f32(h)));
+  }
+}
+
+struct TcPlan {
+  int nx = 0, ny = 0, nz = 0;
+  size_t nb = 0;
+  __nv_bfloat16 *rho = nullptr, *t1 = nullptr, *cz = nullptr, *sz = nullptr, *xinv = nullptr, *x2 = nullptr;
+  float *t2 = nullptr;
+  __nv_bfloat16 *Wfx = nullptr, *Wfy = nullptr, *Wbx = nullptr, *Wcy = nullptr, *Wsy = nullptr;
+  const ZStageC *zc = nullptr;
+  int *err = nullptr;
+  Group g_fx, g_fy, g_ix, g_iy;
+};
+
+static void free_plan(TcPlan *p) {
+  void *bufs[] = {p->rho, p->t1, p->cz, p->sz, p->xinv, p->x2, p->t2, p->Wfx, p->Wfy, p->Wbx, p->Wcy, p->Wsy, p->err};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  delete p;
+}
+
+template <typename T> static bool dev_alloc(T **p, size_t elems, std::string *why) {
+  if (cudaMalloc(reinterpret_cast<void **>(p), elems * sizeof(T)) != cudaSuccess) {
+    if (why) *why = "device allocation failed";
+    return false;
+  }
+  return true;
+}
+
+static bool upload_split(__nv_bfloat16 **dst, const std::vector<double> &v, std::string *why) {
+  std::vector<uint16_t> h;
+  host_split(v, h);
+  if (!dev_alloc(dst, h.size(), why)) return false;
+  return cudaMemcpy(*dst, h.data(), h.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+TcPlan *create(int device, int nx, int ny, int nz, double dx, double dy, double dz, void *ex, void *ey, void *ez,
+               const ZStageC *zc, std::string *why) {
+  (void)dz;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess || prop.major != 10 || prop.minor != 3) {
+    if (why) *why = "the tensor-core path is built for sm_103 (GB300) devices";
+    return nullptr;
+  }
+  if (nx % 128 || ny % 128) {
+    if (why) *why = "N_x and N_y must be multiples of 128";
+    return nullptr;
+  }
+  if (cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess) {
+    if (why) *why = "cannot reserve shared memory for the tensor-core kernel";
+    return nullptr;
+  }
+  TcPlan *p = new TcPlan();
+  p->nx = nx;
+  p->ny = ny;
+  p->nz = nz;
+  p->nb = (size_t)nx * ny * nz;
+  p->zc = zc;
+  const size_t nb = p->nb;
+  bool ok = dev_alloc(&p->rho, 2 * nb, why) && dev_alloc(&p->t1, 2 * nb, why) && dev_alloc(&p->cz, 2 * nb, why) &&
+            dev_alloc(&p->sz, 2 * nb, why) && dev_alloc(&p->xinv, 4 * nb, why) && dev_alloc(&p->x2, 2 * nb, why) &&
+            dev_alloc(&p->t2, nb, why) && dev_alloc(&p->err, 1, why);
+  if (ok) ok = cudaMemset(p->err, 0, sizeof(int)) == cudaSuccess;
+  // trig matrices (rows = output index n, K-contiguous), split into BF16 planes
+  const double pi = 3.14159265358979323846;
+  auto fwd = [&](int n) {
+    std::vector<double> m((size_t)n * n);
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) m[(size_t)j * n + i] = std::cos(pi * j * (i + 0.5) / n);
+    return m;
+  };
+  auto inv = [&](int n, double d, bool sine) {
+    std::vector<double> m((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        const double arg = pi * j * (i + 0.5) / n;
+        m[(size_t)i * n + j] = sine ? (j * pi / d) * std::sin(arg) : std::cos(arg);
+      }
+    return m;
+  };
+  if (ok) {
+    std::vector<double> bx = inv(nx, dx, true), cx = inv(nx, dx, false);
+    bx.insert(bx.end(), cx.begin(), cx.end());  // [S_x; C_x], 2 nx rows
+    ok = upload_split(&p->Wfx, fwd(nx), why) && upload_split(&p->Wfy, fwd(ny), why) &&
+         upload_split(&p->Wbx, bx, why) && upload_split(&p->Wcy, inv(ny, dy, false), why) &&
+         upload_split(&p->Wsy, inv(ny, dy, true), why);
+  }
+  const long long pl = (long long)nx * ny, snb = (long long)nb;
+  const long long wx = (long long)nx * nx, wy = (long long)ny * ny;
+  if (ok)  // x forward: rho[z][y][x] -> t1[z][j][y] (split)
+    ok = make_group(&p->g_fx, {{p->rho, pl, snb, p->Wfx, wx, p->t1, pl, snb, OUT_SPLIT, nz, ny, nx, nx}}, p->err, why);
+  if (ok)  // y forward: t1[z][j][y] -> t2[z][k][j] (FP32, for the z stage)
+    ok = make_group(&p->g_fy, {{p->t1, pl, snb, p->Wfy, wy, p->t2, pl, 0, OUT_F32, nz, nx, ny, ny}}, p->err, why);
+  if (ok)  // x inverse: [S_x; C_x] Czpsi -> xinv[z][2nx][ny], C_x Szpsi -> x2[z][nx][ny]
+    ok = make_group(&p->g_ix,
+                    {{p->cz, pl, snb, p->Wbx, 2 * wx, p->xinv, 2 * pl, 2 * snb, OUT_SPLIT, nz, ny, 2 * nx, nx},
+                     {p->sz, pl, snb, p->Wbx + wx, 2 * wx, p->x2, pl, snb, OUT_SPLIT, nz, ny, nx, nx}},
+                    p->err, why);
+  if (ok)  // y inverse: E_x = C_y (S_x C_z psi), E_y = S_y (C_x C_z psi), E_z = C_y (C_x S_z psi)
+    ok = make_group(&p->g_iy,
+                    {{p->xinv, 2 * pl, 2 * snb, p->Wcy, wy, ex, pl, 0, OUT_F32, nz, nx, ny, ny},
+                     {p->xinv + pl, 2 * pl, 2 * snb, p->Wsy, wy, ey, pl, 0, OUT_F32, nz, nx, ny, ny},
+                     {p->x2, pl, snb, p->Wcy, wy, ez, pl, 0, OUT_F32, nz, nx, ny, ny}},
+                    p->err, why);
+  if (!ok) {
+    free_plan(p);
+    return nullptr;
+  }
+  return p;
+}
+
+void densify(TcPlan *p, cudaStream_t s, int nxy, int nz, const long long *q, const long long *corner) {
+  k_densify<float><<<(nxy + 255) / 256, 256, 0, s>>>(nxy, nz, q, corner, OutSplit{p->rho, (long long)p->nb});
+}
+
+int forward(TcPlan *p, cudaStream_t s) {
+  launch(p->g_fx, s);
+  launch(p->g_fy, s);
+  return 2;
+}
+
+int zstage(TcPlan *p, cudaStream_t s, double *esum) {
+  const int pl = p->nx * p->ny;
+  const int g = (pl + 255) / 256;
+  const OutSplit cz{p->cz, (long long)p->nb}, sz{p->sz, (long long)p->nb};
+  if (p->nz <= 2)
+    k_zstage<float, 2><<<g, 256, 0, s>>>(p->zc, p->t2, cz, sz, esum);
+  else if (p->nz <= 4)
+    k_zstage<float, 4><<<g, 256, 0, s>>>(p->zc, p->t2, cz, sz, esum);
+  else if (p->nz <= 8)
+    k_zstage<float, 8><<<g, 256, 0, s>>>(p->zc, p->t2, cz, sz, esum);
+  else
+    k_zstage<float, 16><<<g, 256, 0, s>>>(p->zc, p->t2, cz, sz, esum);
+  return 1;
+}
+
+int inverse(TcPlan *p, cudaStream_t s) {
+  launch(p->g_ix, s);
+  launch(p->g_iy, s);
+  return 2;
+}
+
+int error_code(TcPlan *p) {
+  int e = 0;
+  if (cudaMemcpy(&e, p->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  return e;
+}
+
+void destroy(TcPlan *p) {
+  if (p) free_plan(p);
+}
+
 }  // namespace p3d_tc
+
+// Self-test of one product through the tensor cores: A [batches][M][K] and
+// W [N][K] (host FP32, row-major) -> out [batches][N][M] (host FP32).
+extern "C" int place3d_tc_selftest(int M, int N, int K, int batches, const float *A, const float *W, float *out,
+                                   int *wait_error) {
+  using namespace p3d_tc;
+  if (M <= 0 || N <= 0 || K <= 0 || batches <= 0 || !A || !W || !out) return PLACE3D_ERR_INVALID_ARG;
+  if (M % BM || N % BN || K % BK) return PLACE3D_ERR_INVALID_ARG;
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess ||
+      prop.major != 10 || prop.minor != 3)
+    return PLACE3D_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess)
+    return PLACE3D_ERR_CUDA;
+  const size_t na = (size_t)batches * M * K, nw = (size_t)N * K, no = (size_t)batches * N * M;
+  std::vector<double> av(A, A + na), wv(W, W + nw);
+  std::string why;
+  __nv_bfloat16 *da = nullptr, *dw = nullptr;
+  float *dout = nullptr;
+  int *err = nullptr;
+  int rc = PLACE3D_ERR_CUDA;
+  Group g;
+  if (upload_split(&da, av, &why) && upload_split(&dw, wv, &why) && dev_alloc(&dout, no, &why) &&
+      dev_alloc(&err, 1, &why) && cudaMemset(err, 0, sizeof(int)) == cudaSuccess &&
+      cudaMemset(dout, 0, no * sizeof(float)) == cudaSuccess &&
+      make_group(&g, {{da, (long long)M * K, (long long)na, dw, (long long)nw, dout, (long long)N * M, 0, OUT_F32,
+                       batches, M, N, K}},
+                 err, &why)) {
+    launch(g, 0);
+    if (cudaDeviceSynchronize() == cudaSuccess &&
+        cudaMemcpy(out, dout, no * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      int e = 0;
+      cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost);
+      if (wait_error) *wait_error = e;
+      rc = e ? PLACE3D_ERR_TIMEOUT : PLACE3D_OK;
+    }
+  }
+  if (da) cudaFree(da);
+  if (dw) cudaFree(dw);
+  if (dout) cudaFree(dout);
+  if (err) cudaFree(err);
+  return rc;
+}

@@ -26,6 +26,9 @@ void densify(TcPlan *p, cudaStream_t s, int nxy, int nz, const long long *q, con
 int forward(TcPlan *p, cudaStream_t s);
 int zstage(TcPlan *p, cudaStream_t s, double *esum);
 int inverse(TcPlan *p, cudaStream_t s);
+// Error code left by a bounded wait of the tensor-core kernel (0 = none);
+// synchronises with the device.
+int error_code(TcPlan *p);
 void destroy(TcPlan *p);
 
 }  // namespace p3d_tc

@@ -99,44 +99,50 @@ struct ZStageC {
 // Input T2[z][k][j] (x and y already transformed, j fastest).  For each
 // (k, j): a_l = (1/N) sum_z T2[z] cos(...), psi = c_j c_k c_l a/|w|^2 (psi_000
 // = 0), energy sum += c c c a^2/|w|^2, then Czpsi[z] = sum_l psi_l cos(...)
-// and Szpsi[z] = sum_l psi_l w_l sin(...).  One thread per (k, j).
-template <typename T>
+// and Szpsi[z] = sum_l psi_l w_l sin(...).  One thread per (k, j); the z
+// loops are unrolled to NZM >= N_z so the per-thread vectors stay in
+// registers.
+template <typename T, int NZM, typename Out>
 __global__ void __launch_bounds__(256) k_zstage(const ZStageC *__restrict__ zc, const T *__restrict__ in,
-                                                T *__restrict__ czpsi, T *__restrict__ szpsi,
-                                                double *__restrict__ esum) {
+                                                Out czpsi, Out szpsi, double *__restrict__ esum) {
   const int nx = zc->nx, ny = zc->ny, nz = zc->nz;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   double e = 0.0;
   if (t < nx * ny) {
     const int j = t % nx, k = t / nx;
     const size_t plane = (size_t)nx * ny;
-    T v[kMaxNz];
-    for (int z = 0; z < nz; ++z) v[z] = in[z * plane + t];
+    T v[NZM];
+#pragma unroll
+    for (int z = 0; z < NZM; ++z) v[z] = z < nz ? in[z * plane + t] : T(0);
     const double wj = j * zc->pi_dx, wk = k * zc->pi_dy;
     const double cjk = (j ? 2.0 : 1.0) * (k ? 2.0 : 1.0);
-    T psi[kMaxNz];
-    for (int l = 0; l < nz; ++l) {
+    T psi[NZM];
+#pragma unroll
+    for (int l = 0; l < NZM; ++l) {
       T a = 0;
-      for (int z = 0; z < nz; ++z) a += v[z] * (T)zc->cz[l * kMaxNz + z];
+#pragma unroll
+      for (int z = 0; z < NZM; ++z) a += v[z] * (T)zc->cz[l * kMaxNz + z];
       a *= (T)zc->inv_n;
       const double wl = l * zc->pi_dz;
       const double w2 = wj * wj + wk * wk + wl * wl;
-      if (j == 0 && k == 0 && l == 0) {
-        psi[l] = 0;
-      } else {
+      psi[l] = T(0);
+      if (l < nz && (j | k | l)) {
         const double cc = cjk * (l ? 2.0 : 1.0);
         psi[l] = (T)(cc / w2) * a;
         e += cc * (double)a * (double)a / w2;
       }
     }
-    for (int z = 0; z < nz; ++z) {
+#pragma unroll
+    for (int z = 0; z < NZM; ++z) {
+      if (z >= nz) break;
       T sc = 0, ss = 0;
-      for (int l = 0; l < nz; ++l) {
+#pragma unroll
+      for (int l = 0; l < NZM; ++l) {
         sc += psi[l] * (T)zc->cz[l * kMaxNz + z];
         ss += psi[l] * (T)zc->sz[l * kMaxNz + z];
       }
-      czpsi[z * plane + t] = sc;
-      szpsi[z * plane + t] = ss;
+      czpsi.put(z * plane + t, sc);
+      szpsi.put(z * plane + t, ss);
     }
   }
   double v1[1] = {e};

@@ -91,10 +91,14 @@ template <typename T> struct NetExt {
     zmn = big<T>();
   }
   __device__ __forceinline__ void add(const Pin<T> &p) {
-    const int s = p.top;
-    e[0][s].add(p.px, p.slot);
-    e[1][s].add(p.py, p.slot);
-    ntop += s;
+    if (p.top) {
+      e[0][1].add(p.px, p.slot);
+      e[1][1].add(p.py, p.slot);
+    } else {
+      e[0][0].add(p.px, p.slot);
+      e[1][0].add(p.py, p.slot);
+    }
+    ntop += p.top ? 1 : 0;
     n += 1;
     zmx = p.pz > zmx ? p.pz : zmx;
     zmn = p.pz < zmn ? p.pz : zmn;
@@ -172,26 +176,29 @@ template <typename T> struct Sums {
 template <typename T>
 __device__ __forceinline__ void pin_exps(const Pin<T> &p, const NetExt<T> &X, const WlC<T> &c,
                                          T (&ex)[6]) {
-  const int s = p.top;
-  ex[0] = r_exp((p.px - X.e[0][s].mx1) * c.inv_g);
-  ex[1] = r_exp((X.e[0][s].mn1 - p.px) * c.inv_g);
-  ex[2] = r_exp((p.py - X.e[1][s].mx1) * c.inv_g);
-  ex[3] = r_exp((X.e[1][s].mn1 - p.py) * c.inv_g);
+  const bool s = p.top;
+  const T xmx = s ? X.e[0][1].mx1 : X.e[0][0].mx1, xmn = s ? X.e[0][1].mn1 : X.e[0][0].mn1;
+  const T ymx = s ? X.e[1][1].mx1 : X.e[1][0].mx1, ymn = s ? X.e[1][1].mn1 : X.e[1][0].mn1;
+  ex[0] = r_exp((p.px - xmx) * c.inv_g);
+  ex[1] = r_exp((xmn - p.px) * c.inv_g);
+  ex[2] = r_exp((p.py - ymx) * c.inv_g);
+  ex[3] = r_exp((ymn - p.py) * c.inv_g);
   ex[4] = r_exp((p.pz - X.zmx) * c.inv_gz);
   ex[5] = r_exp((X.zmn - p.pz) * c.inv_gz);
 }
 
 template <typename T>
 __device__ __forceinline__ void sums_add(Sums<T> &S, const Pin<T> &p, const T (&ex)[6]) {
-  const int s = p.top;
-  S.v[0][s][0] += ex[0];
-  S.v[0][s][1] += p.px * ex[0];
-  S.v[0][s][2] += ex[1];
-  S.v[0][s][3] += p.px * ex[1];
-  S.v[1][s][0] += ex[2];
-  S.v[1][s][1] += p.py * ex[2];
-  S.v[1][s][2] += ex[3];
-  S.v[1][s][3] += p.py * ex[3];
+  const T v[4] = {ex[0], p.px * ex[0], ex[1], p.px * ex[1]};
+  const T w[4] = {ex[2], p.py * ex[2], ex[3], p.py * ex[3]};
+  // predicated adds into the pin's side (no dynamic indexing: stays in registers)
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    S.v[0][1][k] += p.top ? v[k] : T(0);
+    S.v[0][0][k] += p.top ? T(0) : v[k];
+    S.v[1][1][k] += p.top ? w[k] : T(0);
+    S.v[1][0][k] += p.top ? T(0) : w[k];
+  }
   S.z[0] += ex[4];
   S.z[1] += p.pz * ex[4];
   S.z[2] += ex[5];
@@ -302,27 +309,43 @@ __device__ __forceinline__ T wa_grad(T v, T ep, T SP, T M, T em, T SM, T m, T in
   return (ep / SP) * (T(1) + (v - M) * inv_g) - (em / SM) * (T(1) - (v - m) * inv_g);
 }
 
+template <typename T>
+__device__ __forceinline__ Ext<T> pick(bool s, const Ext<T> &a1, const Ext<T> &a0) {
+  Ext<T> r;
+  r.mx1 = s ? a1.mx1 : a0.mx1;
+  r.mx2 = s ? a1.mx2 : a0.mx2;
+  r.mn1 = s ? a1.mn1 : a0.mn1;
+  r.mn2 = s ? a1.mn2 : a0.mn2;
+  r.amx = s ? a1.amx : a0.amx;
+  r.amn = s ? a1.amn : a0.amn;
+  return r;
+}
+
 // Per-pin outputs (gx, gy, fd, waz) -> instance accumulators.
 template <typename T>
 __device__ __forceinline__ void pin_outputs(const Pin<T> &p, const T (&ex)[6], const NetExt<T> &X,
                                             const Sums<T> &S, const NetScal<T> &N,
                                             const WlC<T> &c, V4<T> *__restrict__ acc) {
-  const int s = p.top;
+  const bool s = p.top;
   T g[2];
   const T v[2] = {p.px, p.py};
 #pragma unroll
   for (int a = 0; a < 2; ++a) {
     const AxisNet<T> &A = N.ax[a];
-    if (A.all)
-      g[a] = wa_grad(v[a], ex[2 * a] * A.f[s], A.SP, A.M, ex[2 * a + 1] * A.h[s], A.SM, A.m, c.inv_g);
-    else
-      g[a] = wa_grad(v[a], ex[2 * a], S.v[a][s][0], A.Ms[s], ex[2 * a + 1], S.v[a][s][2], A.ms[s],
-                     c.inv_g);
+    if (A.all) {
+      const T f = s ? A.f[1] : A.f[0], h = s ? A.h[1] : A.h[0];
+      g[a] = wa_grad(v[a], ex[2 * a] * f, A.SP, A.M, ex[2 * a + 1] * h, A.SM, A.m, c.inv_g);
+    } else {
+      const T sp = s ? S.v[a][1][0] : S.v[a][0][0], sm = s ? S.v[a][1][2] : S.v[a][0][2];
+      const T Ms = s ? A.Ms[1] : A.Ms[0], ms = s ? A.ms[1] : A.ms[0];
+      g[a] = wa_grad(v[a], ex[2 * a], sp, Ms, ex[2 * a + 1], sm, ms, c.inv_g);
+    }
   }
   const T gz = wa_grad(p.pz, ex[4], N.zS1, N.zM, ex[5], N.zS2, N.zm, c.inv_gz);
   const int ns = s ? X.ntop : X.n - X.ntop, no = X.n - ns;
-  const T wm = moved_axis(X.e[0][s], X.e[0][1 - s], ns, no, p.slot, p.qx) +
-               moved_axis(X.e[1][s], X.e[1][1 - s], ns, no, p.slot, p.qy);
+  const Ext<T> ex0 = pick(s, X.e[0][1], X.e[0][0]), eo0 = pick(!s, X.e[0][1], X.e[0][0]);
+  const Ext<T> ex1 = pick(s, X.e[1][1], X.e[1][0]), eo1 = pick(!s, X.e[1][1], X.e[1][0]);
+  const T wm = moved_axis(ex0, eo0, ns, no, p.slot, p.qx) + moved_axis(ex1, eo1, ns, no, p.slot, p.qy);
   const T fd = c.fd_scale * (s ? (N.wcur - wm) : (wm - N.wcur));
   acc_add(acc + p.inst, g[0], g[1], fd, gz);
 }

@@ -22,7 +22,8 @@ F64, F32 = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
 FLAG_CHECKS = 1
 MAP_RHO_FIXED, MAP_EX, MAP_EY, MAP_EZ = 0, 1, 2, 3
-ERRORS = {-1: "INVALID_ARG", -2: "BAD_CSR", -3: "OUT_OF_RANGE", -4: "CUDA", -5: "OOM", -7: "UNSUPPORTED"}
+ERRORS = {-1: "INVALID_ARG", -2: "BAD_CSR", -3: "OUT_OF_RANGE", -4: "CUDA", -5: "OOM", -6: "TIMEOUT",
+          -7: "UNSUPPORTED"}
 
 
 class Place3DError(RuntimeError):
@@ -57,7 +58,7 @@ EXPORTS = ("place3d_create", "place3d_geometry", "place3d_alpha", "place3d_set_p
            "place3d_eval_objective_and_grad", "place3d_get_result", "place3d_copy_map",
            "place3d_copy_wl_parts", "place3d_set_profiling", "place3d_num_stages", "place3d_stage_name",
            "place3d_stage_times", "place3d_launches_per_eval", "place3d_last_error", "place3d_destroy",
-           "place3d_density_map_noalloc")
+           "place3d_density_map_noalloc", "place3d_tc_selftest")
 NOALLOC_MAX_BINS = 262144
 
 _lib = None
@@ -98,6 +99,7 @@ def load_library(build_if_missing: bool = True):
     L.place3d_last_error.restype = C.c_char_p
     L.place3d_destroy.argtypes = [vp]
     L.place3d_destroy.restype = None
+    L.place3d_tc_selftest.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp]
     L.place3d_density_map_noalloc.argtypes = [i32] + [vp] * 8 + [d] * 4 + [i32] * 3 + [vp, vp]
     _lib = L
     return L
@@ -286,3 +288,19 @@ def density_map_noalloc(x, y, z, w_bot, h_bot, w_top, h_top, is_macro, region, g
                                        xl, yl, xh, yh, nx, ny, nz, rho.data_ptr(), C.c_void_p(stream or 0))
     if rc != 0:
         raise Place3DError(rc, "place3d_density_map_noalloc failed")
+
+
+def tc_selftest(A, W):
+    """The tensor-core split-BF16 product out[b][n][m] = sum_k A[b][m][k] W[n][k]
+    (place3d_tc_selftest) on host float32 arrays; returns (out, wait_error)."""
+    L = load_library()
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    W = np.ascontiguousarray(W, dtype=np.float32)
+    batches, M, K = A.shape
+    N = W.shape[0]
+    out = np.zeros((batches, N, M), np.float32)
+    err = np.zeros(1, np.int32)
+    rc = L.place3d_tc_selftest(M, N, K, batches, A.ctypes.data, W.ctypes.data, out.ctypes.data, err.ctypes.data)
+    if rc != 0:
+        raise Place3DError(rc, f"place3d_tc_selftest failed (wait error {int(err[0])})")
+    return out, int(err[0])
