@@ -239,6 +239,9 @@ def main():
         h.set_positions(*xyz)
         h.eval(*grads, sync=False)
 
+    h.set_positions(*xyz)
+    h.autotune(3)  # per-bucket reduction forms, timed on this workload
+
     for _ in range(a.warmup):
         flush.zero_()
         step()
@@ -262,6 +265,7 @@ def main():
     clocks = clk.stop()
     h.set_profiling(False)
     res = h.get_result()
+    h_forms = h.wl_forms()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
     total_ms = float(sum(step_ms))
     if world > 1:
@@ -349,6 +353,7 @@ def main():
             "stages": stages,
             "clocks": clocks,
             "objective": res["obj"],
+            "wl_forms": h_forms,
         }
         if cpu is not None:
             line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": cpu["workers"], "kind": "oracle",

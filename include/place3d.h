@@ -53,6 +53,16 @@ extern "C" {
 
 /* ---- flags (place3d_problem.flags) ---- */
 #define PLACE3D_FLAG_CHECKS 1 /* validate positions on every set_positions */
+/* Macro field gather: by default the library picks the bin-parallel direct
+ * form when the macros cover fewer bins than twice the grid, else Theorem 1's
+ * adjoint (suffix sums of the field, 8 corners per macro, Sec. IV-A).  These
+ * flags force one form (both give the same gradient up to rounding). */
+#define PLACE3D_FLAG_MACRO_GATHER_SCAN 2
+#define PLACE3D_FLAG_MACRO_GATHER_DIRECT 4
+/* Run the wirelength path on the caller's stream after the density path
+ * instead of concurrently on a second stream (for profiling one kernel at a
+ * time). */
+#define PLACE3D_FLAG_SERIAL 8
 
 /* ---- dtype and memory kind of caller buffers ---- */
 #define PLACE3D_F64 0
@@ -151,6 +161,25 @@ int place3d_set_positions(place3d_handle *h, const void *x, const void *y,
 int place3d_eval_objective_and_grad(place3d_handle *h, place3d_result *out,
                                     void *gx, void *gy, void *gz, int dtype,
                                     int mem);
+
+/* Autotune the per-net reductions: for every net-degree bucket, time each
+ * supported (lanes per net, pins per lane) form of the wirelength kernel
+ * `repeats` times at the current positions and keep the fastest.  Call after
+ * place3d_set_positions; synchronises the device.  Results are unchanged up
+ * to floating-point summation order. */
+int place3d_autotune(place3d_handle *h, int repeats);
+
+/* The degree buckets and their chosen forms: writes up to cap entries of
+ * (largest degree, lanes per net (0 = one block per net), pins per lane) and
+ * returns the number of buckets. */
+int place3d_wl_forms(const place3d_handle *h, int32_t *dmax, int32_t *lanes,
+                     int32_t *pins, int cap);
+
+/* Force the form of one bucket (index as listed by place3d_wl_forms): lanes
+ * per net in {1,2,4,8,16,32}, pins per lane in {1,2,4} with lanes*pins at
+ * least the bucket's largest degree (the supported pairs are those the
+ * autotuner tries).  INVALID_ARG otherwise. */
+int place3d_set_wl_form(place3d_handle *h, int bucket, int lanes, int pins);
 
 /* Synchronise the handle's stream and return the scalars of the last
  * evaluation. */

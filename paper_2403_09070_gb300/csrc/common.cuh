@@ -26,7 +26,9 @@ __device__ __forceinline__ float r_ceil(float a) { return ceilf(a); }
 __device__ __forceinline__ double r_ceil(double a) { return ceil(a); }
 __device__ __forceinline__ long long r_rint(float a) { return __float2ll_rn(a); }
 __device__ __forceinline__ long long r_rint(double a) { return __double2ll_rn(a); }
-__device__ __forceinline__ float r_exp(float a) { return expf(a); }
+// FP32 mode uses the fast exponential (a few ulp near 0, where the dominant
+// WA terms are); FP64 mode the full-precision one.
+__device__ __forceinline__ float r_exp(float a) { return __expf(a); }
 __device__ __forceinline__ double r_exp(double a) { return exp(a); }
 
 template <typename T> __device__ __forceinline__ T big();
@@ -70,28 +72,29 @@ __device__ __forceinline__ void acc_add(V4<double> *p, double a, double b, doubl
   atomicAdd(&p->w, d);
 }
 
-// Block-wide sum of up to 4 doubles into global accumulators (one atomic per
-// block and value).  All threads of the block must call it.
-template <int NV>
-__device__ __forceinline__ void block_sum_atomic(double (&v)[NV], double *dst) {
+// Block-wide sum of NV values into FP64 global accumulators (one atomic per
+// block and value).  Lanes reduce in their own precision T (FP32 lanes stay
+// off the slow FP64 pipe); each warp's partial is widened to FP64 once and
+// one thread adds the block's warps in FP64.  All threads must call it.
+template <int NV, typename T>
+__device__ __forceinline__ void block_sum_atomic(T (&v)[NV], double *dst) {
   __shared__ double red[32][NV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    double s = v[k];
+    T s = v[k];
 #pragma unroll
     for (int m = 16; m; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
-    if (lane == 0) red[warp][k] = s;
+    if (lane == 0) red[warp][k] = (double)s;
   }
   __syncthreads();
-  if (warp == 0) {
+  if (threadIdx.x == 0) {
     const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      double s = lane < nw ? red[lane][k] : 0.0;
-#pragma unroll
-      for (int m = 16; m; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
-      if (lane == 0 && s != 0.0) atomicAdd(dst + k, s);
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += red[w][k];
+      if (s != 0.0) atomicAdd(dst + k, s);
     }
   }
 }

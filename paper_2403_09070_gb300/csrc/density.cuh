@@ -271,10 +271,50 @@ __global__ void k_macro_gather(int nm, const int *__restrict__ macro_ids,
     if (acc[comp] != 0.0) atomicAdd(out + m * 3 + comp, sign > 0 ? acc[comp] : -acc[comp]);
 }
 
+// ---- a10 (macros), bin-parallel direct form: grid (macros, slices) ----
+// Block (m, s) sums omega * ovx*ovy*ovz * E over every S-th (z, y) row of
+// macro m's clipped cuboid, threads striding over the rows' x bins.  Same
+// result as the suffix-sum adjoint; cost proportional to the macros' bins.
+template <typename T>
+__global__ void __launch_bounds__(256) k_macro_gather_direct(const int *__restrict__ macro_ids,
+                                                             const V4<T> *__restrict__ pos,
+                                                             const V4<T> *__restrict__ size, DensC<T> c,
+                                                             const T *__restrict__ ex, const T *__restrict__ ey,
+                                                             const T *__restrict__ ez, double *__restrict__ out) {
+  const int m = blockIdx.x, i = macro_ids[m];
+  const V4<T> p = pos[i];
+  const Box<T> b = inst_box(c, p.x, p.y, p.z, size[i], true);
+  T cl[3], chh[3];
+  int b0[3], b1[3];
+  T acc[3] = {0, 0, 0};
+  if (clip_axis(b.lo[0], b.hi[0], c.fnx, c.nx, cl[0], chh[0], b0[0], b1[0]) &&
+      clip_axis(b.lo[1], b.hi[1], c.fny, c.ny, cl[1], chh[1], b0[1], b1[1]) &&
+      clip_axis(b.lo[2], b.hi[2], c.fnz, c.nz, cl[2], chh[2], b0[2], b1[2])) {
+    const int nyr = b1[1] - b0[1] + 1, nzr = b1[2] - b0[2] + 1, nxr = b1[0] - b0[0] + 1;
+    for (int r = blockIdx.y; r < nyr * nzr; r += gridDim.y) {
+      const int j = b0[1] + r % nyr, k = b0[2] + r / nyr;
+      const T oyz = ov_axis(cl[1], chh[1], j) * ov_axis(cl[2], chh[2], k);
+      const size_t row = ((size_t)k * c.ny + j) * c.nx;
+      for (int u = threadIdx.x; u < nxr; u += blockDim.x) {
+        const int ii = b0[0] + u;
+        const T v = ov_axis(cl[0], chh[0], ii) * oyz;
+        acc[0] += v * ex[row + ii];
+        acc[1] += v * ey[row + ii];
+        acc[2] += v * ez[row + ii];
+      }
+    }
+  }
+  acc[0] *= b.om;
+  acc[1] *= b.om;
+  acc[2] *= b.om;
+  block_sum_atomic<3>(acc, out + 3 * m);
+}
+
 // Final assembly constants.
 template <typename T> struct FinalC {
   T lam, alpha, volb;
   const double *scal;  // device scalars (S_x, S_y, S_z for g)
+  T g;                 // filled per block from scal
 };
 
 __device__ __forceinline__ double g_scale_of(const double *scal) {
@@ -296,6 +336,10 @@ __global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ 
                                                const V4<T> *__restrict__ acc, FinalC<T> fc,
                                                TO *__restrict__ gx, TO *__restrict__ gy,
                                                TO *__restrict__ gz) {
+  __shared__ T g_sh;
+  if (threadIdx.x == 0) g_sh = (T)g_scale_of(fc.scal);  // one FP64 division per block
+  __syncthreads();
+  fc.g = g_sh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint8_t f = flags[i];
@@ -334,7 +378,7 @@ __global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ 
     }
   }
   const V4<T> a = acc[i];
-  const T g = (T)g_scale_of(fc.scal);
+  const T g = fc.g;
   T ozg = g * a.z + fc.alpha * a.w + fc.lam * dgz;
   if (f & 2) ozg = T(0);
   gx[i] = (TO)(a.x + fc.lam * dgx);

@@ -43,8 +43,16 @@ const char *kStageNames[ST_COUNT] = {"prep",         "scatter",    "prefix_densi
 
 struct Bucket {
   int first, count;  // net range in the reordered CSR
-  int kind;          // 7: 2 lanes, 0..5: 4..32 lanes x 1..4 pins, 6: block kernel
+  int dmax;          // largest degree in the bucket
+  int G, PPL;        // lanes per net x pins per lane (G = 0: one block per net)
 };
+
+// (lanes per net, pins per lane) forms of the group kernel; G = 1 is one
+// thread per net with no shuffles.
+// (1, 1) is the closed-form kernel of 2-pin nets.
+const int kForms[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 2}, {4, 1}, {2, 4}, {8, 1}, {4, 4},
+                         {16, 1}, {8, 4}, {32, 1}, {16, 4}, {32, 2}, {32, 4}};
+const int kNumForms = sizeof(kForms) / sizeof(kForms[0]);
 
 struct StageEv {
   cudaEvent_t a, b;
@@ -59,6 +67,7 @@ struct place3d_handle {
   cudaStream_t stream = nullptr, side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int precision = 0, flags = 0;
+  bool macro_direct = true;  // bin-parallel direct macro gather (else Theorem 1 suffix sums)
   int n = 0, nm = 0, nnet = 0, npin = 0;
   int nx = 0, ny = 0, nz = 0;
   size_t nb = 0;
@@ -245,6 +254,40 @@ void launch_gemm(place3d_handle *h, cudaStream_t s, std::initializer_list<GemmPr
   count_launch(h, stage);
 }
 
+template <typename T>
+void launch_wl(place3d_handle *h, const Bucket &b, int G, int PPL, cudaStream_t w, const WlC<T> &c) {
+  V4<T> *acc = as<V4<T>>(h->acc);
+  const V4<T> *pos = as<V4<T>>(h->pos), *off = as<V4<T>>(h->off);
+  if (G == 0) {
+    k_wl_block<T><<<b.count, 256, 0, w>>>(b.first, h->net_start, h->pin_inst, off, pos, c, acc, h->scal);
+    return;
+  }
+  if (G == 1 && PPL == 1) {  // 2-pin nets, closed form
+    k_wl_pair<T><<<grid_for(b.count, 256), 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c,
+                                                        acc, h->scal);
+    return;
+  }
+  const int blocks = grid_for((long long)b.count * G, 256);
+#define P3D_WL(GG, PP)                                                                                     \
+  if (G == GG && PPL == PP) {                                                                              \
+    k_wl_group<T, GG, PP><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, \
+                                                 acc, h->scal);                                            \
+    return;                                                                                                \
+  }
+  P3D_WL(1, 2) P3D_WL(1, 4) P3D_WL(2, 2) P3D_WL(4, 1) P3D_WL(2, 4) P3D_WL(8, 1) P3D_WL(4, 4)
+  P3D_WL(16, 1) P3D_WL(8, 4) P3D_WL(32, 1) P3D_WL(16, 4) P3D_WL(32, 2) P3D_WL(32, 4)
+#undef P3D_WL
+}
+
+template <typename T> WlC<T> wl_consts(const place3d_handle *h) {
+  WlC<T> c;
+  c.zmid = (T)(0.5 * h->dz);
+  c.inv_g = (T)(1.0 / h->gamma);
+  c.inv_gz = (T)(1.0 / (h->gamma_z > 0 ? h->gamma_z : h->gamma));
+  c.fd_scale = (T)(4.0 / h->dz);
+  return c;
+}
+
 // The spectral solve: rho -> E_x, E_y, E_z (and the energy sum).
 template <typename T> void run_transforms(place3d_handle *h, cudaStream_t s) {
   const int nx = h->nx, ny = h->ny, nz = h->nz;
@@ -307,7 +350,7 @@ void run_transforms_tc(place3d_handle *h, cudaStream_t s) {
 }
 
 template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void *gz, int dtype, int mem) {
-  cudaStream_t s = h->stream, w = h->side;
+  cudaStream_t s = h->stream, w = (h->flags & PLACE3D_FLAG_SERIAL) ? h->stream : h->side;
   const int n = h->n;
   const DensC<T> dc = dens_consts<T>(h, h->xl, h->yl);
   h->launches = 0;
@@ -318,26 +361,9 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
   {
     StageScope sc(h, ST_WIRELENGTH, w);
     P3D_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(V4<T>) * (size_t)std::max(n, 1), w));
-    WlC<T> c;
-    c.zmid = (T)(0.5 * h->dz);
-    c.inv_g = (T)(1.0 / h->gamma);
-    c.inv_gz = (T)(1.0 / (h->gamma_z > 0 ? h->gamma_z : h->gamma));
-    c.fd_scale = (T)(4.0 / h->dz);
-    V4<T> *acc = as<V4<T>>(h->acc);
-    const V4<T> *pos = as<V4<T>>(h->pos), *off = as<V4<T>>(h->off);
+    const WlC<T> c = wl_consts<T>(h);
     for (const Bucket &b : h->buckets) {
-      const int G = b.kind == 7 ? 2 : b.kind == 0 ? 4 : b.kind == 1 ? 8 : b.kind == 2 ? 16 : 32;
-      const int blocks = grid_for((long long)b.count * G, 256);
-      switch (b.kind) {
-        case 7: k_wl_group<T, 2, 1><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
-        case 0: k_wl_group<T, 4, 1><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
-        case 1: k_wl_group<T, 8, 1><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
-        case 2: k_wl_group<T, 16, 1><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
-        case 3: k_wl_group<T, 32, 1><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
-        case 4: k_wl_group<T, 32, 2><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
-        case 5: k_wl_group<T, 32, 4><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
-        default: k_wl_block<T><<<b.count, 256, 0, w>>>(b.first, h->net_start, h->pin_inst, off, pos, c, acc, h->scal); break;
-      }
+      launch_wl<T>(h, b, b.G, b.PPL, w, c);
       count_launch(h, ST_WIRELENGTH);
     }
   }
@@ -384,7 +410,13 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     run_transforms_tc(h, s);
   else
     run_transforms<T>(h, s);
-  if (h->nm > 0) {
+  if (h->nm > 0 && h->macro_direct) {
+    StageScope sc(h, ST_MACRO_GATHER, s);
+    P3D_CUDA(h, cudaMemsetAsync(h->mgrad, 0, sizeof(double) * 3 * h->nm, s));
+    k_macro_gather_direct<T><<<dim3(h->nm, 16), 256, 0, s>>>(h->macro_ids, as<V4<T>>(h->pos), as<V4<T>>(h->size),
+                                                            dc, as<T>(h->ex), as<T>(h->ey), as<T>(h->ez), h->mgrad);
+    count_launch(h, ST_MACRO_GATHER);
+  } else if (h->nm > 0) {
     StageScope sc(h, ST_MACRO_GATHER, s);
     const int rows = h->ny * h->nz;
     for (int comp = 0; comp < 3; ++comp) {
@@ -611,17 +643,23 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
   };
 
   // net-degree buckets: nets of degree < 2 are dropped (they contribute 0)
+  const int kLimits[8] = {2, 4, 8, 16, 32, 64, 128, 1 << 30};
+  // default forms (lanes, pins per lane) per bucket; place3d_autotune refines them
+  const int kDefault[8][2] = {{1, 1}, {1, 4}, {8, 1}, {16, 1}, {32, 1}, {32, 2}, {32, 4}, {0, 0}};
   std::vector<std::vector<int>> cls(8);
   for (int e = 0; e < p->n_net; ++e) {
     const int d = p->net_start[e + 1] - p->net_start[e];
     if (d < 2) continue;
-    const int k = d == 2 ? 7 : d <= 4 ? 0 : d <= 8 ? 1 : d <= 16 ? 2 : d <= 32 ? 3 : d <= 64 ? 4 : d <= 128 ? 5 : 6;
+    int k = 0;
+    while (d > kLimits[k]) ++k;
     cls[k].push_back(e);
   }
   std::vector<int> order, new_start(1, 0);
-  for (int k : {7, 0, 1, 2, 3, 4, 5, 6}) {
+  for (int k = 0; k < 8; ++k) {
     if (cls[k].empty()) continue;
-    h->buckets.push_back({(int)order.size(), (int)cls[k].size(), k});
+    int dmax = 0;
+    for (int e : cls[k]) dmax = std::max(dmax, p->net_start[e + 1] - p->net_start[e]);
+    h->buckets.push_back({(int)order.size(), (int)cls[k].size(), dmax, kDefault[k][0], kDefault[k][1]});
     for (int e : cls[k]) {
       order.push_back(e);
       new_start.push_back(new_start.back() + (p->net_start[e + 1] - p->net_start[e]));
@@ -641,6 +679,20 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
     if (p->z_fixed && p->z_fixed[i]) fl[i] |= 2;
   }
   h->nm = (int)mids.size();
+  // macro gather form: direct when the macros' bins (at their larger size) are
+  // fewer than twice the grid, Theorem 1's suffix-sum adjoint otherwise
+  {
+    double covered = 0;
+    const double wbv = (p->xh - p->xl) / p->nx, hbv = (p->yh - p->yl) / p->ny;
+    for (int i : mids) {
+      const double w = std::max(p->w_bot[i], p->w_top[i]), hh = std::max(p->h_bot[i], p->h_top[i]);
+      covered += (std::ceil(std::max(w, std::sqrt(2.0) * wbv) / wbv) + 1) *
+                 (std::ceil(std::max(hh, std::sqrt(2.0) * hbv) / hbv) + 1) * (p->nz / 2 + 2);
+    }
+    h->macro_direct = covered <= 2.0 * (double)p->nx * p->ny * p->nz;
+    if (p->flags & PLACE3D_FLAG_MACRO_GATHER_SCAN) h->macro_direct = false;
+    if (p->flags & PLACE3D_FLAG_MACRO_GATHER_DIRECT) h->macro_direct = true;
+  }
 
   // device allocation
   const size_t es = h->esz, nb = h->nb, nn = std::max(n, 1);
@@ -656,7 +708,7 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
       {(void **)&h->corner, h->nm ? 8 * nb : (size_t)8}, {&h->rho, es * nb}, {&h->t1, es * nb}, {&h->t2, es * nb},
       {&h->czpsi, es * nb}, {&h->szpsi, es * nb}, {&h->xinv, 2 * es * nb}, {&h->x2, es * nb},
       {&h->ex, es * nb}, {&h->ey, es * nb}, {&h->ez, es * nb},
-      {(void **)&h->suffix, h->nm ? 3 * 8 * nb : (size_t)8}, {(void **)&h->mgrad, (size_t)24 * std::max(h->nm, 1)},
+      {(void **)&h->suffix, h->nm && !h->macro_direct ? 3 * 8 * nb : (size_t)8}, {(void **)&h->mgrad, (size_t)24 * std::max(h->nm, 1)},
       {(void **)&h->scal, sizeof(double) * S_COUNT}, {(void **)&h->zc, sizeof(ZStageC)},
       {&h->gout, 3 * es * nn}, {(void **)&h->check_flag, sizeof(int)}};
   for (auto &a : allocs) {
@@ -691,6 +743,10 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
   zc.pi_dy = pi / h->dy;
   zc.pi_dz = pi / h->dz;
   zc.inv_n = 1.0 / (double)h->nb;
+  zc.pi_dx_f = (float)zc.pi_dx;
+  zc.pi_dy_f = (float)zc.pi_dy;
+  zc.pi_dz_f = (float)zc.pi_dz;
+  zc.inv_n_f = (float)zc.inv_n;
   for (int l = 0; l < h->nz; ++l)
     for (int z = 0; z < h->nz; ++z) {
       const double arg = pi * l * (z + 0.5) / h->nz;
@@ -872,6 +928,72 @@ int place3d_copy_wl_parts(place3d_handle *h, double *gx, double *gy, double *gfd
     if (gwaz) gwaz[i] = v[4 * i + 3];
   }
   return PLACE3D_OK;
+}
+
+int place3d_autotune(place3d_handle *h, int repeats) {
+  if (!h) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL handle");
+  P3D_CUDA(h, cudaSetDevice(h->device));
+  if (repeats < 1) repeats = 3;
+  cudaStream_t w = h->side;
+  cudaEvent_t e0, e1;
+  P3D_CUDA(h, cudaEventCreate(&e0));
+  P3D_CUDA(h, cudaEventCreate(&e1));
+  P3D_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (Bucket &b : h->buckets) {
+    if (b.G == 0) continue;  // high-fanout nets: block form only
+    float best = 1e30f;
+    int bg = b.G, bp = b.PPL;
+    for (int f = 0; f < kNumForms; ++f) {
+      const int G = kForms[f][0], PPL = kForms[f][1];
+      const bool pair = G == 1 && PPL == 1;
+      if (pair ? b.dmax != 2 : (G * PPL < b.dmax || G * PPL > 4 * std::max(b.dmax, 8))) continue;
+      for (int r = 0; r <= repeats; ++r) {  // first run warms up
+        if (r == 1) cudaEventRecord(e0, w);
+        if (h->precision == PLACE3D_FP64)
+          launch_wl<double>(h, b, G, PPL, w, wl_consts<double>(h));
+        else
+          launch_wl<float>(h, b, G, PPL, w, wl_consts<float>(h));
+      }
+      cudaEventRecord(e1, w);
+      P3D_CUDA(h, cudaEventSynchronize(e1));
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bg = G; bp = PPL; }
+    }
+    b.G = bg;
+    b.PPL = bp;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  P3D_CUDA(h, cudaGetLastError());
+  return PLACE3D_OK;
+}
+
+int place3d_set_wl_form(place3d_handle *h, int bucket, int lanes, int pins) {
+  if (!h || bucket < 0 || bucket >= (int)h->buckets.size()) return fail(h, PLACE3D_ERR_INVALID_ARG, "bad bucket");
+  Bucket &b = h->buckets[bucket];
+  if (b.G == 0) return lanes == 0 && pins == 0 ? PLACE3D_OK : fail(h, PLACE3D_ERR_INVALID_ARG, "block-form bucket");
+  for (int f = 0; f < kNumForms; ++f)
+    if (kForms[f][0] == lanes && kForms[f][1] == pins && (lanes * pins >= b.dmax || (lanes == 1 && pins == 1 && b.dmax == 2))) {
+      b.G = lanes;
+      b.PPL = pins;
+      return PLACE3D_OK;
+    }
+  return fail(h, PLACE3D_ERR_INVALID_ARG, "unsupported form for this bucket");
+}
+
+int place3d_wl_forms(const place3d_handle *h, int32_t *dmax, int32_t *lanes, int32_t *pins, int cap) {
+  if (!h) return 0;
+  int k = 0;
+  for (const Bucket &b : h->buckets) {
+    if (k < cap) {
+      if (dmax) dmax[k] = b.dmax;
+      if (lanes) lanes[k] = b.G;
+      if (pins) pins[k] = b.PPL;
+    }
+    ++k;
+  }
+  return k;
 }
 
 int place3d_set_profiling(place3d_handle *h, int on) {

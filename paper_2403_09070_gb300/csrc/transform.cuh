@@ -92,6 +92,7 @@ struct ZStageC {
   int nx, ny, nz;
   double pi_dx, pi_dy, pi_dz;  // pi/d_x, pi/d_y, pi/d_z
   double inv_n;                // 1/N
+  float pi_dx_f, pi_dy_f, pi_dz_f, inv_n_f;  // the same, rounded to FP32
   double cz[kMaxNz * kMaxNz];  // cos(pi l (z+1/2)/N_z), [l][z]
   double sz[kMaxNz * kMaxNz];  // w_l sin(pi l (z+1/2)/N_z), [l][z]
 };
@@ -102,34 +103,51 @@ struct ZStageC {
 // and Szpsi[z] = sum_l psi_l w_l sin(...).  One thread per (k, j); the z
 // loops are unrolled to NZM >= N_z so the per-thread vectors stay in
 // registers.
+template <typename T> struct ZPar;
+template <> struct ZPar<double> {
+  static __device__ __forceinline__ double pdx(const ZStageC *z) { return z->pi_dx; }
+  static __device__ __forceinline__ double pdy(const ZStageC *z) { return z->pi_dy; }
+  static __device__ __forceinline__ double pdz(const ZStageC *z) { return z->pi_dz; }
+  static __device__ __forceinline__ double invn(const ZStageC *z) { return z->inv_n; }
+};
+template <> struct ZPar<float> {
+  static __device__ __forceinline__ float pdx(const ZStageC *z) { return z->pi_dx_f; }
+  static __device__ __forceinline__ float pdy(const ZStageC *z) { return z->pi_dy_f; }
+  static __device__ __forceinline__ float pdz(const ZStageC *z) { return z->pi_dz_f; }
+  static __device__ __forceinline__ float invn(const ZStageC *z) { return z->inv_n_f; }
+};
+
+// All arithmetic in T (FP32 threads stay off the FP64 pipe); the energy sum
+// is widened to FP64 per warp.
 template <typename T, int NZM, typename Out>
 __global__ void __launch_bounds__(256) k_zstage(const ZStageC *__restrict__ zc, const T *__restrict__ in,
                                                 Out czpsi, Out szpsi, double *__restrict__ esum) {
   const int nx = zc->nx, ny = zc->ny, nz = zc->nz;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  double e = 0.0;
+  T e = 0;
   if (t < nx * ny) {
     const int j = t % nx, k = t / nx;
     const size_t plane = (size_t)nx * ny;
     T v[NZM];
 #pragma unroll
     for (int z = 0; z < NZM; ++z) v[z] = z < nz ? in[z * plane + t] : T(0);
-    const double wj = j * zc->pi_dx, wk = k * zc->pi_dy;
-    const double cjk = (j ? 2.0 : 1.0) * (k ? 2.0 : 1.0);
+    const T wj = (T)j * ZPar<T>::pdx(zc), wk = (T)k * ZPar<T>::pdy(zc);
+    const T cjk = (j ? T(2) : T(1)) * (k ? T(2) : T(1));
+    const T invn = ZPar<T>::invn(zc);
     T psi[NZM];
 #pragma unroll
     for (int l = 0; l < NZM; ++l) {
       T a = 0;
 #pragma unroll
       for (int z = 0; z < NZM; ++z) a += v[z] * (T)zc->cz[l * kMaxNz + z];
-      a *= (T)zc->inv_n;
-      const double wl = l * zc->pi_dz;
-      const double w2 = wj * wj + wk * wk + wl * wl;
+      a *= invn;
+      const T wl = (T)l * ZPar<T>::pdz(zc);
+      const T w2 = wj * wj + wk * wk + wl * wl;
       psi[l] = T(0);
       if (l < nz && (j | k | l)) {
-        const double cc = cjk * (l ? 2.0 : 1.0);
-        psi[l] = (T)(cc / w2) * a;
-        e += cc * (double)a * (double)a / w2;
+        const T cw = cjk * (l ? T(2) : T(1)) / w2;
+        psi[l] = cw * a;
+        e += cw * a * a;
       }
     }
 #pragma unroll
@@ -145,7 +163,7 @@ __global__ void __launch_bounds__(256) k_zstage(const ZStageC *__restrict__ zc, 
       szpsi.put(z * plane + t, ss);
     }
   }
-  double v1[1] = {e};
+  T v1[1] = {e};
   block_sum_atomic<1>(v1, esum);
 }
 

@@ -209,8 +209,9 @@ __device__ __forceinline__ void sums_add(Sums<T> &S, const Pin<T> &p, const T (&
 template <typename T> struct AxisNet {
   bool all;          // active branch of max{p^_e, p^_e+ + p^_e-} (ties -> whole net)
   T f[2], h[2];      // rescale of each side's + and - sums to the whole net's shifts
-  T SP, SM, M, m;    // whole-net WA sums and the two weighted averages
+  T iSP, iSM, M, m;  // reciprocals of the whole-net WA sums, the two weighted averages
   T Ms[2], ms[2];    // per side weighted averages
+  T iSs[2], iSm[2];  // per side reciprocals of the + and - sums
   T what;            // W^_e on this axis
   T wexact;          // eq. wl-obj on this axis, exact extremes
 };
@@ -225,13 +226,15 @@ __device__ __forceinline__ AxisNet<T> axis_net(int a, const NetExt<T> &X, const 
   T p[2] = {T(0), T(0)}, hp[2] = {T(0), T(0)};
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
-    r.Ms[s] = r.ms[s] = T(0);
+    r.Ms[s] = r.ms[s] = r.iSs[s] = r.iSm[s] = T(0);
     if (has[s]) {
       const Ext<T> &e = X.e[a][s];
       mxA = e.mx1 > mxA ? e.mx1 : mxA;
       mnA = e.mn1 < mnA ? e.mn1 : mnA;
-      r.Ms[s] = S.v[a][s][1] / S.v[a][s][0];
-      r.ms[s] = S.v[a][s][3] / S.v[a][s][2];
+      r.iSs[s] = T(1) / S.v[a][s][0];
+      r.iSm[s] = T(1) / S.v[a][s][2];
+      r.Ms[s] = S.v[a][s][1] * r.iSs[s];
+      r.ms[s] = S.v[a][s][3] * r.iSm[s];
       p[s] = r.Ms[s] - r.ms[s];
       hp[s] = e.mx1 - e.mn1;
     }
@@ -249,10 +252,10 @@ __device__ __forceinline__ AxisNet<T> axis_net(int a, const NetExt<T> &X, const 
       NM += S.v[a][s][3] * r.h[s];
     }
   }
-  r.SP = SP;
-  r.SM = SM;
-  r.M = NP / SP;
-  r.m = NM / SM;
+  r.iSP = T(1) / SP;
+  r.iSM = T(1) / SM;
+  r.M = NP * r.iSP;
+  r.m = NM * r.iSM;
   const T pall = r.M - r.m;
   r.all = pall >= p[0] + p[1];
   r.what = r.all ? pall : p[0] + p[1];
@@ -261,29 +264,9 @@ __device__ __forceinline__ AxisNet<T> axis_net(int a, const NetExt<T> &X, const 
   return r;
 }
 
-// W_e,x after pin `slot` leaves side s for the other side at coordinate v.
-template <typename T>
-__device__ __forceinline__ T moved_axis(const Ext<T> &es, const Ext<T> &eo, int ns, int no, int slot,
-                                        T v) {
-  const int ns1 = ns - 1;
-  T smax = 0, smin = 0, ps = 0;
-  if (ns1 > 0) {
-    smax = slot == es.amx ? es.mx2 : es.mx1;
-    smin = slot == es.amn ? es.mn2 : es.mn1;
-    ps = smax - smin;
-  }
-  const T omax = no ? (eo.mx1 > v ? eo.mx1 : v) : v;
-  const T omin = no ? (eo.mn1 < v ? eo.mn1 : v) : v;
-  const T po = omax - omin;
-  const T amax = ns1 > 0 ? (smax > omax ? smax : omax) : omax;
-  const T amin = ns1 > 0 ? (smin < omin ? smin : omin) : omin;
-  const T hall = amax - amin;
-  return hall > ps + po ? hall : ps + po;
-}
-
 template <typename T> struct NetScal {
   AxisNet<T> ax[2];
-  T zM, zm, zS1, zS2, pz;
+  T zM, zm, izS1, izS2, pz;
   T wcur;  // exact W_Bi
 };
 
@@ -293,32 +276,43 @@ __device__ __forceinline__ NetScal<T> net_scalars(const NetExt<T> &X, const Sums
   NetScal<T> r;
   r.ax[0] = axis_net(0, X, S, c);
   r.ax[1] = axis_net(1, X, S, c);
-  r.zS1 = S.z[0];
-  r.zS2 = S.z[2];
-  r.zM = S.z[1] / S.z[0];
-  r.zm = S.z[3] / S.z[2];
+  r.izS1 = T(1) / S.z[0];
+  r.izS2 = T(1) / S.z[2];
+  r.zM = S.z[1] * r.izS1;
+  r.zm = S.z[3] * r.izS2;
   r.pz = r.zM - r.zm;
   r.wcur = r.ax[0].wexact + r.ax[1].wexact;
   return r;
 }
 
 // Gradient of one WA average pair at v given the exponentials (eq.
-// wa-model-approx differentiated): (e+/S+)(1 + (v-M)/g) - (e-/S-)(1 - (v-m)/g).
+// wa-model-approx differentiated): (e+/S+)(1 + (v-M)/g) - (e-/S-)(1 - (v-m)/g),
+// with the reciprocals 1/S+ and 1/S- precomputed per net.
 template <typename T>
-__device__ __forceinline__ T wa_grad(T v, T ep, T SP, T M, T em, T SM, T m, T inv_g) {
-  return (ep / SP) * (T(1) + (v - M) * inv_g) - (em / SM) * (T(1) - (v - m) * inv_g);
+__device__ __forceinline__ T wa_grad(T v, T ep, T iSP, T M, T em, T iSM, T m, T inv_g) {
+  return (ep * iSP) * (T(1) + (v - M) * inv_g) - (em * iSM) * (T(1) - (v - m) * inv_g);
 }
 
+// W_e on one axis (eq. wl-obj) after pin `slot` leaves side s (extremes in
+// the s-side Ext, ns pins) for the other side (o-side Ext, no pins) at
+// coordinate v; the 2nd extremes replace the 1st when the pin was extreme.
 template <typename T>
-__device__ __forceinline__ Ext<T> pick(bool s, const Ext<T> &a1, const Ext<T> &a0) {
-  Ext<T> r;
-  r.mx1 = s ? a1.mx1 : a0.mx1;
-  r.mx2 = s ? a1.mx2 : a0.mx2;
-  r.mn1 = s ? a1.mn1 : a0.mn1;
-  r.mn2 = s ? a1.mn2 : a0.mn2;
-  r.amx = s ? a1.amx : a0.amx;
-  r.amn = s ? a1.amn : a0.amn;
-  return r;
+__device__ __forceinline__ T moved_sel(bool s, const Ext<T> &e1, const Ext<T> &e0, int ns, int no, int slot,
+                                       T v) {
+  const T smx1 = s ? e1.mx1 : e0.mx1, smx2 = s ? e1.mx2 : e0.mx2;
+  const T smn1 = s ? e1.mn1 : e0.mn1, smn2 = s ? e1.mn2 : e0.mn2;
+  const int samx = s ? e1.amx : e0.amx, samn = s ? e1.amn : e0.amn;
+  const T omx = s ? e0.mx1 : e1.mx1, omn = s ? e0.mn1 : e1.mn1;
+  const bool keep = ns > 1;
+  const T smax = slot == samx ? smx2 : smx1, smin = slot == samn ? smn2 : smn1;
+  const T ps = keep ? smax - smin : T(0);
+  const T omax = no ? (omx > v ? omx : v) : v;
+  const T omin = no ? (omn < v ? omn : v) : v;
+  const T po = omax - omin;
+  const T amax = keep ? (smax > omax ? smax : omax) : omax;
+  const T amin = keep ? (smin < omin ? smin : omin) : omin;
+  const T hall = amax - amin;
+  return hall > ps + po ? hall : ps + po;
 }
 
 // Per-pin outputs (gx, gy, fd, waz) -> instance accumulators.
@@ -334,20 +328,66 @@ __device__ __forceinline__ void pin_outputs(const Pin<T> &p, const T (&ex)[6], c
     const AxisNet<T> &A = N.ax[a];
     if (A.all) {
       const T f = s ? A.f[1] : A.f[0], h = s ? A.h[1] : A.h[0];
-      g[a] = wa_grad(v[a], ex[2 * a] * f, A.SP, A.M, ex[2 * a + 1] * h, A.SM, A.m, c.inv_g);
+      g[a] = wa_grad(v[a], ex[2 * a] * f, A.iSP, A.M, ex[2 * a + 1] * h, A.iSM, A.m, c.inv_g);
     } else {
-      const T sp = s ? S.v[a][1][0] : S.v[a][0][0], sm = s ? S.v[a][1][2] : S.v[a][0][2];
+      const T isp = s ? A.iSs[1] : A.iSs[0], ism = s ? A.iSm[1] : A.iSm[0];
       const T Ms = s ? A.Ms[1] : A.Ms[0], ms = s ? A.ms[1] : A.ms[0];
-      g[a] = wa_grad(v[a], ex[2 * a], sp, Ms, ex[2 * a + 1], sm, ms, c.inv_g);
+      g[a] = wa_grad(v[a], ex[2 * a], isp, Ms, ex[2 * a + 1], ism, ms, c.inv_g);
     }
   }
-  const T gz = wa_grad(p.pz, ex[4], N.zS1, N.zM, ex[5], N.zS2, N.zm, c.inv_gz);
+  const T gz = wa_grad(p.pz, ex[4], N.izS1, N.zM, ex[5], N.izS2, N.zm, c.inv_gz);
   const int ns = s ? X.ntop : X.n - X.ntop, no = X.n - ns;
-  const Ext<T> ex0 = pick(s, X.e[0][1], X.e[0][0]), eo0 = pick(!s, X.e[0][1], X.e[0][0]);
-  const Ext<T> ex1 = pick(s, X.e[1][1], X.e[1][0]), eo1 = pick(!s, X.e[1][1], X.e[1][0]);
-  const T wm = moved_axis(ex0, eo0, ns, no, p.slot, p.qx) + moved_axis(ex1, eo1, ns, no, p.slot, p.qy);
+  const T wm = moved_sel(s, X.e[0][1], X.e[0][0], ns, no, p.slot, p.qx) +
+               moved_sel(s, X.e[1][1], X.e[1][0], ns, no, p.slot, p.qy);
   const T fd = c.fd_scale * (s ? (N.wcur - wm) : (wm - N.wcur));
   acc_add(acc + p.inst, g[0], g[1], fd, gz);
+}
+
+// ---- 2-pin nets, one thread per net, closed form ----
+// For two pins every branch of eq. wl-obj collapses to the two-point WA
+// span L tanh(L / 2g) (same die: the sub-net is the net; different dies:
+// both sub-nets are single pins), with derivative tanh(u) + u sech^2(u),
+// u = L / 2g, written with e = exp(-L/g).  Moving pin a to the other die
+// changes the exact W_Bi from |a - b| to |a' - b| per axis.
+template <typename T>
+__device__ __forceinline__ T wa_pair(T va, T vb, T inv_g, T &ga) {
+  const T L = va > vb ? va - vb : vb - va;
+  const T e = r_exp(-L * inv_g);
+  const T i1e = T(1) / (T(1) + e);
+  const T th = (T(1) - e) * i1e;
+  const T der = th + T(2) * L * inv_g * e * i1e * i1e;
+  ga = va >= vb ? der : -der;
+  return L * th;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_wl_pair(int net0, int nnets, const int *__restrict__ net_start,
+                                                 const int *__restrict__ pin_inst, const V4<T> *__restrict__ off,
+                                                 const V4<T> *__restrict__ pos, WlC<T> c, V4<T> *__restrict__ acc,
+                                                 double *__restrict__ scal) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  T vals[4] = {0, 0, 0, 0};
+  if (t < nnets) {
+    const int s0 = __ldg(net_start + net0 + t);
+    const Pin<T> a = load_pin(s0, 0, pin_inst, off, pos, c), b = load_pin(s0 + 1, 1, pin_inst, off, pos, c);
+    T gx, gy, gz;
+    const T wx = wa_pair(a.px, b.px, c.inv_g, gx);
+    const T wy = wa_pair(a.py, b.py, c.inv_g, gy);
+    const T wz = wa_pair(a.pz, b.pz, c.inv_gz, gz);
+    const T dx = a.px - b.px, dy = a.py - b.py;
+    const T W = fabs(dx) + fabs(dy);
+    const T Wa = fabs(a.qx - b.px) + fabs(a.qy - b.py);  // a on the other die
+    const T Wb = fabs(a.px - b.qx) + fabs(a.py - b.qy);  // b on the other die
+    const T fa = c.fd_scale * (a.top ? W - Wa : Wa - W);
+    const T fb = c.fd_scale * (b.top ? W - Wb : Wb - W);
+    acc_add(acc + a.inst, gx, gy, fa, gz);
+    acc_add(acc + b.inst, -gx, -gy, fb, -gz);
+    vals[0] = wx + wy;
+    vals[1] = wz;
+    vals[2] = W;
+    vals[3] = a.top != b.top ? T(1) : T(0);
+  }
+  block_sum_atomic<4>(vals, scal + S_WL_BI);
 }
 
 // ---- nets of degree <= G*PPL, one group of G lanes per net ----
@@ -381,25 +421,29 @@ __global__ void __launch_bounds__(256) k_wl_group(int net0, int nnets, const int
   X.template shfl_reduce<G>();
   Sums<T> S;
   S.init();
-  T ex[PPL][6];
 #pragma unroll
   for (int r = 0; r < PPL; ++r)
     if (has[r]) {
-      pin_exps(pin[r], X, c, ex[r]);
-      sums_add(S, pin[r], ex[r]);
+      T ex[6];
+      pin_exps(pin[r], X, c, ex);
+      sums_add(S, pin[r], ex);
     }
   S.template shfl_reduce<G>();
-  double vals[4] = {0, 0, 0, 0};
+  T vals[4] = {0, 0, 0, 0};
   if (d >= 2) {
     const NetScal<T> N = net_scalars(X, S, c);
 #pragma unroll
     for (int r = 0; r < PPL; ++r)
-      if (has[r]) pin_outputs(pin[r], ex[r], X, S, N, c, acc);
+      if (has[r]) {
+        T ex[6];  // recomputed: keeping them live across the reductions costs registers
+        pin_exps(pin[r], X, c, ex);
+        pin_outputs(pin[r], ex, X, S, N, c, acc);
+      }
     if (lane == 0) {
-      vals[0] = (double)N.ax[0].what + (double)N.ax[1].what;
-      vals[1] = (double)N.pz;
-      vals[2] = (double)N.wcur;
-      vals[3] = (X.ntop > 0 && X.ntop < X.n) ? 1.0 : 0.0;
+      vals[0] = N.ax[0].what + N.ax[1].what;
+      vals[1] = N.pz;
+      vals[2] = N.wcur;
+      vals[3] = (X.ntop > 0 && X.ntop < X.n) ? T(1) : T(0);
     }
   }
   block_sum_atomic<4>(vals, scal + S_WL_BI);
@@ -462,12 +506,12 @@ __global__ void __launch_bounds__(256) k_wl_block(int net0, const int *__restric
 // ---- a9: L1 norms S_x, S_y, S_z of the wirelength gradient (FP64) ----
 template <typename T>
 __global__ void __launch_bounds__(256) k_norms(int n, const V4<T> *__restrict__ acc, double *__restrict__ scal) {
-  double v[3] = {0, 0, 0};
+  T v[3] = {0, 0, 0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const V4<T> a = acc[i];
-    v[0] += fabs((double)a.x);
-    v[1] += fabs((double)a.y);
-    v[2] += fabs((double)a.z);
+    v[0] += fabs(a.x);
+    v[1] += fabs(a.y);
+    v[2] += fabs(a.z);
   }
   block_sum_atomic<3>(v, scal + S_SX);
 }

@@ -21,6 +21,9 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_tc": FP32_TC}
 F64, F32 = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
 FLAG_CHECKS = 1
+FLAG_MACRO_GATHER_SCAN, FLAG_MACRO_GATHER_DIRECT, FLAG_SERIAL = 2, 4, 8
+WL_FORMS = ((1, 1), (1, 2), (1, 4), (2, 2), (4, 1), (2, 4), (8, 1), (4, 4), (16, 1), (8, 4), (32, 1), (16, 4), (32, 2),
+            (32, 4))
 MAP_RHO_FIXED, MAP_EX, MAP_EY, MAP_EZ = 0, 1, 2, 3
 ERRORS = {-1: "INVALID_ARG", -2: "BAD_CSR", -3: "OUT_OF_RANGE", -4: "CUDA", -5: "OOM", -6: "TIMEOUT",
           -7: "UNSUPPORTED"}
@@ -58,7 +61,8 @@ EXPORTS = ("place3d_create", "place3d_geometry", "place3d_alpha", "place3d_set_p
            "place3d_eval_objective_and_grad", "place3d_get_result", "place3d_copy_map",
            "place3d_copy_wl_parts", "place3d_set_profiling", "place3d_num_stages", "place3d_stage_name",
            "place3d_stage_times", "place3d_launches_per_eval", "place3d_last_error", "place3d_destroy",
-           "place3d_density_map_noalloc", "place3d_tc_selftest")
+           "place3d_density_map_noalloc", "place3d_tc_selftest", "place3d_autotune", "place3d_wl_forms",
+           "place3d_set_wl_form")
 NOALLOC_MAX_BINS = 262144
 
 _lib = None
@@ -99,6 +103,9 @@ def load_library(build_if_missing: bool = True):
     L.place3d_last_error.restype = C.c_char_p
     L.place3d_destroy.argtypes = [vp]
     L.place3d_destroy.restype = None
+    L.place3d_autotune.argtypes = [vp, i32]
+    L.place3d_set_wl_form.argtypes = [vp, i32, i32, i32]
+    L.place3d_wl_forms.argtypes = [vp, vp, vp, vp, i32]
     L.place3d_tc_selftest.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp]
     L.place3d_density_map_noalloc.argtypes = [i32] + [vp] * 8 + [d] * 4 + [i32] * 3 + [vp, vp]
     _lib = L
@@ -264,6 +271,20 @@ class Place3D:
                                                 int(reset)))
         names = [self._L.place3d_stage_name(k).decode() for k in range(ns)]
         return dict(evals=int(ev[0]), stages={nm: (float(ms[k]), int(ln[k])) for k, nm in enumerate(names)})
+
+    def autotune(self, repeats: int = 3):
+        """Pick the fastest reduction form per net-degree bucket (call after set_positions)."""
+        self._check(self._L.place3d_autotune(self._h, int(repeats)))
+
+    def wl_forms(self) -> list:
+        """[(largest degree, lanes per net, pins per lane)] per degree bucket."""
+        cap = 16
+        a, b, c = (np.zeros(cap, np.int32) for _ in range(3))
+        k = self._L.place3d_wl_forms(self._h, a.ctypes.data, b.ctypes.data, c.ctypes.data, cap)
+        return [(int(a[i]), int(b[i]), int(c[i])) for i in range(min(k, cap))]
+
+    def set_wl_form(self, bucket: int, lanes: int, pins: int):
+        self._check(self._L.place3d_set_wl_form(self._h, int(bucket), int(lanes), int(pins)))
 
     def launches_per_eval(self) -> int:
         return int(self._L.place3d_launches_per_eval(self._h))

@@ -27,11 +27,14 @@ def rel_l2(a, b):
     return 0.0 if num == 0 else num / max(den, 1e-300)
 
 
-def run_gpu(prob, x, y, z, precision="fp64", alpha=None, maps=True, pos_dtype=None):
+def run_gpu(prob, x, y, z, precision="fp64", alpha=None, maps=True, pos_dtype=None, flags=0,
+            autotune=False):
     """Create a handle, evaluate once, return scalars, gradient, maps."""
-    with P.Place3D(prob, precision=precision, alpha=alpha) as h:
+    with P.Place3D(prob, precision=precision, alpha=alpha, flags=flags) as h:
         dt = pos_dtype or (np.float64 if precision == "fp64" else np.float32)
         h.set_positions(np.asarray(x, dt), np.asarray(y, dt), np.asarray(z, dt))
+        if autotune:
+            h.autotune(1)
         gdt = np.float64 if precision == "fp64" else np.float32
         g = [np.zeros(prob["n_inst"], gdt) for _ in range(3)]
         r = h.eval(*g)
@@ -41,6 +44,7 @@ def run_gpu(prob, x, y, z, precision="fp64", alpha=None, maps=True, pos_dtype=No
             out["ex"], out["ey"], out["ez"] = (h.copy_map(m) for m in (P.MAP_EX, P.MAP_EY, P.MAP_EZ))
             out["wl"] = h.wl_parts()
         out["launches"] = h.launches_per_eval()
+        out["forms"] = h.wl_forms()
     return out
 
 

@@ -14,8 +14,8 @@ pytestmark = pytest.mark.gpu
 TOL64 = 1e-9
 
 
-def _check_fp64(prob, x, y, z, maps=True):
-    g = run_gpu(prob, x, y, z, "fp64", maps=maps)
+def _check_fp64(prob, x, y, z, maps=True, flags=0, autotune=False):
+    g = run_gpu(prob, x, y, z, "fp64", maps=maps, flags=flags, autotune=autotune)
     o, r = run_oracle(prob, x, y, z, g["alpha"], density_mode=1)
     if maps:
         q = o.density_fixed(x, y, z, use_float=False)
@@ -37,9 +37,9 @@ def _check_fp64(prob, x, y, z, maps=True):
     return g, r
 
 
-def _check_fp32(prob, x, y, z, precision="fp32"):
+def _check_fp32(prob, x, y, z, precision="fp32", flags=0, autotune=False):
     x32, y32, z32 = (np.asarray(a, np.float32).astype(np.float64) for a in (x, y, z))
-    g = run_gpu(prob, x32, y32, z32, precision)
+    g = run_gpu(prob, x32, y32, z32, precision, flags=flags, autotune=autotune)
     o, r = run_oracle(prob, x32, y32, z32, g["alpha"], density_mode=0)
     q = o.density_fixed(x32, y32, z32, use_float=True)
     assert np.array_equal(g["q"], q), "fixed-point density map (float contract) differs"
@@ -160,3 +160,61 @@ def test_positions_from_device_tensors_and_device_gradients():
     assert r["obj"] == pytest.approx(ref["res"]["obj"], rel=1e-12)
     for t, k in zip(gs, ("gx", "gy", "gz")):
         np.testing.assert_allclose(t.cpu().numpy(), ref[k], rtol=1e-12, atol=1e-12 * np.abs(ref[k]).max())
+
+
+@pytest.mark.parametrize("kind", ["default", "outside", "hifanout"])
+@pytest.mark.parametrize("flags", [2, 4])  # Theorem 1 suffix-sum adjoint / direct bin-parallel gather
+def test_macro_gather_forms(kind, flags):
+    p, x, y, z = _edge(kind)
+    _check_fp64(p, x, y, z, flags=flags)
+    _check_fp32(p, x, y, z, flags=flags)
+
+
+def test_macro_gather_forms_cells_2k():
+    p = synth.make_problem("cells_2k")
+    for flags in (2, 4):
+        _check_fp64(p, p["x"], p["y"], p["z"], flags=flags)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_autotuned_forms_keep_parity(precision):
+    """Every reduction form the autotuner may pick gives the oracle's result."""
+    p = synth.make_problem("cells_200k")
+    if precision == "fp64":
+        g, _ = _check_fp64(p, p["x"], p["y"], p["z"], maps=False, autotune=True)
+    else:
+        g, _ = _check_fp32(p, p["x"], p["y"], p["z"], autotune=True)
+    assert all(G * ppl >= d or (G, ppl, d) == (1, 1, 2) for d, G, ppl in g["forms"] if G > 0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_every_reduction_form(precision):
+    """Each (lanes per net, pins per lane) form of every degree bucket gives
+    the same wirelength parts as the oracle."""
+    from paper_2403_09070_gb300 import place3d as P
+    p, x, y, z = _edge("hifanout")
+    rng = np.random.default_rng(3)
+    n = p["n_inst"]
+    dt = np.float64 if precision == "fp64" else np.float32
+    xs = [np.asarray(a, dt) for a in (x, y, z)]
+    ref = None
+    with P.Place3D(p, precision=precision) as h:
+        h.set_positions(*xs)
+        forms = h.wl_forms()
+        from oracle import Oracle
+        w = Oracle(p, alpha=h.alpha).wirelength(*[a.astype(np.float64) for a in xs])
+        for bi, (dmax, G, ppl) in enumerate(forms):
+            if G == 0:
+                continue
+            for (g2, p2) in P.WL_FORMS:
+                if (g2, p2) == (1, 1) and dmax != 2:
+                    continue  # the closed-form kernel serves 2-pin nets only
+                if g2 * p2 < dmax and (g2, p2) != (1, 1):
+                    continue
+                h.set_wl_form(bi, g2, p2)
+                h.eval()
+                parts = h.wl_parts()
+                tol = 1e-9 if precision == "fp64" else 1e-4
+                for k in ("gx", "gy", "gwaz", "gfd"):
+                    assert rel_l2(parts[k], w[k]) < tol, (bi, g2, p2, k)
+            h.set_wl_form(bi, G, ppl)
