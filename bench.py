@@ -70,6 +70,24 @@ def algorithmic(prob: dict, precision: str) -> dict:
         flops=dict(transform_fwd=2 * flops_pass * tc_mult, transform_inv=6 * flops_pass * tc_mult))
 
 
+# ---------------------------------------------------------------- multi-rank helpers
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The largest value over all ranks (the slowest rank's time); identity
+    without a process group."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, total_ms: float) -> float:
+    """Whole-job evaluations per second: every rank evaluates `steps` times
+    (weak scaling), the job ends with its slowest rank."""
+    return world * steps / (total_ms / 1000.0)
+
+
 # ---------------------------------------------------------------- clocks
 class Clocks:
     """nvidia-smi samples (SM clock, throttle reasons) during the timed region."""
@@ -267,14 +285,10 @@ def main():
     res = h.get_result()
     h_forms = h.wl_forms()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(step_ms)), dist if world > 1 else None, "cuda")
     st = h.stage_times(reset=True)
     launches = h.launches_per_eval() + 1  # + the position-packing kernel
-    value = world * a.steps / (total_ms / 1000.0)
+    value = job_throughput(world, a.steps, total_ms)
 
     # roofline of the dominant stage (per-stage CUDA events on the launching stream)
     alg = algorithmic(prob, precision)
@@ -322,11 +336,7 @@ def main():
         h.set_positions(*hx)
         r2 = h.eval(*hg, sync=True)
         e2e_s += time.perf_counter() - t0
-    e2e_ms = e2e_s * 1000.0
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_s * 1000.0, dist if world > 1 else None, "cuda")
     h.close()
 
     fp64 = None
@@ -346,7 +356,7 @@ def main():
                        "n_inst": n, "n_pin": prob["n_pin"], "n_net": prob["n_net"],
                        "l2": "flushed between timed steps (256 MiB write, outside the step's event pair)",
                        "parallelism": f"replicas x{world}"},
-            "e2e": {"value": world * a.steps / (e2e_ms / 1000.0), "unit": UNIT,
+            "e2e": {"value": job_throughput(world, a.steps, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": 3 * n * esz, "d2h_bytes_per_step": 3 * n * esz + 80},
             "gpu_launches": launches * a.steps,
             "roofline": roof,
