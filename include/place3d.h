@@ -63,6 +63,12 @@ extern "C" {
  * instead of concurrently on a second stream (for profiling one kernel at a
  * time). */
 #define PLACE3D_FLAG_SERIAL 8
+/* Bucket the std cells per evaluation into 16x16-bin tiles and scatter /
+ * gather them through shared-memory windows (a counting sort by tile, then
+ * one block per chunk of a tile), instead of one thread per cell with global
+ * int64 atomics and global field gathers.  Same results; which is faster
+ * depends on the cell order and density (see the design notes). */
+#define PLACE3D_FLAG_TILES 16
 
 /* ---- dtype and memory kind of caller buffers ---- */
 #define PLACE3D_F64 0

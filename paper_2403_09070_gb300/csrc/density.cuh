@@ -386,4 +386,306 @@ __global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ 
   gz[i] = (TO)ozg;
 }
 
+// ======================= tile-bucketed scatter and gather =======================
+// Cells are bucketed per evaluation by the 16x16-bin tile (all layers) that
+// holds their centre (counting sort: block histograms give ranks, a scan
+// gives tile starts, a placement pass writes each cell's record in tile
+// order).  A work item is a chunk of one tile's cells; its block accumulates
+// contributions in a shared-memory window (tile + halo of R bins, all
+// layers) and adds the window to the map once, and later gathers the field
+// from a shared-memory copy of the same window.  Cells whose footprint
+// leaves the window use the global map directly.
+constexpr int kTile = 16;
+constexpr int kChunk = 1024;  // cells per work item
+constexpr int kCountPerThread = 8;
+
+struct TileC {
+  int ntx, nty, R, WX, WY;  // tiles per axis, halo, window size (bins)
+};
+
+template <typename T>
+__device__ __forceinline__ int tile_of(const DensC<T> &c, const TileC &tc, T X, T Y) {
+  const int ix = (int)r_floor(rn_mul(rn_sub(X, c.x0), c.iwb)), iy = (int)r_floor(rn_mul(rn_sub(Y, c.y0), c.ihb));
+  int tx = ix < 0 ? 0 : ix / kTile, ty = iy < 0 ? 0 : iy / kTile;
+  tx = tx >= tc.ntx ? tc.ntx - 1 : tx;
+  ty = ty >= tc.nty ? tc.nty - 1 : ty;
+  return ty * tc.ntx + tx;
+}
+
+// Tile of every cell and its rank inside the tile (macros get -1).  Each
+// block of 1024 threads takes 8 cells per thread, ranks them in a
+// shared-memory histogram, then reserves its range of every tile with one
+// global atomic per (block, tile).
+template <typename T>
+__global__ void __launch_bounds__(1024) k_tile_count(int n, const V4<T> *__restrict__ pos,
+                                                     const uint8_t *__restrict__ flags, DensC<T> c, TileC tc,
+                                                     int ntiles, int *__restrict__ count, int2 *__restrict__ key) {
+  extern __shared__ int hist[];
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
+  __syncthreads();
+  const int base = blockIdx.x * blockDim.x * kCountPerThread + threadIdx.x;
+  int tl[kCountPerThread], rk[kCountPerThread];
+#pragma unroll
+  for (int u = 0; u < kCountPerThread; ++u) {
+    const int i = base + u * blockDim.x;
+    tl[u] = -1;
+    rk[u] = 0;
+    if (i < n && !(flags[i] & 1)) {
+      const V4<T> p = pos[i];
+      tl[u] = tile_of(c, tc, p.x, p.y);
+      rk[u] = atomicAdd(hist + tl[u], 1);
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    const int v = hist[t];
+    hist[t] = v ? atomicAdd(count + t, v) : 0;  // this block's first rank in tile t
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < kCountPerThread; ++u) {
+    const int i = base + u * blockDim.x;
+    if (i < n) key[i] = tl[u] >= 0 ? make_int2(tl[u], hist[tl[u]] + rk[u]) : make_int2(-1, 0);
+  }
+}
+
+// Exclusive scan of the tile counts and the work-item list (one block).
+static __global__ void __launch_bounds__(1024) k_tile_scan(int ntiles, const int *__restrict__ count,
+                                                           int *__restrict__ start, int2 *__restrict__ items,
+                                                           int *__restrict__ nitems) {
+  __shared__ int s_cells[1024], s_items[1024];
+  const int t = threadIdx.x, per = (ntiles + 1023) / 1024;
+  const int t0 = t * per, t1 = min(ntiles, t0 + per);
+  int cells = 0, its = 0;
+  for (int k = t0; k < t1; ++k) {
+    cells += count[k];
+    its += (count[k] + kChunk - 1) / kChunk;
+  }
+  s_cells[t] = cells;
+  s_items[t] = its;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {  // inclusive Hillis-Steele scan
+    const int a = t >= off ? s_cells[t - off] : 0, b = t >= off ? s_items[t - off] : 0;
+    __syncthreads();
+    s_cells[t] += a;
+    s_items[t] += b;
+    __syncthreads();
+  }
+  int cs = s_cells[t] - cells, is = s_items[t] - its;
+  for (int k = t0; k < t1; ++k) {
+    start[k] = cs;
+    const int nc = (count[k] + kChunk - 1) / kChunk;
+    for (int j = 0; j < nc; ++j) items[is + j] = make_int2(k, j);
+    cs += count[k];
+    is += nc;
+  }
+  if (t == 1023) {
+    start[ntiles] = s_cells[1023];
+    *nitems = s_items[1023];
+  }
+}
+
+// Cell record in tile order: position, sizes, and the instance index with
+// its flags in the top byte.
+template <typename T> struct CellRec {
+  V4<T> pos, size;
+  int idx_flags, pad[3];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_tile_place(int n, const int2 *__restrict__ key, const int *__restrict__ start,
+                                                    const V4<T> *__restrict__ pos, const V4<T> *__restrict__ size,
+                                                    const uint8_t *__restrict__ flags, CellRec<T> *__restrict__ rec) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int2 k = key[i];
+  if (k.x < 0) return;
+  CellRec<T> r;
+  r.pos = pos[i];
+  r.size = size[i];
+  r.idx_flags = i | ((int)flags[i] << 24);
+  r.pad[0] = r.pad[1] = r.pad[2] = 0;
+  rec[start[k.x] + k.y] = r;
+}
+
+// Window of a tile: bins [x0, x0 + WX) x [y0, y0 + WY) x all layers.
+__device__ __forceinline__ void tile_window(const TileC &tc, int tile, int &x0, int &y0) {
+  x0 = (tile % tc.ntx) * kTile - tc.R;
+  y0 = (tile / tc.ntx) * kTile - tc.R;
+}
+
+// ---- a2 with shared-memory bin tiles ----
+// The window keeps each int64 count as two 32-bit words (low word, and high
+// word plus the low word's carries), so every update is a native 32-bit
+// shared-memory atomic; the window is added to the map once per item.
+template <typename T>
+__global__ void __launch_bounds__(256) k_scatter_tiles(const int2 *__restrict__ items, const int *__restrict__ nitems,
+                                                       const int *__restrict__ start,
+                                                       const CellRec<T> *__restrict__ rec, DensC<T> c, TileC tc,
+                                                       long long *__restrict__ q) {
+  extern __shared__ unsigned win32[];
+  if ((int)blockIdx.x >= *nitems) return;
+  const int2 it = items[blockIdx.x];
+  int x0, y0;
+  tile_window(tc, it.x, x0, y0);
+  const int nwin = tc.WX * tc.WY * c.nz;
+  unsigned *wlo = win32, *whi = win32 + nwin;
+  for (int k = threadIdx.x; k < 2 * nwin; k += blockDim.x) win32[k] = 0u;
+  __syncthreads();
+  const int c0 = start[it.x] + it.y * kChunk, c1 = min(start[it.x + 1], c0 + kChunk);
+  const T scale = (T)kFixedScale;
+  for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) {
+    const CellRec<T> r = rec[s];
+    const Box<T> b = inst_box(c, r.pos.x, r.pos.y, r.pos.z, r.size, false);
+    T cl[3], chh[3];
+    int b0[3], b1[3];
+    if (!clip_axis(b.lo[0], b.hi[0], c.fnx, c.nx, cl[0], chh[0], b0[0], b1[0])) continue;
+    if (!clip_axis(b.lo[1], b.hi[1], c.fny, c.ny, cl[1], chh[1], b0[1], b1[1])) continue;
+    if (!clip_axis(b.lo[2], b.hi[2], c.fnz, c.nz, cl[2], chh[2], b0[2], b1[2])) continue;
+    const bool inwin = b0[0] >= x0 && b1[0] < x0 + tc.WX && b0[1] >= y0 && b1[1] < y0 + tc.WY;
+    for (int k = b0[2]; k <= b1[2]; ++k) {
+      const T oz = ov_axis(cl[2], chh[2], k);
+      for (int j = b0[1]; j <= b1[1]; ++j) {
+        const T oy = ov_axis(cl[1], chh[1], j);
+        for (int ii = b0[0]; ii <= b1[0]; ++ii) {
+          const T ox = ov_axis(cl[0], chh[0], ii);
+          const long long v = r_rint(rn_mul(rn_mul(rn_mul(rn_mul(b.om, ox), oy), oz), scale));
+          if (inwin) {
+            const int w = (k * tc.WY + (j - y0)) * tc.WX + (ii - x0);
+            const unsigned lo = (unsigned)v, hi = (unsigned)((unsigned long long)v >> 32);
+            const unsigned old = atomicAdd(wlo + w, lo);
+            const unsigned up = hi + (old + lo < old ? 1u : 0u);  // low-word carry
+            if (up) atomicAdd(whi + w, up);
+          } else {
+            atomic_add_i64(q + ((size_t)k * c.ny + j) * c.nx + ii, v);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nwin; k += blockDim.x) {
+    const long long v = (long long)(((unsigned long long)whi[k] << 32) | (unsigned long long)wlo[k]);
+    if (!v) continue;
+    const int xx = x0 + k % tc.WX, yy = y0 + (k / tc.WX) % tc.WY, zz = k / (tc.WX * tc.WY);
+    if (xx >= 0 && xx < c.nx && yy >= 0 && yy < c.ny) atomic_add_i64(q + ((size_t)zz * c.ny + yy) * c.nx + xx, v);
+  }
+}
+
+// ---- a10 + a9 + a11 for the cells of one work item, field from shared memory ----
+// Writes (gx, gy, gz, 0) per instance into an interleaved buffer (one write
+// per cell); k_split_grad copies it to the caller's arrays.
+template <typename T>
+__global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ items, const int *__restrict__ nitems,
+                                                     const int *__restrict__ start,
+                                                     const CellRec<T> *__restrict__ rec, DensC<T> c, TileC tc,
+                                                     const T *__restrict__ ex, const T *__restrict__ ey,
+                                                     const T *__restrict__ ez, const V4<T> *__restrict__ acc,
+                                                     FinalC<T> fc, V4<T> *__restrict__ g4) {
+  extern __shared__ __align__(16) unsigned char fwin_raw[];
+  T *wx = reinterpret_cast<T *>(fwin_raw);
+  __shared__ T g_sh;
+  if ((int)blockIdx.x >= *nitems) return;
+  const int2 it = items[blockIdx.x];
+  int x0, y0;
+  tile_window(tc, it.x, x0, y0);
+  const int nwin = tc.WX * tc.WY * c.nz;
+  T *wy = wx + nwin, *wz = wy + nwin;
+  for (int k = threadIdx.x; k < nwin; k += blockDim.x) {
+    const int xx = x0 + k % tc.WX, yy = y0 + (k / tc.WX) % tc.WY, zz = k / (tc.WX * tc.WY);
+    T a = 0, b2 = 0, d2 = 0;
+    if (xx >= 0 && xx < c.nx && yy >= 0 && yy < c.ny) {
+      const size_t id = ((size_t)zz * c.ny + yy) * c.nx + xx;
+      a = ex[id];
+      b2 = ey[id];
+      d2 = ez[id];
+    }
+    wx[k] = a;
+    wy[k] = b2;
+    wz[k] = d2;
+  }
+  if (threadIdx.x == 0) g_sh = (T)g_scale_of(fc.scal);
+  __syncthreads();
+  const T g = g_sh;
+  const int c0 = start[it.x] + it.y * kChunk, c1 = min(start[it.x + 1], c0 + kChunk);
+  for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) {
+    const CellRec<T> r = rec[s];
+    const int i = r.idx_flags & 0xffffff, f = (r.idx_flags >> 24) & 0xff;
+    const V4<T> a = acc[i];
+    const Box<T> b = inst_box(c, r.pos.x, r.pos.y, r.pos.z, r.size, false);
+    T cl[3], chh[3];
+    int b0[3], b1[3];
+    T sx = 0, sy = 0, sz = 0;
+    if (clip_axis(b.lo[0], b.hi[0], c.fnx, c.nx, cl[0], chh[0], b0[0], b1[0]) &&
+        clip_axis(b.lo[1], b.hi[1], c.fny, c.ny, cl[1], chh[1], b0[1], b1[1]) &&
+        clip_axis(b.lo[2], b.hi[2], c.fnz, c.nz, cl[2], chh[2], b0[2], b1[2])) {
+      const bool inwin = b0[0] >= x0 && b1[0] < x0 + tc.WX && b0[1] >= y0 && b1[1] < y0 + tc.WY;
+      for (int k = b0[2]; k <= b1[2]; ++k) {
+        const T oz = ov_axis(cl[2], chh[2], k);
+        for (int j = b0[1]; j <= b1[1]; ++j) {
+          const T oyz = ov_axis(cl[1], chh[1], j) * oz;
+          for (int ii = b0[0]; ii <= b1[0]; ++ii) {
+            const T v = ov_axis(cl[0], chh[0], ii) * oyz;
+            if (inwin) {
+              const int w = (k * tc.WY + (j - y0)) * tc.WX + (ii - x0);
+              sx += v * wx[w];
+              sy += v * wy[w];
+              sz += v * wz[w];
+            } else {
+              const size_t id = ((size_t)k * c.ny + j) * c.nx + ii;
+              sx += v * ex[id];
+              sy += v * ey[id];
+              sz += v * ez[id];
+            }
+          }
+        }
+      }
+    }
+    const T kk = -b.om * fc.volb;
+    T ozg = g * a.z + fc.alpha * a.w + fc.lam * (kk * sz);
+    if (f & 2) ozg = T(0);
+    V4<T> o;
+    o.x = a.x + fc.lam * (kk * sx);
+    o.y = a.y + fc.lam * (kk * sy);
+    o.z = ozg;
+    o.w = T(0);
+    g4[i] = o;
+  }
+}
+
+// Final gradient of the macros (their density part comes from mgrad).
+template <typename T>
+__global__ void k_final_macros(int nm, const int *__restrict__ macro_ids, const uint8_t *__restrict__ flags,
+                               const double *__restrict__ mgrad, const V4<T> *__restrict__ acc, FinalC<T> fc,
+                               V4<T> *__restrict__ g4) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nm) return;
+  const int i = macro_ids[m];
+  const T g = (T)g_scale_of(fc.scal);
+  const T dgx = (T)(-(double)fc.volb * mgrad[m * 3 + 0]);
+  const T dgy = (T)(-(double)fc.volb * mgrad[m * 3 + 1]);
+  const T dgz = (T)(-(double)fc.volb * mgrad[m * 3 + 2]);
+  const V4<T> a = acc[i];
+  T ozg = g * a.z + fc.alpha * a.w + fc.lam * dgz;
+  if (flags[i] & 2) ozg = T(0);
+  V4<T> o;
+  o.x = a.x + fc.lam * dgx;
+  o.y = a.y + fc.lam * dgy;
+  o.z = ozg;
+  o.w = T(0);
+  g4[i] = o;
+}
+
+// Interleaved gradient -> the caller's three arrays (coalesced).
+template <typename T, typename TO>
+__global__ void __launch_bounds__(256) k_split_grad(int n, const V4<T> *__restrict__ g4, TO *__restrict__ gx,
+                                                    TO *__restrict__ gy, TO *__restrict__ gz) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const V4<T> v = g4[i];
+  gx[i] = (TO)v.x;
+  gy[i] = (TO)v.y;
+  gz[i] = (TO)v.z;
+}
+
 }  // namespace p3d

@@ -68,6 +68,15 @@ struct place3d_handle {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int precision = 0, flags = 0;
   bool macro_direct = true;  // bin-parallel direct macro gather (else Theorem 1 suffix sums)
+  // tile-bucketed scatter / gather
+  bool tiles = false;
+  TileC tcfg{};
+  int ntiles = 0, max_items = 0;
+  size_t smem_scatter = 0, smem_final = 0;
+  int2 *tkey = nullptr, *titems = nullptr;
+  void *trec = nullptr;  // CellRec<T>[n] in tile order
+  void *g4 = nullptr;    // interleaved gradient V4<T>[n]
+  int *tcount = nullptr, *tstart = nullptr, *tnitems = nullptr;
   int n = 0, nm = 0, nnet = 0, npin = 0;
   int nx = 0, ny = 0, nz = 0;
   size_t nb = 0;
@@ -349,6 +358,22 @@ void run_transforms_tc(place3d_handle *h, cudaStream_t s) {
   }
 }
 
+template <typename T, typename TO>
+void launch_final_tiles(place3d_handle *h, cudaStream_t s, const DensC<T> &dc, const FinalC<T> &fc, TO *ox, TO *oy,
+                        TO *oz) {
+  k_final_tiles<T><<<h->max_items, 256, h->smem_final, s>>>(h->titems, h->tnitems, h->tstart, as<CellRec<T>>(h->trec),
+                                                            dc, h->tcfg, as<T>(h->ex), as<T>(h->ey), as<T>(h->ez),
+                                                            as<V4<T>>(h->acc), fc, as<V4<T>>(h->g4));
+  count_launch(h, ST_FINAL);
+  if (h->nm > 0) {
+    k_final_macros<T><<<grid_for(h->nm, 128), 128, 0, s>>>(h->nm, h->macro_ids, h->flags_d, h->mgrad,
+                                                           as<V4<T>>(h->acc), fc, as<V4<T>>(h->g4));
+    count_launch(h, ST_FINAL);
+  }
+  k_split_grad<T, TO><<<grid_for(h->n, 256), 256, 0, s>>>(h->n, as<V4<T>>(h->g4), ox, oy, oz);
+  count_launch(h, ST_FINAL);
+}
+
 template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void *gz, int dtype, int mem) {
   cudaStream_t s = h->stream, w = (h->flags & PLACE3D_FLAG_SERIAL) ? h->stream : h->side;
   const int n = h->n;
@@ -377,7 +402,17 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
   {
     StageScope sc(h, ST_SCATTER, s);
     P3D_CUDA(h, cudaMemsetAsync(h->q, 0, sizeof(long long) * h->nb, s));
-    if (n > 0) {
+    if (n > 0 && h->tiles) {
+      P3D_CUDA(h, cudaMemsetAsync(h->tcount, 0, sizeof(int) * h->ntiles, s));
+      k_tile_count<T><<<grid_for(n, 1024 * kCountPerThread), 1024, sizeof(int) * h->ntiles, s>>>(
+          n, as<V4<T>>(h->pos), h->flags_d, dc, h->tcfg, h->ntiles, h->tcount, h->tkey);
+      k_tile_scan<<<1, 1024, 0, s>>>(h->ntiles, h->tcount, h->tstart, h->titems, h->tnitems);
+      k_tile_place<T><<<grid_for(n, 256), 256, 0, s>>>(n, h->tkey, h->tstart, as<V4<T>>(h->pos), as<V4<T>>(h->size),
+                                                       h->flags_d, as<CellRec<T>>(h->trec));
+      k_scatter_tiles<T><<<h->max_items, 256, h->smem_scatter, s>>>(h->titems, h->tnitems, h->tstart,
+                                                                    as<CellRec<T>>(h->trec), dc, h->tcfg, h->q);
+      for (int k = 0; k < 4; ++k) count_launch(h, ST_SCATTER);
+    } else if (n > 0) {
       k_scatter_cells<T><<<grid_for(n, 256), 256, 0, s>>>(n, as<V4<T>>(h->pos), as<V4<T>>(h->size), h->flags_d,
                                                           dc, h->q);
       count_launch(h, ST_SCATTER);
@@ -445,7 +480,12 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     void *ox = direct ? gx : h->gout;
     void *oy = direct ? gy : (char *)h->gout + (size_t)n * sizeof(T);
     void *oz = direct ? gz : (char *)h->gout + (size_t)2 * n * sizeof(T);
-    if (n > 0) {
+    if (n > 0 && h->tiles) {
+      if (odt == PLACE3D_F64)
+        launch_final_tiles<T, double>(h, s, dc, fc, (double *)ox, (double *)oy, (double *)oz);
+      else
+        launch_final_tiles<T, float>(h, s, dc, fc, (float *)ox, (float *)oy, (float *)oz);
+    } else if (n > 0) {
       if (odt == PLACE3D_F64)
         k_final<T, double><<<grid_for(n, 256), 256, 0, s>>>(n, as<V4<T>>(h->pos), as<V4<T>>(h->size), h->flags_d,
                                                             h->macro_slot, dc, as<T>(h->ex), as<T>(h->ey), as<T>(h->ez),
@@ -494,7 +534,8 @@ void free_all(place3d_handle *h) {
   void *bufs[] = {h->pos,   h->size,  h->off,   h->acc,   h->flags_d, h->macro_ids, h->macro_slot,
                   h->net_start, h->pin_inst, h->q, h->corner, h->rho, h->t1, h->t2, h->czpsi,
                   h->szpsi, h->xinv, h->x2, h->ex, h->ey, h->ez, h->mats, h->suffix, h->mgrad,
-                  h->scal, h->zc, h->gout, h->stage_in, h->check_flag};
+                  h->scal, h->zc, h->gout, h->stage_in, h->check_flag, h->tkey, h->titems,
+                  h->tcount, h->tstart, h->tnitems, h->trec, h->g4};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (h->tc) p3d_tc::destroy(h->tc);
@@ -693,6 +734,29 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
     if (p->flags & PLACE3D_FLAG_MACRO_GATHER_SCAN) h->macro_direct = false;
     if (p->flags & PLACE3D_FLAG_MACRO_GATHER_DIRECT) h->macro_direct = true;
   }
+  // tile windows: halo R covers the largest std-cell footprint (stretched)
+  {
+    const double wbv = (p->xh - p->xl) / p->nx, hbv = (p->yh - p->yl) / p->ny;
+    double hw = std::sqrt(2.0) * wbv, hh = std::sqrt(2.0) * hbv;
+    for (int i = 0; i < n; ++i)
+      if (!p->is_macro[i]) {
+        hw = std::max(hw, std::max(p->w_bot[i], p->w_top[i]));
+        hh = std::max(hh, std::max(p->h_bot[i], p->h_top[i]));
+      }
+    const int R = (int)std::max(std::ceil(0.5 * hw / wbv), std::ceil(0.5 * hh / hbv)) + 1;
+    h->tcfg.ntx = (p->nx + kTile - 1) / kTile;
+    h->tcfg.nty = (p->ny + kTile - 1) / kTile;
+    h->tcfg.R = R;
+    h->tcfg.WX = kTile + 2 * R;
+    h->tcfg.WY = kTile + 2 * R;
+    h->ntiles = h->tcfg.ntx * h->tcfg.nty;
+    const size_t wbins = (size_t)h->tcfg.WX * h->tcfg.WY * p->nz;
+    h->smem_scatter = wbins * 8;  // two 32-bit words per bin
+    h->smem_final = wbins * 3 * (p->precision == PLACE3D_FP64 ? 8 : 4);
+    h->tiles = (p->flags & PLACE3D_FLAG_TILES) && R <= 8 && h->ntiles <= 8192 && n < (1 << 24) &&
+               h->smem_final <= 200 * 1024 && h->smem_scatter <= 200 * 1024;
+    h->max_items = (n + kChunk - 1) / kChunk + h->ntiles;
+  }
 
   // device allocation
   const size_t es = h->esz, nb = h->nb, nn = std::max(n, 1);
@@ -710,7 +774,13 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
       {&h->ex, es * nb}, {&h->ey, es * nb}, {&h->ez, es * nb},
       {(void **)&h->suffix, h->nm && !h->macro_direct ? 3 * 8 * nb : (size_t)8}, {(void **)&h->mgrad, (size_t)24 * std::max(h->nm, 1)},
       {(void **)&h->scal, sizeof(double) * S_COUNT}, {(void **)&h->zc, sizeof(ZStageC)},
-      {&h->gout, 3 * es * nn}, {(void **)&h->check_flag, sizeof(int)}};
+      {&h->gout, 3 * es * nn}, {(void **)&h->check_flag, sizeof(int)},
+      {(void **)&h->tkey, sizeof(int2) * nn},
+      {&h->trec, (p->precision == PLACE3D_FP64 ? sizeof(CellRec<double>) : sizeof(CellRec<float>)) * nn},
+      {&h->g4, v4 * nn},
+      {(void **)&h->tcount, sizeof(int) * (size_t)std::max(h->ntiles, 1)},
+      {(void **)&h->tstart, sizeof(int) * (size_t)(h->ntiles + 1)},
+      {(void **)&h->titems, sizeof(int2) * (size_t)std::max(h->max_items, 1)}, {(void **)&h->tnitems, sizeof(int)}};
   for (auto &a : allocs) {
     cudaError_t e = cudaMalloc(a.p, a.bytes);
     if (e != cudaSuccess) {
@@ -756,6 +826,18 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
   if (cudaMemcpy(h->zc, &zc, sizeof(zc), cudaMemcpyHostToDevice) != cudaSuccess) {
     fail(h, PLACE3D_ERR_CUDA, "upload failed");
     return bail(PLACE3D_ERR_CUDA);
+  }
+  if (h->tiles) {
+    const bool f64 = h->precision == PLACE3D_FP64;
+    cudaError_t e1 = f64 ? cudaFuncSetAttribute(k_scatter_tiles<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)h->smem_scatter)
+                         : cudaFuncSetAttribute(k_scatter_tiles<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)h->smem_scatter);
+    cudaError_t e2 = f64 ? cudaFuncSetAttribute(k_final_tiles<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)h->smem_final)
+                         : cudaFuncSetAttribute(k_final_tiles<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)h->smem_final);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) h->tiles = false;
   }
   if (h->precision == PLACE3D_FP32_TC) {
     std::string why;

@@ -21,7 +21,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_tc": FP32_TC}
 F64, F32 = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
 FLAG_CHECKS = 1
-FLAG_MACRO_GATHER_SCAN, FLAG_MACRO_GATHER_DIRECT, FLAG_SERIAL = 2, 4, 8
+FLAG_MACRO_GATHER_SCAN, FLAG_MACRO_GATHER_DIRECT, FLAG_SERIAL, FLAG_TILES = 2, 4, 8, 16
 WL_FORMS = ((1, 1), (1, 2), (1, 4), (2, 2), (4, 1), (2, 4), (8, 1), (4, 4), (16, 1), (8, 4), (32, 1), (16, 4), (32, 2),
             (32, 4))
 MAP_RHO_FIXED, MAP_EX, MAP_EY, MAP_EZ = 0, 1, 2, 3

@@ -218,3 +218,20 @@ def test_every_reduction_form(precision):
                 for k in ("gx", "gy", "gwaz", "gfd"):
                     assert rel_l2(parts[k], w[k]) < tol, (bi, g2, p2, k)
             h.set_wl_form(bi, G, ppl)
+
+
+@pytest.mark.parametrize("kind", ["default", "outside", "hifanout", "zfixed"])
+def test_tile_bucketed_scatter_gather_path(kind):
+    """The shared-memory tile scatter/gather (PLACE3D_FLAG_TILES) matches the
+    oracle like the default per-cell path (bit-exact map included)."""
+    p, x, y, z = _edge(kind)
+    _check_fp64(p, x, y, z, flags=16)
+    _check_fp32(p, x, y, z, flags=16)
+
+
+@pytest.mark.parametrize("positions", ["uniform", "center"])
+def test_tiles_cells_200k_fp64(positions):
+    """Tile-bucketed path at 256x256x4 with clustered and uniform cells."""
+    p = synth.make_problem("cells_200k", positions=positions)
+    _check_fp64(p, p["x"], p["y"], p["z"], maps=True, flags=16)
+    _check_fp32(p, p["x"], p["y"], p["z"], flags=16)

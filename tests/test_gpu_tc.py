@@ -73,3 +73,18 @@ def test_fp32_tc_rejects_unaligned_grid():
     with pytest.raises(P.Place3DError) as ei:
         P.Place3D(p, precision="fp32_tc")
     assert ei.value.code == -7
+
+
+def test_fp32_tc_full_size_bench_configuration():
+    """The bench's workload and launch configuration (1M cells, 512x512x4,
+    FP32_TC, autotuned reduction forms) against the full FP64 oracle."""
+    p = synth.make_problem("cells_1m")
+    x32, y32, z32 = (np.asarray(p[k], np.float32).astype(np.float64) for k in ("x", "y", "z"))
+    g = run_gpu(p, x32, y32, z32, "fp32_tc", autotune=True)
+    o, r = run_oracle(p, x32, y32, z32, g["alpha"], density_mode=0)
+    assert np.array_equal(g["q"], o.density_fixed(x32, y32, z32, use_float=True))
+    assert g["res"]["obj"] == pytest.approx(r["obj"], rel=2e-5)
+    assert g["res"]["n_cross"] == r["n_cross"]
+    assert g["res"]["hpwl_d2d"] == pytest.approx(r["hpwl_d2d"], rel=1e-6)
+    for k in ("gx", "gy", "gz"):
+        assert rel_l2(g[k], r[k]) < 1e-4, (k, rel_l2(g[k], r[k]))
