@@ -191,6 +191,18 @@ int place3d_set_wl_form(place3d_handle *h, int bucket, int lanes, int pins);
  * evaluation. */
 int place3d_get_result(place3d_handle *h, place3d_result *out);
 
+/* Enqueue, on the handle's stream, a copy of the last evaluation's scalars
+ * into dst (a DEVICE buffer of 10 doubles, in place3d_result order: obj,
+ * wl_bi, wl_z, energy, hpwl_d2d, n_cross, g_scale, s_x, s_y, s_z) without
+ * synchronising (for optimisers that keep the objective on the device). */
+int place3d_result_to_device(place3d_handle *h, double *dst);
+
+/* Change gamma, gamma_z, alpha and lambda for the following evaluations (a
+ * placement loop anneals gamma and raises lambda, eq. analytical-placement).
+ * Errors: INVALID_ARG (gamma <= 0 or a non-finite value). */
+int place3d_set_params(place3d_handle *h, double gamma, double gamma_z,
+                       double alpha, double lambda);
+
 /* Read an intermediate map of the last evaluation into dst (host or device,
  * [N_z][N_y][N_x] with x fastest):
  *   PLACE3D_MAP_RHO_FIXED: int64 density counts of 2^-36 (the fixed-point

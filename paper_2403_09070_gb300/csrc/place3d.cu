@@ -1012,6 +1012,43 @@ int place3d_copy_wl_parts(place3d_handle *h, double *gx, double *gy, double *gfd
   return PLACE3D_OK;
 }
 
+// Result scalars on the device (one thread): obj, wl_bi, wl_z, energy,
+// hpwl_d2d, n_cross, g_scale, s_x, s_y, s_z (the place3d_result order).
+__global__ void k_result(const double *__restrict__ s, double alpha, double lambda, double ef, double *__restrict__ out) {
+  const double energy = ef * s[S_ESUM];
+  out[0] = s[S_WL_BI] + alpha * s[S_WL_Z] + lambda * energy;
+  out[1] = s[S_WL_BI];
+  out[2] = s[S_WL_Z];
+  out[3] = energy;
+  out[4] = s[S_HPWL];
+  out[5] = s[S_NCROSS];
+  out[6] = s[S_SZ] > 0 ? (s[S_SX] + s[S_SY]) / (2.0 * s[S_SZ]) : 0.0;
+  out[7] = s[S_SX];
+  out[8] = s[S_SY];
+  out[9] = s[S_SZ];
+}
+
+int place3d_result_to_device(place3d_handle *h, double *dst) {
+  if (!h || !dst) return fail(h, PLACE3D_ERR_INVALID_ARG, "NULL argument");
+  P3D_CUDA(h, cudaSetDevice(h->device));
+  const double ef = 0.5 * (h->wb * h->hb * h->db) * (double)h->nb;
+  k_result<<<1, 1, 0, h->stream>>>(h->scal, h->alpha, h->lambda, ef, dst);
+  P3D_CUDA(h, cudaGetLastError());
+  return PLACE3D_OK;
+}
+
+int place3d_set_params(place3d_handle *h, double gamma, double gamma_z, double alpha, double lambda) {
+  if (!h) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL handle");
+  if (!(gamma > 0) || !std::isfinite(gamma) || !std::isfinite(gamma_z) || !std::isfinite(alpha) ||
+      !std::isfinite(lambda))
+    return fail(h, PLACE3D_ERR_INVALID_ARG, "gamma must be > 0; gamma_z, alpha, lambda finite");
+  h->gamma = gamma;
+  h->gamma_z = gamma_z;
+  h->alpha = alpha;
+  h->lambda = lambda;
+  return PLACE3D_OK;
+}
+
 int place3d_autotune(place3d_handle *h, int repeats) {
   if (!h) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL handle");
   P3D_CUDA(h, cudaSetDevice(h->device));

@@ -62,7 +62,7 @@ EXPORTS = ("place3d_create", "place3d_geometry", "place3d_alpha", "place3d_set_p
            "place3d_copy_wl_parts", "place3d_set_profiling", "place3d_num_stages", "place3d_stage_name",
            "place3d_stage_times", "place3d_launches_per_eval", "place3d_last_error", "place3d_destroy",
            "place3d_density_map_noalloc", "place3d_tc_selftest", "place3d_autotune", "place3d_wl_forms",
-           "place3d_set_wl_form")
+           "place3d_set_wl_form", "place3d_result_to_device", "place3d_set_params")
 NOALLOC_MAX_BINS = 262144
 
 _lib = None
@@ -105,6 +105,8 @@ def load_library(build_if_missing: bool = True):
     L.place3d_destroy.restype = None
     L.place3d_autotune.argtypes = [vp, i32]
     L.place3d_set_wl_form.argtypes = [vp, i32, i32, i32]
+    L.place3d_result_to_device.argtypes = [vp, vp]
+    L.place3d_set_params.argtypes = [vp, d, d, d, d]
     L.place3d_wl_forms.argtypes = [vp, vp, vp, vp, i32]
     L.place3d_tc_selftest.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp]
     L.place3d_density_map_noalloc.argtypes = [i32] + [vp] * 8 + [d] * 4 + [i32] * 3 + [vp, vp]
@@ -240,6 +242,14 @@ class Place3D:
         self._check(self._L.place3d_eval_objective_and_grad(
             self._h, C.byref(res) if sync else None, *ptrs, dt, mem))
         return res.as_dict() if sync else None
+
+    def result_to_device(self, dst):
+        """Enqueue the last evaluation's 10 scalars into a CUDA float64 tensor."""
+        self._check(self._L.place3d_result_to_device(self._h, dst.data_ptr()))
+
+    def set_params(self, gamma: float, gamma_z: float, alpha: float, lam: float):
+        self._check(self._L.place3d_set_params(self._h, float(gamma), float(gamma_z), float(alpha), float(lam)))
+        self.alpha = float(alpha)
 
     def get_result(self) -> dict:
         res = Result()
