@@ -44,6 +44,7 @@ def _args():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32_tc", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time separate launches instead of a CUDA graph")
     return ap.parse_args()
 
 
@@ -253,40 +254,61 @@ def main():
     grads = [torch.empty(n, device="cuda", dtype=dt) for _ in range(3)]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
-    def step():
+    def step_launches():
         h.set_positions(*xyz)
         h.eval(*grads, sync=False)
+
+    def step_graph():
+        h.eval_graph(*xyz, *grads)
+
+    step = step_launches if a.no_graph else step_graph
 
     h.set_positions(*xyz)
     h.autotune(3)  # per-bucket reduction forms, timed on this workload
 
+    def timed(fn, k, profile=False):
+        """k steps bracketed by barriers + syncs; per-step CUDA events on the
+        launching stream, L2 flushed between steps outside the event pairs."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        if profile:
+            h.stage_times(reset=True)
+            h.set_profiling(True)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(k):
+            flush.zero_()
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        st = None
+        if profile:
+            h.set_profiling(False)
+            st = h.stage_times(reset=True)
+        tot = max_over_ranks(float(sum(e0.elapsed_time(e1) for e0, e1 in ev)), dist if world > 1 else None, "cuda")
+        return tot, st
+
     for _ in range(a.warmup):
         flush.zero_()
         step()
+        flush.zero_()
+        (step_launches if step is step_graph else step_graph)()
     torch.cuda.synchronize()
-    h.stage_times(reset=True)
-    h.set_profiling(True)
+    # timed region A: the measured path (CUDA graph unless --no-graph), clocks sampled
     clk = Clocks(local)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     clk.start()
-    for k in range(a.steps):
-        flush.zero_()  # L2 flush between timed steps (outside the event pair)
-        ev[k][0].record(stream)
-        step()
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    total_ms, st_a = timed(step, a.steps, profile=step is step_launches)
     clocks = clk.stop()
-    h.set_profiling(False)
+    # timed region B: separate launches with per-stage CUDA events (stages and roofline)
+    total_b_ms, st = timed(step_launches, a.steps, profile=True)
+    if st_a is not None:
+        st = st_a
+    alt_rate = job_throughput(world, a.steps, total_b_ms)
     res = h.get_result()
     h_forms = h.wl_forms()
-    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    total_ms = max_over_ranks(float(sum(step_ms)), dist if world > 1 else None, "cuda")
-    st = h.stage_times(reset=True)
     launches = h.launches_per_eval() + 1  # + the position-packing kernel
     value = job_throughput(world, a.steps, total_ms)
 
@@ -363,6 +385,9 @@ def main():
             "stages": stages,
             "clocks": clocks,
             "objective": res["obj"],
+            "timed_path": "separate launches" if a.no_graph else "CUDA graph (pack + evaluation)",
+            "separate_launches_evals_per_s": alt_rate,
+            "stages_from": "timed region of separate launches with per-stage CUDA events (same workload, K steps)",
             "wl_forms": h_forms,
         }
         if cpu is not None:

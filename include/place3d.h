@@ -191,6 +191,34 @@ int place3d_set_wl_form(place3d_handle *h, int bucket, int lanes, int pins);
  * evaluation. */
 int place3d_get_result(place3d_handle *h, place3d_result *out);
 
+/* One evaluation as a CUDA graph: position packing (as set_positions with
+ * DEVICE arrays) plus the whole evaluation, writing the gradient to DEVICE
+ * arrays gx, gy, gz.  The first call (and any call with other pointers or
+ * dtype) captures the graph on a private stream and instantiates it; every
+ * call launches it on the handle's stream.  The pointers are baked into the
+ * graph: the arrays must stay allocated while the handle replays it.
+ * Results: place3d_get_result / place3d_result_to_device. */
+int place3d_eval_graph(place3d_handle *h, const void *x, const void *y,
+                       const void *z, void *gx, void *gy, void *gz, int dtype);
+
+/* Batches of independent placement problems (possibly of uneven sizes and
+ * precisions) evaluated by ONE CUDA-graph launch: every handle's packing and
+ * evaluation is captured on its own stream, forked from and joined to one
+ * root, so the instances run concurrently.  handles stay owned by the
+ * caller and must outlive the batch; all on one device.  place3d_batch_eval
+ * takes per-instance DEVICE pointers (arrays of count pointers, dtype as in
+ * place3d_eval_graph), captures on first use or when any pointer changes,
+ * and launches on cuda_stream.  Per-instance results via
+ * place3d_get_result.  Errors: INVALID_ARG, CUDA. */
+typedef struct place3d_batch place3d_batch;
+int place3d_batch_create(place3d_handle *const *handles, int count,
+                         place3d_batch **out);
+int place3d_batch_eval(place3d_batch *b, const void *const *xs,
+                       const void *const *ys, const void *const *zs,
+                       void *const *gxs, void *const *gys, void *const *gzs,
+                       int dtype, void *cuda_stream);
+void place3d_batch_destroy(place3d_batch *b);
+
 /* Enqueue, on the handle's stream, a copy of the last evaluation's scalars
  * into dst (a DEVICE buffer of 10 doubles, in place3d_result order: obj,
  * wl_bi, wl_z, energy, hpwl_d2d, n_cross, g_scale, s_x, s_y, s_z) without

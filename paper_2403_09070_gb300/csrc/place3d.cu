@@ -101,6 +101,11 @@ struct place3d_handle {
   std::vector<Bucket> buckets;
   // tensor-core transform state (FP32_TC)
   p3d_tc::TcPlan *tc = nullptr;
+  // CUDA graph of one evaluation (place3d_eval_graph)
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  const void *gptr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int gdtype = -1;
   // results
   double host_scal[S_COUNT];
   bool have_result = false;
@@ -544,6 +549,8 @@ void free_all(place3d_handle *h) {
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
 }
 
 template <typename T>
@@ -863,6 +870,32 @@ int place3d_geometry(const place3d_handle *h, double out[6]) {
   return PLACE3D_OK;
 }
 
+// Pack device positions into the handle's float4/double4 buffer (no checks,
+// no host copies: usable inside a stream capture).
+static int enqueue_pack(place3d_handle *h, const void *px, const void *py, const void *pz, int dtype) {
+  cudaStream_t s = h->stream;
+  const int n = h->n;
+  const int g = grid_for(n, 256);
+  if (n == 0) return PLACE3D_OK;
+  if (h->precision == PLACE3D_FP64) {
+    if (dtype == PLACE3D_F64)
+      k_pack<double, double><<<g, 256, 0, s>>>(n, (const double *)px, (const double *)py, (const double *)pz,
+                                               as<V4<double>>(h->pos), 0, 0, nullptr);
+    else
+      k_pack<float, double><<<g, 256, 0, s>>>(n, (const float *)px, (const float *)py, (const float *)pz,
+                                              as<V4<double>>(h->pos), 0, 0, nullptr);
+  } else {
+    if (dtype == PLACE3D_F64)
+      k_pack<double, float><<<g, 256, 0, s>>>(n, (const double *)px, (const double *)py, (const double *)pz,
+                                              as<V4<float>>(h->pos), 0, 0, nullptr);
+    else
+      k_pack<float, float><<<g, 256, 0, s>>>(n, (const float *)px, (const float *)py, (const float *)pz,
+                                             as<V4<float>>(h->pos), 0, 0, nullptr);
+  }
+  count_launch(h, ST_PREP);
+  return PLACE3D_OK;
+}
+
 int place3d_set_positions(place3d_handle *h, const void *x, const void *y, const void *z, int dtype, int mem) {
   if (!h) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL handle");
   if (h->n == 0) return PLACE3D_OK;
@@ -927,9 +960,9 @@ int place3d_eval_objective_and_grad(place3d_handle *h, place3d_result *out, void
   const int rc = h->precision == PLACE3D_FP64 ? eval_impl<double>(h, gx, gy, gz, dtype, mem)
                                               : eval_impl<float>(h, gx, gy, gz, dtype, mem);
   if (rc != PLACE3D_OK) return rc;
-  P3D_CUDA(h, cudaMemcpyAsync(h->host_scal, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, h->stream));
   h->have_result = true;
   if (out || (ng && mem == PLACE3D_MEM_HOST)) {
+    P3D_CUDA(h, cudaMemcpyAsync(h->host_scal, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, h->stream));
     P3D_CUDA(h, cudaStreamSynchronize(h->stream));
     if (h->tc && p3d_tc::error_code(h->tc) != 0)
       return fail(h, PLACE3D_ERR_TIMEOUT, "a tensor-core transform wait expired");
@@ -943,6 +976,7 @@ int place3d_get_result(place3d_handle *h, place3d_result *out) {
   if (!h->have_result) return fail(h, PLACE3D_ERR_INVALID_ARG, "no evaluation has been enqueued");
   P3D_CUDA(h, cudaSetDevice(h->device));
   P3D_CUDA(h, cudaStreamSynchronize(h->stream));
+  P3D_CUDA(h, cudaMemcpy(h->host_scal, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost));
   if (h->tc && p3d_tc::error_code(h->tc) != 0)
     return fail(h, PLACE3D_ERR_TIMEOUT, "a tensor-core transform wait expired");
   fill_result(h, out);
@@ -1115,6 +1149,61 @@ int place3d_wl_forms(const place3d_handle *h, int32_t *dmax, int32_t *lanes, int
   return k;
 }
 
+// Capture pack + evaluation of one handle on `cs` (the handle's streams are
+// redirected to cs for the capture; the side stream forks from it).
+static int capture_eval(place3d_handle *h, cudaStream_t cs, const void *const *ptr, int dtype) {
+  const bool prof = h->profiling;
+  cudaStream_t keep = h->stream;
+  h->profiling = false;
+  h->stream = cs;
+  int rc = enqueue_pack(h, ptr[0], ptr[1], ptr[2], dtype);
+  if (rc == PLACE3D_OK)
+    rc = h->precision == PLACE3D_FP64
+             ? eval_impl<double>(h, const_cast<void *>(ptr[3]), const_cast<void *>(ptr[4]), const_cast<void *>(ptr[5]),
+                                 dtype, PLACE3D_MEM_DEVICE)
+             : eval_impl<float>(h, const_cast<void *>(ptr[3]), const_cast<void *>(ptr[4]), const_cast<void *>(ptr[5]),
+                                dtype, PLACE3D_MEM_DEVICE);
+  h->stream = keep;
+  h->profiling = prof;
+  return rc;
+}
+
+int place3d_eval_graph(place3d_handle *h, const void *x, const void *y, const void *z, void *gx, void *gy, void *gz,
+                       int dtype) {
+  if (!h) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL handle");
+  if (!x || !y || !z || !gx || !gy || !gz) return fail(h, PLACE3D_ERR_INVALID_ARG, "NULL device array");
+  if (dtype != PLACE3D_F64 && dtype != PLACE3D_F32) return fail(h, PLACE3D_ERR_INVALID_ARG, "bad dtype");
+  P3D_CUDA(h, cudaSetDevice(h->device));
+  const void *ptr[6] = {x, y, z, gx, gy, gz};
+  bool same = h->gexec && h->gdtype == dtype;
+  for (int k = 0; k < 6 && same; ++k) same = h->gptr[k] == ptr[k];
+  if (!same) {
+    if (h->gexec) {
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+    }
+    if (!h->cap_stream) P3D_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    P3D_CUDA(h, cudaStreamSynchronize(h->stream));
+    P3D_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = capture_eval(h, h->cap_stream, ptr, dtype);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (rc != PLACE3D_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    const cudaError_t ei = cudaGraphInstantiate(&h->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return cuda_fail(h, ei, "cudaGraphInstantiate");
+    for (int k = 0; k < 6; ++k) h->gptr[k] = ptr[k];
+    h->gdtype = dtype;
+  }
+  P3D_CUDA(h, cudaGraphLaunch(h->gexec, h->stream));
+  h->have_result = true;
+  return PLACE3D_OK;
+}
+
 int place3d_set_profiling(place3d_handle *h, int on) {
   if (!h) return PLACE3D_ERR_INVALID_ARG;
   h->profiling = on != 0;
@@ -1152,6 +1241,115 @@ int place3d_stage_times(place3d_handle *h, double *ms, int64_t *launches, int64_
 }
 
 int place3d_launches_per_eval(const place3d_handle *h) { return h ? h->launches : 0; }
+
+struct place3d_batch {
+  std::vector<place3d_handle *> hs;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> done;
+  cudaStream_t root = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void *> ptrs;
+  int dtype = -1, device = 0;
+  std::string err;
+};
+
+static void batch_free(place3d_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto s : b->streams) cudaStreamDestroy(s);
+  for (auto e : b->done) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->root) cudaStreamDestroy(b->root);
+  delete b;
+}
+
+int place3d_batch_create(place3d_handle *const *handles, int count, place3d_batch **out) {
+  if (!handles || count < 1 || !out) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "bad batch arguments");
+  *out = nullptr;
+  const int dev = handles[0] ? handles[0]->device : -1;
+  for (int i = 0; i < count; ++i)
+    if (!handles[i] || handles[i]->device != dev)
+      return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "batch handles must be non-NULL and on one device");
+  if (cudaSetDevice(dev) != cudaSuccess) return fail(nullptr, PLACE3D_ERR_CUDA, "cudaSetDevice failed");
+  place3d_batch *b = new place3d_batch();
+  b->device = dev;
+  b->hs.assign(handles, handles + count);
+  bool ok = cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < count && ok; ++i) {
+    cudaStream_t s;
+    cudaEvent_t e;
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) {
+      b->streams.push_back(s);
+      b->done.push_back(e);
+    }
+  }
+  if (!ok) {
+    batch_free(b);
+    return fail(nullptr, PLACE3D_ERR_CUDA, "batch stream/event creation failed");
+  }
+  *out = b;
+  return PLACE3D_OK;
+}
+
+int place3d_batch_eval(place3d_batch *b, const void *const *xs, const void *const *ys, const void *const *zs,
+                       void *const *gxs, void *const *gys, void *const *gzs, int dtype, void *cuda_stream) {
+  if (!b || !xs || !ys || !zs || !gxs || !gys || !gzs) return PLACE3D_ERR_INVALID_ARG;
+  if (dtype != PLACE3D_F64 && dtype != PLACE3D_F32) return PLACE3D_ERR_INVALID_ARG;
+  if (cudaSetDevice(b->device) != cudaSuccess) return PLACE3D_ERR_CUDA;
+  const int n = (int)b->hs.size();
+  std::vector<const void *> ptr;
+  for (int i = 0; i < n; ++i) {
+    const void *pi[6] = {xs[i], ys[i], zs[i], gxs[i], gys[i], gzs[i]};
+    for (int k = 0; k < 6; ++k) {
+      if (!pi[k]) return PLACE3D_ERR_INVALID_ARG;
+      ptr.push_back(pi[k]);
+    }
+  }
+  if (!b->exec || b->dtype != dtype || b->ptrs != ptr) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    for (auto *h : b->hs)
+      if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PLACE3D_ERR_CUDA;
+    if (cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PLACE3D_ERR_CUDA;
+    int rc = cudaEventRecord(b->fork, b->root) == cudaSuccess ? PLACE3D_OK : PLACE3D_ERR_CUDA;
+    for (int i = 0; i < n && rc == PLACE3D_OK; ++i) {
+      if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) {
+        rc = PLACE3D_ERR_CUDA;
+        break;
+      }
+      rc = capture_eval(b->hs[i], b->streams[i], &ptr[6 * i], dtype);
+      if (rc == PLACE3D_OK && (cudaEventRecord(b->done[i], b->streams[i]) != cudaSuccess ||
+                               cudaStreamWaitEvent(b->root, b->done[i], 0) != cudaSuccess))
+        rc = PLACE3D_ERR_CUDA;
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->root, &graph);
+    if (rc != PLACE3D_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc != PLACE3D_OK ? rc : PLACE3D_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return PLACE3D_ERR_CUDA;
+    b->ptrs = ptr;
+    b->dtype = dtype;
+  }
+  if (cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(cuda_stream)) != cudaSuccess) return PLACE3D_ERR_CUDA;
+  for (auto *h : b->hs) h->have_result = true;
+  return PLACE3D_OK;
+}
+
+void place3d_batch_destroy(place3d_batch *b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  batch_free(b);
+}
 
 const char *place3d_last_error(const place3d_handle *h) { return h ? h->err.c_str() : g_thread_err.c_str(); }
 

@@ -62,7 +62,8 @@ EXPORTS = ("place3d_create", "place3d_geometry", "place3d_alpha", "place3d_set_p
            "place3d_copy_wl_parts", "place3d_set_profiling", "place3d_num_stages", "place3d_stage_name",
            "place3d_stage_times", "place3d_launches_per_eval", "place3d_last_error", "place3d_destroy",
            "place3d_density_map_noalloc", "place3d_tc_selftest", "place3d_autotune", "place3d_wl_forms",
-           "place3d_set_wl_form", "place3d_result_to_device", "place3d_set_params")
+           "place3d_set_wl_form", "place3d_result_to_device", "place3d_set_params", "place3d_eval_graph",
+           "place3d_batch_create", "place3d_batch_eval", "place3d_batch_destroy")
 NOALLOC_MAX_BINS = 262144
 
 _lib = None
@@ -106,6 +107,11 @@ def load_library(build_if_missing: bool = True):
     L.place3d_autotune.argtypes = [vp, i32]
     L.place3d_set_wl_form.argtypes = [vp, i32, i32, i32]
     L.place3d_result_to_device.argtypes = [vp, vp]
+    L.place3d_eval_graph.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32]
+    L.place3d_batch_create.argtypes = [vp, i32, C.POINTER(vp)]
+    L.place3d_batch_eval.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, vp]
+    L.place3d_batch_destroy.argtypes = [vp]
+    L.place3d_batch_destroy.restype = None
     L.place3d_set_params.argtypes = [vp, d, d, d, d]
     L.place3d_wl_forms.argtypes = [vp, vp, vp, vp, i32]
     L.place3d_tc_selftest.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp]
@@ -251,6 +257,15 @@ class Place3D:
         self._check(self._L.place3d_set_params(self._h, float(gamma), float(gamma_z), float(alpha), float(lam)))
         self.alpha = float(alpha)
 
+    def eval_graph(self, x, y, z, gx, gy, gz):
+        """Pack + evaluate as one CUDA-graph launch (CUDA tensors; the graph is
+        re-captured only when a tensor's address or the dtype changes)."""
+        b = [_buf(a) for a in (x, y, z, gx, gy, gz)]
+        if any(v[2] != MEM_DEVICE for v in b) or len({v[1] for v in b}) != 1:
+            raise ValueError("eval_graph takes CUDA tensors of one dtype")
+        self._gkeep = [v[3] for v in b]
+        self._check(self._L.place3d_eval_graph(self._h, *[v[0] for v in b], b[0][1]))
+
     def get_result(self) -> dict:
         res = Result()
         self._check(self._L.place3d_get_result(self._h, C.byref(res)))
@@ -335,3 +350,44 @@ def tc_selftest(A, W):
     if rc != 0:
         raise Place3DError(rc, f"place3d_tc_selftest failed (wait error {int(err[0])})")
     return out, int(err[0])
+
+
+class Batch:
+    """Independent placement problems evaluated by one CUDA-graph launch."""
+
+    def __init__(self, handles):
+        L = load_library()
+        self._L = L
+        self.handles = list(handles)
+        arr = (C.c_void_p * len(self.handles))(*[h._h.value for h in self.handles])
+        b = C.c_void_p()
+        rc = L.place3d_batch_create(arr, len(self.handles), C.byref(b))
+        if rc != 0:
+            raise Place3DError(rc, L.place3d_last_error(None).decode())
+        self._b = b
+
+    def eval(self, xs, ys, zs, gxs, gys, gzs, stream=None):
+        """Per-instance CUDA tensors (lists); launches the batch graph."""
+        cols = [xs, ys, zs, gxs, gys, gzs]
+        bufs = [[_buf(a) for a in col] for col in cols]
+        dts = {v[1] for col in bufs for v in col}
+        if len(dts) != 1 or any(v[2] != MEM_DEVICE for col in bufs for v in col):
+            raise ValueError("batch eval takes CUDA tensors of one dtype")
+        self._keep = [v[3] for col in bufs for v in col]
+        arrs = [(C.c_void_p * len(col))(*[v[0] for v in col]) for col in bufs]
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        rc = self._L.place3d_batch_eval(self._b, *arrs, dts.pop(), C.c_void_p(stream or 0))
+        if rc != 0:
+            raise Place3DError(rc, "place3d_batch_eval failed")
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._L.place3d_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -224,3 +224,21 @@ def draw_positions(rng: np.random.Generator, prob: dict, kind: str = "uniform"):
         z[idx[0::2]] = zlo
         z[idx[1::2]] = zhi
     return x, y, z
+
+
+def make_batch(count: int = 24, seed: int = 4, n_min: int = 5000, n_max: int = 300_000) -> list:
+    """Independent instances of uneven size: cell counts log-uniform in
+    [n_min, n_max], macros 0.01 % of the cells (at least 1), nets 1.05 x the
+    cells with the usual degree mix, dies 3,000 * sqrt(n / 200k) wide, grids
+    N_x = N_y = the power of two nearest sqrt(n) clamped to [64, 512] and
+    N_z = 2 for N_x <= 128, else 4."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        nm = max(1, int(round(1e-4 * n)))
+        nxy = int(min(512, max(64, 2 ** round(math.log2(math.sqrt(n))))))
+        wl = Workload(f"batch{k}", n, nm, int(1.05 * n), 3000.0 * math.sqrt(n / 200_000.0), nxy, nxy,
+                      2 if nxy <= 128 else 4, seed * 1000 + k)
+        out.append(make_problem(wl))
+    return out
