@@ -65,6 +65,7 @@ def lib():
         L.orc_density_grad_exact.argtypes = [P] + [vp] * 7
         L.orc_wirelength.argtypes = [P, vp, vp, vp, C.c_int, vp, vp, vp, vp, vp]
         L.orc_eval.argtypes = [P, vp, vp, vp, C.c_int, C.c_int, vp, vp, vp, vp]
+        L.orc_filler_plan.argtypes = [P, vp, d, d, vp]
         _lib = L
     return _lib
 
@@ -132,6 +133,16 @@ class Oracle:
         lib().orc_attributes(C.byref(self.s), _ptr(x), _ptr(y), _ptr(z), _ptr(delta),
                              *[_ptr(a) for a in out])
         return dict(delta=delta, w=out[0], h=out[1], sw=out[2], sh=out[3], omega=out[4])
+
+    def filler_plan(self, z, u_top: float, u_bot: float) -> dict:
+        """Eqs. filler-vol / free-filler-vol at initial depths z."""
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        o = np.zeros(11)
+        lib().orc_filler_plan(C.byref(self.s), _ptr(z), float(u_top), float(u_bot), _ptr(o))
+        keys = ("vol_a", "vol_f_top", "vol_f_bot", "vol_fr", "w_top", "h_top", "w_bot", "h_bot")
+        d = dict(zip(keys, o[:8].tolist()))
+        d.update(n_top=int(o[8]), n_bot=int(o[9]), n_free=int(o[10]))
+        return d
 
     def density_direct(self, x, y, z):
         x, y, z = self._xyz(x, y, z)

@@ -825,3 +825,45 @@ void orc_eval(const orc_problem *p, const double *x, const double *y,
   free(wgx); free(wgy); free(wfd); free(wgz); free(rho);
   free(ex); free(ey); free(ez); free(dgx); free(dgy); free(dgz);
 }
+
+/* Sec. III-A, eqs. filler-vol and free-filler-vol (see oracle.h). */
+void orc_filler_plan(const orc_problem *p, const double *z, double u_top,
+                     double u_bot, double out[11]) {
+  double g[6];
+  orc_geometry(p, g);
+  const double depth = 0.5 * g[5];
+  const double V = g[3] * g[4] * g[5];
+  double vol_a = 0.0, sw_t = 0.0, sh_t = 0.0, sw_b = 0.0, sh_b = 0.0;
+  long n_std = 0;
+  for (int i = 0; i < p->n_inst; ++i) {
+    double w, h;
+    attr_one(p, g, i, z[i], NULL, &w, &h, NULL, NULL, NULL);
+    vol_a += w * h * depth;
+    if (!p->is_macro[i] && !(p->z_fixed && p->z_fixed[i])) {
+      sw_t += p->w_top[i];
+      sh_t += p->h_top[i];
+      sw_b += p->w_bot[i];
+      sh_b += p->h_bot[i];
+      ++n_std;
+    }
+  }
+  double vf_t = 0.5 * V * (1.0 - u_top);
+  double vf_b = 0.5 * V * (1.0 - u_bot);
+  double vfr = V - (vf_t + vf_b + vol_a);
+  if (vfr < 0.0) vfr = 0.0;
+  double wt = n_std ? sw_t / n_std : 0.0, ht = n_std ? sh_t / n_std : 0.0;
+  double wb = n_std ? sw_b / n_std : 0.0, hb = n_std ? sh_b / n_std : 0.0;
+  double unit_t = wt * ht * depth, unit_b = wb * hb * depth;
+  double unit_fr = 0.5 * (unit_t + unit_b);
+  out[0] = vol_a;
+  out[1] = vf_t;
+  out[2] = vf_b;
+  out[3] = vfr;
+  out[4] = wt;
+  out[5] = ht;
+  out[6] = wb;
+  out[7] = hb;
+  out[8] = unit_t > 0.0 ? floor(vf_t / unit_t + 0.5) : 0.0;
+  out[9] = unit_b > 0.0 ? floor(vf_b / unit_b + 0.5) : 0.0;
+  out[10] = unit_fr > 0.0 ? floor(vfr / unit_fr + 0.5) : 0.0;
+}

@@ -118,6 +118,20 @@ void orc_wirelength(const orc_problem *p, const double *x, const double *y,
                     const double *z, int fd_mode, double out[4], double *gx,
                     double *gy, double *gfd, double *gwaz);
 
+/* Dummy fillers of Sec. III-A: eq. filler-vol (z-fixed fillers, one set per
+ * die, volume (1/2) d_x d_y d_z (1 - u)) and eq. free-filler-vol (free
+ * fillers, the remaining white space).  vol_a is the total instance volume at
+ * the initial depths z: each instance a cuboid of depth d_z/2 whose footprint
+ * is that of its die (eq. std-size-tech; eq. macro-size-tech for macros).
+ * Filler footprint on a die (reading): the mean std-cell width and height on
+ * that die, std cells being the instances that are neither macros nor
+ * z-fixed.  Counts: the set's volume over one filler's volume, rounded to the
+ * nearest integer; a free filler counts the mean of the two dies' filler
+ * volumes.
+ * out = {vol_a, vol_f+, vol_f-, vol_fr, w+, h+, w-, h-, n+, n-, n_fr}. */
+void orc_filler_plan(const orc_problem *p, const double *z, double u_top,
+                     double u_bot, double out[11]);
+
 /* Full objective and gradient (a1..a11).  density_mode: 0 = direct FP64
  * density, 1 = fixed-point replica in double, 2 = fixed-point replica in
  * float.  out = {obj, wl_bi, wl_z, energy, hpwl_d2d, n_cross, g_scale,
