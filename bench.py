@@ -40,7 +40,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="place3d", choices=["place3d", "reference"])
-    ap.add_argument("--workload", default="cells_1m")
+    ap.add_argument("--workload", default="cells_1m", help="cells_2k|cells_200k|cells_1m|cells_4m_skewed|batch24")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32_tc", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -148,8 +148,7 @@ def _oracle_worker(args):
     """Generate the workload once, then time `count` full oracle evaluations."""
     workload, count = args
     from oracle import Oracle
-    from paper_2403_09070_gb300 import synth
-    p = synth.make_problem(workload)
+    p = make_workload(workload)
     o = Oracle(p)
     times = []
     for _ in range(count):
@@ -209,11 +208,142 @@ def run_reference(a):
     return 0
 
 
-def _workload_desc(name):
+FILLER_U = 0.8  # maximum utilisation of each die for the "<base>_fillers" workloads
+
+
+def make_workload(name: str) -> dict:
+    """A named synthetic problem; "<base>_fillers" appends the dummy fillers
+    of eqs. filler-vol / free-filler-vol (u+ = u- = 0.8) to <base>, spread
+    uniformly over the region (a mid-placement state)."""
+    from paper_2403_09070_gb300 import fillers, synth
+    if name.endswith("_fillers"):
+        p = synth.make_problem(name[:-len("_fillers")])
+        return fillers.insert(p, FILLER_U, FILLER_U, seed=11, positions="uniform")
+    return synth.make_problem(name)
+
+
+def _workload_desc(name, prob=None):
     from paper_2403_09070_gb300 import synth
-    w = synth.WORKLOADS[name]
-    return (f"{name}: {w.n_std} std cells + {w.n_macro} macros, {w.n_net} nets (+{w.n_hifanout} high-fanout), "
-            f"{w.die:g}x{w.die:g} dies, {w.nx}x{w.ny}x{w.nz} bins")
+    base = name[:-len("_fillers")] if name.endswith("_fillers") else name
+    w = synth.WORKLOADS[base]
+    d = (f"{name}: {w.n_std} std cells + {w.n_macro} macros, {w.n_net} nets (+{w.n_hifanout} high-fanout), "
+         f"{w.die:g}x{w.die:g} dies, {w.nx}x{w.ny}x{w.nz} bins")
+    if prob is not None and "fillers" in prob:
+        f = prob["fillers"]
+        d += (f" + {f['n_top']} top / {f['n_bot']} bottom z-fixed and {f['n_free']} free fillers "
+              f"(u+ = u- = {FILLER_U})")
+    return d
+
+
+# ---------------------------------------------------------------- batch workload
+def run_batch(a):
+    """24 independent instances of uneven size (cell counts log-uniform in
+    5k..300k, per-instance grids 64x64x2 .. 512x512x4) evaluated by one CUDA
+    graph launch per step; grad evals/s counts instance evaluations."""
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2403_09070_gb300 import place3d as P
+    from paper_2403_09070_gb300 import synth
+    probs = synth.make_batch(24, seed=4)
+    stream = torch.cuda.current_stream()
+    hs, xyz, gs = [], [], []
+    for p in probs:
+        prec = "fp32_tc" if p["nx"] % 128 == 0 else "fp32"
+        h = P.Place3D(p, precision=prec, device=local, stream=stream)
+        v = [torch.tensor(p[k], device="cuda", dtype=torch.float32) for k in ("x", "y", "z")]
+        h.set_positions(*v)
+        h.autotune(2)
+        hs.append(h)
+        xyz.append(v)
+        gs.append([torch.empty(p["n_inst"], device="cuda", dtype=torch.float32) for _ in range(3)])
+    batch = P.Batch(hs)
+    cols = [[v[k] for v in xyz] for k in range(3)] + [[g[k] for g in gs] for k in range(3)]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def one_graph():
+        batch.eval(*cols, stream=stream)
+
+    def sequential():
+        for h, v, g in zip(hs, xyz, gs):
+            h.eval_graph(*v, *g)
+
+    def timed(fn, k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(k):
+            flush.zero_()
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        return max_over_ranks(float(sum(e0.elapsed_time(e1) for e0, e1 in ev)), dist if world > 1 else None, "cuda")
+
+    for _ in range(a.warmup):
+        one_graph()
+        sequential()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    ms = timed(one_graph, a.steps)
+    clocks = clk.stop()
+    ms_seq = timed(sequential, a.steps)
+    n_total = sum(p["n_inst"] for p in probs)
+    # end to end: host positions in, host gradients out, through the C ABI
+    hx = [[t.cpu().pin_memory() for t in v] for v in xyz]
+    hg = [[torch.empty_like(t, device="cpu").pin_memory() for t in g] for g in gs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        for v, hv in zip(xyz, hx):
+            for d_, s_ in zip(v, hv):
+                d_.copy_(s_, non_blocking=True)
+        one_graph()
+        for g, hgg in zip(gs, hg):
+            for s_, d_ in zip(g, hgg):
+                d_.copy_(s_, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1000.0, dist if world > 1 else None, "cuda")
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    alg = sum(sum(algorithmic(p, "fp32")["bytes"].values()) for p in probs)
+    ach = alg / (ms / a.steps * 1e6)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": job_throughput(world, a.steps * len(probs), ms), "unit": UNIT,
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (transforms bf16x3 split on tensor cores where N_x, N_y are multiples of 128)",
+            "data": "synthetic",
+            "config": {"workload": f"batch24: 24 instances, {n_total} instances in total, cells log-uniform in "
+                                   f"5k..300k, grids 64x64x2..512x512x4, one CUDA-graph launch per step",
+                       "l2": "flushed between timed steps", "parallelism": f"replicas x{world}"},
+            "sequential_graphs_evals_per_s": job_throughput(world, a.steps * len(probs), ms_seq),
+            "e2e": {"value": job_throughput(world, a.steps * len(probs), e2e_ms), "unit": UNIT,
+                    "h2d_bytes_per_step": 12 * n_total, "d2h_bytes_per_step": 12 * n_total},
+            "gpu_launches": a.steps * sum(h.launches_per_eval() + 1 for h in hs),
+            "roofline": {"bound": "hbm", "kernel": "whole batch step", "achieved": ach, "peak": hbm,
+                         "unit": "GB/s", "frac": ach / hbm, "traffic": None},
+            "clocks": clocks}), flush=True)
+    batch.close()
+    for h in hs:
+        h.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -221,6 +351,8 @@ def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "batch24":
+        return run_batch(a)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -237,7 +369,7 @@ def main():
     from paper_2403_09070_gb300 import place3d as P
     from paper_2403_09070_gb300 import synth
 
-    prob = synth.make_problem(a.workload)
+    prob = make_workload(a.workload)
     n = prob["n_inst"]
     precision = a.precision
     if precision == "auto":
@@ -266,9 +398,10 @@ def main():
     h.set_positions(*xyz)
     h.autotune(3)  # per-bucket reduction forms, timed on this workload
 
-    def timed(fn, k, profile=False):
+    def timed(fn, k, profile=False, tag="timed"):
         """k steps bracketed by barriers + syncs; per-step CUDA events on the
-        launching stream, L2 flushed between steps outside the event pairs."""
+        launching stream, L2 flushed between steps outside the event pairs.
+        The steps sit in an NVTX range named `tag` (a profiler filter)."""
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
         if profile:
             h.stage_times(reset=True)
@@ -276,11 +409,13 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push(tag)
         for i in range(k):
             flush.zero_()
             ev[i][0].record(stream)
             fn()
             ev[i][1].record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -300,10 +435,10 @@ def main():
     # timed region A: the measured path (CUDA graph unless --no-graph), clocks sampled
     clk = Clocks(local)
     clk.start()
-    total_ms, st_a = timed(step, a.steps, profile=step is step_launches)
+    total_ms, st_a = timed(step, a.steps, profile=step is step_launches, tag="timed_main")
     clocks = clk.stop()
     # timed region B: separate launches with per-stage CUDA events (stages and roofline)
-    total_b_ms, st = timed(step_launches, a.steps, profile=True)
+    total_b_ms, st = timed(step_launches, a.steps, profile=True, tag="timed_launches")
     if st_a is not None:
         st = st_a
     alt_rate = job_throughput(world, a.steps, total_b_ms)
@@ -374,7 +509,7 @@ def main():
             "dtype": {"fp32_tc": "f32 (transforms bf16x3 split on tensor cores, f64 scalars)",
                       "fp32": "f32 (f64 scalars)", "fp64": "f64"}[precision],
             "data": "synthetic",
-            "config": {"workload": _workload_desc(a.workload), "precision": precision,
+            "config": {"workload": _workload_desc(a.workload, prob), "precision": precision,
                        "n_inst": n, "n_pin": prob["n_pin"], "n_net": prob["n_net"],
                        "l2": "flushed between timed steps (256 MiB write, outside the step's event pair)",
                        "parallelism": f"replicas x{world}"},

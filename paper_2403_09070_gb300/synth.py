@@ -49,8 +49,6 @@ class Workload:
     nz: int
     seed: int
     n_hifanout: int = 0  # extra nets with log-uniform 2k..20k pins
-    n_filler_fixed: int = 0  # z-fixed fillers (pinless), half per die
-    n_filler_free: int = 0  # free fillers (pinless)
 
 
 WORKLOADS = {
@@ -126,8 +124,7 @@ def make_problem(wl: Workload | str, positions: str = "uniform", origin=(0.0, 0.
     rng = np.random.default_rng(wl.seed if seed is None else seed)
     d = float(wl.die)
     n_std, n_mac = wl.n_std, wl.n_macro
-    n_fill = wl.n_filler_fixed + wl.n_filler_free
-    n_inst = n_std + n_mac + n_fill
+    n_inst = n_std + n_mac
 
     # --- sizes (bottom die; top die 0.8x) ---
     w_bot = np.empty(n_inst)
@@ -138,19 +135,11 @@ def make_problem(wl: Workload | str, positions: str = "uniform", origin=(0.0, 0.
         side = math.sqrt(0.2 * d * d / n_mac)
         w_bot[n_std:n_std + n_mac] = side
         h_bot[n_std:n_std + n_mac] = side
-    if n_fill:
-        # Fillers: pinless squares of a few sites, identical on both dies.
-        w_bot[n_std + n_mac:] = 4.0
-        h_bot[n_std + n_mac:] = 4.0
     w_top = 0.8 * w_bot
     h_top = 0.8 * h_bot
-    if n_fill:
-        w_top[n_std + n_mac:] = w_bot[n_std + n_mac:]
-        h_top[n_std + n_mac:] = h_bot[n_std + n_mac:]
     is_macro = np.zeros(n_inst, dtype=np.uint8)
     is_macro[n_std:n_std + n_mac] = 1
     z_fixed = np.zeros(n_inst, dtype=np.uint8)
-    z_fixed[n_std + n_mac:n_std + n_mac + wl.n_filler_fixed] = 1
 
     # --- netlist ---
     deg = _degrees(rng, wl.n_net)
@@ -161,7 +150,7 @@ def make_problem(wl: Workload | str, positions: str = "uniform", origin=(0.0, 0.
     np.cumsum(deg, out=net_start[1:])
     pin_inst = _distinct_pins(rng, net_start, n_std, n_mac, 0.01)
 
-    # --- instance order: interleave macros/fillers among cells ---
+    # --- instance order: interleave macros among cells ---
     perm = rng.permutation(n_inst)  # new index of old instance k is perm[k]
     inv = np.empty_like(perm)
     inv[perm] = np.arange(n_inst)
@@ -218,12 +207,62 @@ def draw_positions(rng: np.random.Generator, prob: dict, kind: str = "uniform"):
         z = np.clip(rng.normal(0.5 * (zlo + zhi), 0.2 * (zhi - zlo), n), zlo, zhi)
     else:
         raise ValueError(kind)
-    zf = prob["z_fixed"].astype(bool)
-    if zf.any():  # z-fixed fillers sit at the centre depth of their die
-        idx = np.nonzero(zf)[0]
-        z[idx[0::2]] = zlo
-        z[idx[1::2]] = zhi
     return x, y, z
+
+
+def append_fillers(prob: dict, fp: dict, seed: int = 0, positions: str = "center") -> dict:
+    """A copy of prob with pinless filler instances appended: fp["n_top"]
+    top z-fixed fillers at depth 3 d_z / 4, fp["n_bot"] bottom z-fixed fillers
+    at d_z / 4, then fp["n_free"] free fillers; footprints fp["w_top"] x
+    fp["h_top"] on the top die and fp["w_bot"] x fp["h_bot"] on the bottom
+    one (a z-fixed filler keeps its own die's footprint in both tables).
+    positions="center": x, y normal about the region's centre (sigma 0.1 of
+    each extent), free fillers' z normal about d_z / 2 (sigma 0.2 of
+    [d_z/4, 3 d_z/4]); "uniform": x, y uniform over the region, free
+    fillers' z uniform in [d_z/4, 3 d_z/4].
+    The counts and footprints are inputs: this draws positions and builds
+    arrays only.  The result carries fp under "fillers" with the first
+    filler's index."""
+    n0 = int(prob["n_inst"])
+    nt, nb, nf = int(fp["n_top"]), int(fp["n_bot"]), int(fp["n_free"])
+    nfill = nt + nb + nf
+    zlo, zhi = depth_range(prob)
+    rng = np.random.default_rng(seed)
+    out = dict(prob)
+
+    def cat(k, vals, dt):
+        return np.concatenate([np.asarray(prob[k], dt), np.asarray(vals, dt)])
+
+    wt, ht = np.full(nfill, float(fp["w_top"])), np.full(nfill, float(fp["h_top"]))
+    wb, hb = np.full(nfill, float(fp["w_bot"])), np.full(nfill, float(fp["h_bot"]))
+    wb[:nt], hb[:nt] = fp["w_top"], fp["h_top"]
+    wt[nt:nt + nb], ht[nt:nt + nb] = fp["w_bot"], fp["h_bot"]
+    out["w_top"], out["h_top"] = cat("w_top", wt, np.float64), cat("h_top", ht, np.float64)
+    out["w_bot"], out["h_bot"] = cat("w_bot", wb, np.float64), cat("h_bot", hb, np.float64)
+    out["is_macro"] = cat("is_macro", np.zeros(nfill), np.uint8)
+    zf0 = prob.get("z_fixed")
+    zf0 = np.zeros(n0, np.uint8) if zf0 is None else np.asarray(zf0, np.uint8)
+    out["z_fixed"] = np.concatenate([zf0, np.ones(nt + nb, np.uint8), np.zeros(nf, np.uint8)])
+    xl, yl, xh, yh = prob["xl"], prob["yl"], prob["xh"], prob["yh"]
+    fz = np.empty(nfill)
+    fz[:nt] = zhi
+    fz[nt:nt + nb] = zlo
+    if positions == "center":
+        fx = np.clip(rng.normal(0.5 * (xl + xh), 0.1 * (xh - xl), nfill), xl, xh)
+        fy = np.clip(rng.normal(0.5 * (yl + yh), 0.1 * (yh - yl), nfill), yl, yh)
+        fz[nt + nb:] = np.clip(rng.normal(0.5 * (zlo + zhi), 0.2 * (zhi - zlo), nf), zlo, zhi)
+    elif positions == "uniform":
+        fx = xl + rng.random(nfill) * (xh - xl)
+        fy = yl + rng.random(nfill) * (yh - yl)
+        fz[nt + nb:] = zlo + rng.random(nf) * (zhi - zlo)
+    else:
+        raise ValueError(positions)
+    for k, v in (("x", fx), ("y", fy), ("z", fz)):
+        if k in prob:
+            out[k] = cat(k, v, np.float64)
+    out["n_inst"] = n0 + nfill
+    out["fillers"] = dict(fp, first=n0)
+    return out
 
 
 def make_batch(count: int = 24, seed: int = 4, n_min: int = 5000, n_max: int = 300_000) -> list:

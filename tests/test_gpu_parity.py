@@ -235,3 +235,27 @@ def test_tiles_cells_200k_fp64(positions):
     p = synth.make_problem("cells_200k", positions=positions)
     _check_fp64(p, p["x"], p["y"], p["z"], maps=True, flags=16)
     _check_fp32(p, p["x"], p["y"], p["z"], flags=16)
+
+
+# ---- dummy fillers (Sec. III-A): pinless instances, z-fixed ones with a zero z-gradient ----
+def _with_fillers(wl, u, positions, seed=5):
+    from oracle import Oracle
+    p = synth.make_problem(wl, positions=positions)
+    fp = Oracle(p).filler_plan(p["z"], *u)  # counts from the oracle's plan
+    return synth.append_fillers(p, fp, seed=seed, positions=positions)
+
+
+@pytest.mark.parametrize("positions", ["center", "uniform"])
+def test_fillers_cells_2k_fp64(positions):
+    q = _with_fillers("cells_2k", (0.8, 0.7), positions)
+    g, r = _check_fp64(q, q["x"], q["y"], q["z"])
+    zf = q["z_fixed"].astype(bool)
+    assert zf.sum() > 1000 and np.all(g["gz"][zf] == 0.0)
+    assert np.abs(g["gx"][q["fillers"]["first"]:]).max() > 0  # fillers feel the field
+
+
+@pytest.mark.parametrize("positions", ["center", "uniform"])
+def test_fillers_cells_2k_fp32(positions):
+    q = _with_fillers("cells_2k", (0.8, 0.7), positions)
+    g, r = _check_fp32(q, q["x"], q["y"], q["z"])
+    assert np.all(g["gz"][q["z_fixed"].astype(bool)] == 0.0)

@@ -88,3 +88,14 @@ def test_fp32_tc_full_size_bench_configuration():
     assert g["res"]["hpwl_d2d"] == pytest.approx(r["hpwl_d2d"], rel=1e-6)
     for k in ("gx", "gy", "gz"):
         assert rel_l2(g[k], r[k]) < 1e-4, (k, rel_l2(g[k], r[k]))
+
+
+def test_fp32_tc_cells_200k_with_fillers():
+    """cells_200k with the fillers of eqs. filler-vol / free-filler-vol at
+    u+ = u- = 0.8 (about 4.3M pinless instances, spread over the region)."""
+    from oracle import Oracle
+    p = synth.make_problem("cells_200k")
+    fp = Oracle(p).filler_plan(p["z"], 0.8, 0.8)
+    q = synth.append_fillers(p, fp, seed=7, positions="uniform")
+    assert q["n_inst"] > 4_000_000
+    _check_tc(q, q["x"], q["y"], q["z"])
