@@ -164,9 +164,11 @@ __global__ void k_macro_corners(int nm, const int *__restrict__ macro_ids,
 }
 
 // ---- eq. def-prefix-sum-3d: inclusive scan along x (one warp per row) ----
-// REV = true scans from the high end (suffix sums).  In/out may alias.
+// REV = true scans from the high end (suffix sums).  In/out may alias (with
+// istride = 1); istride is the input's element stride (4 for one component
+// of the interleaved field map).
 template <typename TI, typename TO, bool REV>
-__global__ void __launch_bounds__(256) k_scan_rows(int rows, int nx, const TI *in, TO *out) {
+__global__ void __launch_bounds__(256) k_scan_rows(int rows, int nx, const TI *in, int istride, TO *out) {
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= rows) return;
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(256) k_scan_rows(int rows, int nx, const TI *i
   for (int base = 0; base < nx; base += 32) {
     const int t = base + lane;
     const int i = REV ? nx - 1 - t : t;
-    TO v = t < nx ? (TO)in[off + i] : (TO)0;
+    TO v = t < nx ? (TO)in[(off + i) * istride] : (TO)0;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const TO u = __shfl_up_sync(0xffffffffu, v, d);
@@ -279,8 +281,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_macro_gather_direct(const int *__restrict__ macro_ids,
                                                              const V4<T> *__restrict__ pos,
                                                              const V4<T> *__restrict__ size, DensC<T> c,
-                                                             const T *__restrict__ ex, const T *__restrict__ ey,
-                                                             const T *__restrict__ ez, double *__restrict__ out) {
+                                                             const V4<T> *__restrict__ e4, double *__restrict__ out) {
   const int m = blockIdx.x, i = macro_ids[m];
   const V4<T> p = pos[i];
   const Box<T> b = inst_box(c, p.x, p.y, p.z, size[i], true);
@@ -298,9 +299,10 @@ __global__ void __launch_bounds__(256) k_macro_gather_direct(const int *__restri
       for (int u = threadIdx.x; u < nxr; u += blockDim.x) {
         const int ii = b0[0] + u;
         const T v = ov_axis(cl[0], chh[0], ii) * oyz;
-        acc[0] += v * ex[row + ii];
-        acc[1] += v * ey[row + ii];
-        acc[2] += v * ez[row + ii];
+        const V4<T> e = e4[row + ii];
+        acc[0] += v * e.x;
+        acc[1] += v * e.y;
+        acc[2] += v * e.z;
       }
     }
   }
@@ -330,8 +332,7 @@ __global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ 
                                                const V4<T> *__restrict__ size,
                                                const uint8_t *__restrict__ flags,
                                                const int *__restrict__ macro_slot, DensC<T> c,
-                                               const T *__restrict__ ex, const T *__restrict__ ey,
-                                               const T *__restrict__ ez,
+                                               const V4<T> *__restrict__ e4,
                                                const double *__restrict__ mgrad,
                                                const V4<T> *__restrict__ acc, FinalC<T> fc,
                                                TO *__restrict__ gx, TO *__restrict__ gy,
@@ -365,9 +366,10 @@ __global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ 
           const size_t row = ((size_t)k * c.ny + j) * c.nx;
           for (int ii = b0[0]; ii <= b1[0]; ++ii) {
             const T v = ov_axis(cl[0], chh[0], ii) * oyz;
-            sx += v * ex[row + ii];
-            sy += v * ey[row + ii];
-            sz += v * ez[row + ii];
+            const V4<T> e = e4[row + ii];  // (E_x, E_y, E_z, -) of one bin: one vector load
+            sx += v * e.x;
+            sy += v * e.y;
+            sz += v * e.z;
           }
         }
       }
@@ -579,8 +581,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ items, const int *__restrict__ nitems,
                                                      const int *__restrict__ start,
                                                      const CellRec<T> *__restrict__ rec, DensC<T> c, TileC tc,
-                                                     const T *__restrict__ ex, const T *__restrict__ ey,
-                                                     const T *__restrict__ ez, const V4<T> *__restrict__ acc,
+                                                     const V4<T> *__restrict__ e4, const V4<T> *__restrict__ acc,
                                                      FinalC<T> fc, V4<T> *__restrict__ g4) {
   extern __shared__ __align__(16) unsigned char fwin_raw[];
   T *wx = reinterpret_cast<T *>(fwin_raw);
@@ -595,10 +596,10 @@ __global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ it
     const int xx = x0 + k % tc.WX, yy = y0 + (k / tc.WX) % tc.WY, zz = k / (tc.WX * tc.WY);
     T a = 0, b2 = 0, d2 = 0;
     if (xx >= 0 && xx < c.nx && yy >= 0 && yy < c.ny) {
-      const size_t id = ((size_t)zz * c.ny + yy) * c.nx + xx;
-      a = ex[id];
-      b2 = ey[id];
-      d2 = ez[id];
+      const V4<T> e = e4[((size_t)zz * c.ny + yy) * c.nx + xx];
+      a = e.x;
+      b2 = e.y;
+      d2 = e.z;
     }
     wx[k] = a;
     wy[k] = b2;
@@ -632,10 +633,10 @@ __global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ it
               sy += v * wy[w];
               sz += v * wz[w];
             } else {
-              const size_t id = ((size_t)k * c.ny + j) * c.nx + ii;
-              sx += v * ex[id];
-              sy += v * ey[id];
-              sz += v * ez[id];
+              const V4<T> e = e4[((size_t)k * c.ny + j) * c.nx + ii];
+              sx += v * e.x;
+              sy += v * e.y;
+              sz += v * e.z;
             }
           }
         }

@@ -150,7 +150,7 @@ extern "C" int place3d_density_map_noalloc(int n_inst, const double *x, const do
     k_noalloc_corners<<<grid_of(n_inst, 256), 256, 0, s>>>(n_inst, a, c, A);
   }
   const int rows = ny * nz;
-  k_scan_rows<long long, long long, false><<<grid_of(rows, 8), 256, 0, s>>>(rows, nx, A, A);
+  k_scan_rows<long long, long long, false><<<grid_of(rows, 8), 256, 0, s>>>(rows, nx, A, 1, A);
   k_scan_cols<long long, false><<<dim3(grid_of(nx, 32), nz), 1024, 0, s>>>(nx, ny, A);
   k_densify<double><<<grid_of((long long)nx * ny, 256), 256, 0, s>>>(nx * ny, nz, q, A, OutPlain<double>{rho});
   return cudaGetLastError() == cudaSuccess ? PLACE3D_OK : PLACE3D_ERR_CUDA;

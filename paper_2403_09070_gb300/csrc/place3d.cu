@@ -90,7 +90,8 @@ struct place3d_handle {
   int *macro_ids = nullptr, *macro_slot = nullptr, *net_start = nullptr, *pin_inst = nullptr;
   long long *q = nullptr, *corner = nullptr;
   void *rho = nullptr, *t1 = nullptr, *t2 = nullptr, *czpsi = nullptr, *szpsi = nullptr;
-  void *xinv = nullptr, *x2 = nullptr, *ex = nullptr, *ey = nullptr, *ez = nullptr;
+  void *xinv = nullptr, *x2 = nullptr;
+  void *e4 = nullptr;  // field map [z][y][x] of (E_x, E_y, E_z, 0) in the handle's real type
   void *mats = nullptr;
   size_t mat_off[5] = {0, 0, 0, 0, 0};  // Fx, Fy, Bx(=[Sx;Cx]), Cy, Sy (elements)
   double *suffix = nullptr, *mgrad = nullptr, *scal = nullptr;
@@ -236,13 +237,14 @@ namespace {
 
 template <typename T>
 GemmProb<T> gp(const void *A, const void *W, void *out, long long abs, long long obs, int batches, int M,
-               int N, int K) {
+               int N, int K, int ostride = 1) {
   GemmProb<T> p;
   p.A = static_cast<const T *>(A);
   p.W = static_cast<const T *>(W);
   p.out = static_cast<T *>(out);
   p.a_bstride = abs;
   p.o_bstride = obs;
+  p.ostride = ostride;
   p.batches = batches;
   p.M = M;
   p.N = N;
@@ -337,9 +339,9 @@ template <typename T> void run_transforms(place3d_handle *h, cudaStream_t s) {
                     gp<T>(h->szpsi, Bx + (size_t)nx * nx, h->x2, pl, pl, nz, ny, nx, nx)},
                    ST_INV);
     launch_gemm<T>(h, s,
-                   {gp<T>(h->xinv, Cy, h->ex, 2 * pl, pl, nz, nx, ny, ny),
-                    gp<T>(as<T>(h->xinv) + pl, Sy, h->ey, 2 * pl, pl, nz, nx, ny, ny),
-                    gp<T>(h->x2, Cy, h->ez, pl, pl, nz, nx, ny, ny)},
+                   {gp<T>(h->xinv, Cy, as<T>(h->e4) + 0, 2 * pl, pl, nz, nx, ny, ny, 4),
+                    gp<T>(as<T>(h->xinv) + pl, Sy, as<T>(h->e4) + 1, 2 * pl, pl, nz, nx, ny, ny, 4),
+                    gp<T>(h->x2, Cy, as<T>(h->e4) + 2, pl, pl, nz, nx, ny, ny, 4)},
                    ST_INV);
   }
 }
@@ -367,8 +369,8 @@ template <typename T, typename TO>
 void launch_final_tiles(place3d_handle *h, cudaStream_t s, const DensC<T> &dc, const FinalC<T> &fc, TO *ox, TO *oy,
                         TO *oz) {
   k_final_tiles<T><<<h->max_items, 256, h->smem_final, s>>>(h->titems, h->tnitems, h->tstart, as<CellRec<T>>(h->trec),
-                                                            dc, h->tcfg, as<T>(h->ex), as<T>(h->ey), as<T>(h->ez),
-                                                            as<V4<T>>(h->acc), fc, as<V4<T>>(h->g4));
+                                                            dc, h->tcfg, as<V4<T>>(h->e4), as<V4<T>>(h->acc), fc,
+                                                            as<V4<T>>(h->g4));
   count_launch(h, ST_FINAL);
   if (h->nm > 0) {
     k_final_macros<T><<<grid_for(h->nm, 128), 128, 0, s>>>(h->nm, h->macro_ids, h->flags_d, h->mgrad,
@@ -433,7 +435,8 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     StageScope sc(h, ST_PREFIX, s);
     const int rows = h->ny * h->nz;
     if (h->nm > 0) {
-      k_scan_rows<long long, long long, false><<<grid_for(rows, 8), 256, 0, s>>>(rows, h->nx, h->corner, h->corner);
+      k_scan_rows<long long, long long, false><<<grid_for(rows, 8), 256, 0, s>>>(rows, h->nx, h->corner, 1,
+                                                                                h->corner);
       count_launch(h, ST_PREFIX);
       k_scan_cols<long long, false><<<dim3(grid_for(h->nx, 32), h->nz), 1024, 0, s>>>(h->nx, h->ny, h->corner);
       count_launch(h, ST_PREFIX);
@@ -454,14 +457,14 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     StageScope sc(h, ST_MACRO_GATHER, s);
     P3D_CUDA(h, cudaMemsetAsync(h->mgrad, 0, sizeof(double) * 3 * h->nm, s));
     k_macro_gather_direct<T><<<dim3(h->nm, 16), 256, 0, s>>>(h->macro_ids, as<V4<T>>(h->pos), as<V4<T>>(h->size),
-                                                            dc, as<T>(h->ex), as<T>(h->ey), as<T>(h->ez), h->mgrad);
+                                                            dc, as<V4<T>>(h->e4), h->mgrad);
     count_launch(h, ST_MACRO_GATHER);
   } else if (h->nm > 0) {
     StageScope sc(h, ST_MACRO_GATHER, s);
     const int rows = h->ny * h->nz;
     for (int comp = 0; comp < 3; ++comp) {
-      const T *E = as<T>(comp == 0 ? h->ex : comp == 1 ? h->ey : h->ez);
-      k_scan_rows<T, double, true><<<grid_for(rows, 8), 256, 0, s>>>(rows, h->nx, E, h->suffix + comp * h->nb);
+      const T *E = as<T>(h->e4) + comp;  // one component of the interleaved field map
+      k_scan_rows<T, double, true><<<grid_for(rows, 8), 256, 0, s>>>(rows, h->nx, E, 4, h->suffix + comp * h->nb);
       count_launch(h, ST_MACRO_GATHER);
     }
     k_scan_cols<double, true><<<dim3(grid_for(h->nx, 32), h->nz * 3), 1024, 0, s>>>(h->nx, h->ny, h->suffix);
@@ -493,12 +496,12 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     } else if (n > 0) {
       if (odt == PLACE3D_F64)
         k_final<T, double><<<grid_for(n, 256), 256, 0, s>>>(n, as<V4<T>>(h->pos), as<V4<T>>(h->size), h->flags_d,
-                                                            h->macro_slot, dc, as<T>(h->ex), as<T>(h->ey), as<T>(h->ez),
+                                                            h->macro_slot, dc, as<V4<T>>(h->e4),
                                                             h->mgrad, as<V4<T>>(h->acc), fc, (double *)ox, (double *)oy,
                                                             (double *)oz);
       else
         k_final<T, float><<<grid_for(n, 256), 256, 0, s>>>(n, as<V4<T>>(h->pos), as<V4<T>>(h->size), h->flags_d,
-                                                           h->macro_slot, dc, as<T>(h->ex), as<T>(h->ey), as<T>(h->ez),
+                                                           h->macro_slot, dc, as<V4<T>>(h->e4),
                                                            h->mgrad, as<V4<T>>(h->acc), fc, (float *)ox, (float *)oy,
                                                            (float *)oz);
       count_launch(h, ST_FINAL);
@@ -538,7 +541,7 @@ void fill_result(const place3d_handle *h, place3d_result *r) {
 void free_all(place3d_handle *h) {
   void *bufs[] = {h->pos,   h->size,  h->off,   h->acc,   h->flags_d, h->macro_ids, h->macro_slot,
                   h->net_start, h->pin_inst, h->q, h->corner, h->rho, h->t1, h->t2, h->czpsi,
-                  h->szpsi, h->xinv, h->x2, h->ex, h->ey, h->ez, h->mats, h->suffix, h->mgrad,
+                  h->szpsi, h->xinv, h->x2, h->e4, h->mats, h->suffix, h->mgrad,
                   h->scal, h->zc, h->gout, h->stage_in, h->check_flag, h->tkey, h->titems,
                   h->tcount, h->tstart, h->tnitems, h->trec, h->g4};
   for (void *b : bufs)
@@ -778,7 +781,7 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
       {(void **)&h->pin_inst, sizeof(int) * (size_t)std::max(h->npin, 1)}, {(void **)&h->q, 8 * nb},
       {(void **)&h->corner, h->nm ? 8 * nb : (size_t)8}, {&h->rho, es * nb}, {&h->t1, es * nb}, {&h->t2, es * nb},
       {&h->czpsi, es * nb}, {&h->szpsi, es * nb}, {&h->xinv, 2 * es * nb}, {&h->x2, es * nb},
-      {&h->ex, es * nb}, {&h->ey, es * nb}, {&h->ez, es * nb},
+      {&h->e4, 4 * es * nb},
       {(void **)&h->suffix, h->nm && !h->macro_direct ? 3 * 8 * nb : (size_t)8}, {(void **)&h->mgrad, (size_t)24 * std::max(h->nm, 1)},
       {(void **)&h->scal, sizeof(double) * S_COUNT}, {(void **)&h->zc, sizeof(ZStageC)},
       {&h->gout, 3 * es * nn}, {(void **)&h->check_flag, sizeof(int)},
@@ -848,8 +851,7 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
   }
   if (h->precision == PLACE3D_FP32_TC) {
     std::string why;
-    h->tc = p3d_tc::create(h->device, h->nx, h->ny, h->nz, h->dx, h->dy, h->dz, h->ex, h->ey, h->ez,
-                           h->zc, &why);
+    h->tc = p3d_tc::create(h->device, h->nx, h->ny, h->nz, h->dx, h->dy, h->dz, h->e4, h->zc, &why);
     if (!h->tc) {
       fail(h, PLACE3D_ERR_UNSUPPORTED, "FP32_TC: " + why);
       return bail(PLACE3D_ERR_UNSUPPORTED);
@@ -990,10 +992,24 @@ int place3d_copy_map(place3d_handle *h, int which, void *dst, int mem) {
   size_t bytes = 0;
   switch (which) {
     case PLACE3D_MAP_RHO_FIXED: src = h->q; bytes = 8 * h->nb; break;
-    case PLACE3D_MAP_EX: src = h->ex; bytes = h->esz * h->nb; break;
-    case PLACE3D_MAP_EY: src = h->ey; bytes = h->esz * h->nb; break;
-    case PLACE3D_MAP_EZ: src = h->ez; bytes = h->esz * h->nb; break;
+    case PLACE3D_MAP_EX:
+    case PLACE3D_MAP_EY:
+    case PLACE3D_MAP_EZ: src = h->e4; bytes = h->esz * h->nb; break;
     default: return fail(h, PLACE3D_ERR_INVALID_ARG, "unknown map");
+  }
+  if (which != PLACE3D_MAP_RHO_FIXED) {
+    // one component of the interleaved (E_x, E_y, E_z, 0) map
+    const int comp = which - PLACE3D_MAP_EX;
+    std::vector<unsigned char> all(4 * bytes), one(bytes);
+    P3D_CUDA(h, cudaStreamSynchronize(h->stream));
+    P3D_CUDA(h, cudaMemcpy(all.data(), h->e4, all.size(), cudaMemcpyDeviceToHost));
+    for (size_t b = 0; b < h->nb; ++b)
+      std::memcpy(one.data() + b * h->esz, all.data() + (4 * b + comp) * h->esz, h->esz);
+    if (mem == PLACE3D_MEM_HOST)
+      std::memcpy(dst, one.data(), bytes);
+    else
+      P3D_CUDA(h, cudaMemcpy(dst, one.data(), bytes, cudaMemcpyHostToDevice));
+    return PLACE3D_OK;
   }
   if (which == PLACE3D_MAP_RHO_FIXED) {
     // the fixed-point map of the last evaluation = cell counts + prefix-summed macro corners

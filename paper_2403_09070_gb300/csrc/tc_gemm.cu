@@ -49,6 +49,7 @@ struct Prob {
   long long plane;    // elements from the hi plane to the lo plane
   long long o_bstride;
   int M, N, K, batches, tiles_m, tiles_n, kind;
+  int ostride;        // OUT_F32: element stride of the output (4 = one component of an interleaved map)
 };
 
 struct Group {
@@ -261,7 +262,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Grou
       if (P.kind == OUT_F32) {
         float *o = static_cast<float *>(P.out);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) o[base + (long long)(n0 + c0 + j) * P.M] = __uint_as_float(v[j]);
+        for (int j = 0; j < 16; ++j)
+          o[(base + (long long)(n0 + c0 + j) * P.M) * P.ostride] = __uint_as_float(v[j]);
       } else {
         __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(P.out);
 #pragma unroll
@@ -351,6 +353,7 @@ struct ProbSpec {
   void *out;
   long long o_bstride, o_plane;
   int kind, batches, M, N, K;
+  int ostride;  // 0 or 1: contiguous
 };
 
 static bool make_group(Group *g, std::initializer_list<ProbSpec> specs, int *err, std::string *why) {
@@ -376,6 +379,7 @@ static bool make_group(Group *g, std::initializer_list<ProbSpec> specs, int *err
     p.tiles_m = s.M / BM;
     p.tiles_n = s.N / BN;
     p.kind = s.kind;
+    p.ostride = s.ostride > 1 ? s.ostride : 1;
     g->tile_start[i] = tiles;
     tiles += s.batches * p.tiles_m * p.tiles_n;
     g->count++;
@@ -447,8 +451,8 @@ static bool upload_split(__nv_bfloat16 **dst, const std::vector<double> &v, std:
   return cudaMemcpy(*dst, h.data(), h.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess;
 }
 
-TcPlan *create(int device, int nx, int ny, int nz, double dx, double dy, double dz, void *ex, void *ey, void *ez,
-               const ZStageC *zc, std::string *why) {
+TcPlan *create(int device, int nx, int ny, int nz, double dx, double dy, double dz, void *e4, const ZStageC *zc,
+               std::string *why) {
   (void)dz;
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess || prop.major != 10 || prop.minor != 3) {
@@ -509,11 +513,14 @@ TcPlan *create(int device, int nx, int ny, int nz, double dx, double dy, double 
                     {{p->cz, pl, snb, p->Wbx, 2 * wx, p->xinv, 2 * pl, 2 * snb, OUT_SPLIT, nz, ny, 2 * nx, nx},
                      {p->sz, pl, snb, p->Wbx + wx, 2 * wx, p->x2, pl, snb, OUT_SPLIT, nz, ny, nx, nx}},
                     p->err, why);
-  if (ok)  // y inverse: E_x = C_y (S_x C_z psi), E_y = S_y (C_x C_z psi), E_z = C_y (C_x S_z psi)
+  // y inverse: E_x = C_y (S_x C_z psi), E_y = S_y (C_x C_z psi), E_z = C_y (C_x S_z psi), written
+  // interleaved into e4[z][y][x] = (E_x, E_y, E_z, -) so the gather reads one vector per bin
+  float *e = static_cast<float *>(e4);
+  if (ok)
     ok = make_group(&p->g_iy,
-                    {{p->xinv, 2 * pl, 2 * snb, p->Wcy, wy, ex, pl, 0, OUT_F32, nz, nx, ny, ny},
-                     {p->xinv + pl, 2 * pl, 2 * snb, p->Wsy, wy, ey, pl, 0, OUT_F32, nz, nx, ny, ny},
-                     {p->x2, pl, snb, p->Wcy, wy, ez, pl, 0, OUT_F32, nz, nx, ny, ny}},
+                    {{p->xinv, 2 * pl, 2 * snb, p->Wcy, wy, e + 0, pl, 0, OUT_F32, nz, nx, ny, ny, 4},
+                     {p->xinv + pl, 2 * pl, 2 * snb, p->Wsy, wy, e + 1, pl, 0, OUT_F32, nz, nx, ny, ny, 4},
+                     {p->x2, pl, snb, p->Wcy, wy, e + 2, pl, 0, OUT_F32, nz, nx, ny, ny, 4}},
                     p->err, why);
   if (!ok) {
     free_plan(p);

@@ -14,15 +14,16 @@ namespace p3d_tc {
 struct TcPlan;
 
 // Build the plan for an nx x ny x nz grid (nx, ny multiples of 128) on the
-// current device; ex/ey/ez are the handle's FP32 field maps (outputs of
-// inverse()), zc the device copy of the z-stage constants.  Returns NULL and
-// sets *why when the device or the grid is not supported.
-TcPlan *create(int device, int nx, int ny, int nz, double dx, double dy, double dz, void *ex, void *ey,
-               void *ez, const p3d::ZStageC *zc, std::string *why);
+// current device; e4 is the handle's FP32 field map [z][y][x] of (E_x, E_y,
+// E_z, unused) (output of inverse()), zc the device copy of the z-stage
+// constants.  Returns NULL and sets *why when the device or the grid is not
+// supported.
+TcPlan *create(int device, int nx, int ny, int nz, double dx, double dy, double dz, void *e4,
+               const p3d::ZStageC *zc, std::string *why);
 // rho (cells + macro corners, z prefix) -> split-BF16 planes of the input.
 void densify(TcPlan *p, cudaStream_t s, int nxy, int nz, const long long *q, const long long *corner);
 // Forward x and y products; z stage (scaling, energy, z transforms);
-// inverse x and y products into ex/ey/ez.  Each returns its launch count.
+// inverse x and y products into the interleaved field map e4.  Each returns its launch count.
 int forward(TcPlan *p, cudaStream_t s);
 int zstage(TcPlan *p, cudaStream_t s, double *esum);
 int inverse(TcPlan *p, cudaStream_t s);

@@ -15,6 +15,7 @@ template <typename T> struct GemmProb {
   const T *W;
   T *out;
   long long a_bstride, o_bstride;  // elements between batches
+  int ostride;                     // element stride of the output (4: one component of an interleaved map)
   int batches, M, N, K;
   int tiles_m, tiles_n;            // filled by the launcher
 };
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmGroup<T> g) {
   const int r = tile - b * per_batch;
   const int m0 = (r % P.tiles_m) * kBM, n0 = (r / P.tiles_m) * kBN;
   const T *A = P.A + (long long)b * P.a_bstride;
-  T *O = P.out + (long long)b * P.o_bstride;
+  T *O = P.out + (long long)b * P.o_bstride * P.ostride;
   const int t = threadIdx.x;
   const int tm = t & 15, tn = t >> 4;
   T acc[4][4];
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmGroup<T> g) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int m = m0 + tm * 4 + i;
-      if (m < P.M) O[(long long)n * P.M + m] = acc[i][j];
+      if (m < P.M) O[((long long)n * P.M + m) * P.ostride] = acc[i][j];
     }
   }
 }
