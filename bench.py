@@ -91,43 +91,63 @@ def job_throughput(world: int, steps: int, total_ms: float) -> float:
 
 # ---------------------------------------------------------------- clocks
 class Clocks:
-    """nvidia-smi samples (SM clock, throttle reasons) during the timed region."""
+    """nvidia-smi samples (SM clock, throttle reasons) during the timed region.
+
+    The sampler polls every 10 ms and is running (first sample seen) before
+    start() returns; only samples that arrive between start() and stop()
+    count.  A timed region shorter than the polling period can still see no
+    sample: then the first sample after it is reported, marked "after"."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 10
 
     def __init__(self, dev: int):
         self.dev = dev
         self.p = None
-        self.lines = []
+        self.lines = []  # (arrival time, line)
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                       "-lms", str(self.PERIOD_MS), "-i", str(self.dev)], stdout=subprocess.PIPE,
                                       stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            deadline = time.time() + 10.0
+            while not self.lines and time.time() < deadline and self.p.poll() is None:
+                time.sleep(0.005)
         except OSError:
             self.p = None
+        self.t0 = time.time()
 
     def _read(self):
         for line in self.p.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
     def stop(self) -> dict:
+        self.t1 = time.time()
         if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        deadline = self.t1 + 1.0
+        while time.time() < deadline and not any(t > self.t1 for t, _ in self.lines):
+            time.sleep(0.005)
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.p.kill()
         self.t.join(timeout=5)
+        inside = [ln for t, ln in self.lines if self.t0 <= t <= self.t1]
+        where = "during"
+        if not inside:
+            inside = [ln for t, ln in self.lines if t > self.t1][:1]
+            where = "after"
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in inside:
             f = [v.strip() for v in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -140,7 +160,8 @@ class Clocks:
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "sampled": where,
+                "period_ms": self.PERIOD_MS}
 
 
 # ---------------------------------------------------------------- oracle legs (CPU)

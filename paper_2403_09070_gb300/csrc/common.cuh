@@ -49,6 +49,11 @@ __device__ __forceinline__ long long r_rint(double a) { return __double2ll_rn(a)
 // WA terms are); FP64 mode the full-precision one.
 __device__ __forceinline__ float r_exp(float a) { return __expf(a); }
 __device__ __forceinline__ double r_exp(double a) { return exp(a); }
+// 1/a for the wirelength's WA sums (a in [1, #pins]): the fast approximate
+// division in FP32 (a few ulp, far inside the FP32 path's tolerance), IEEE
+// division in FP64.
+__device__ __forceinline__ float r_rcp(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ double r_rcp(double a) { return 1.0 / a; }
 
 template <typename T> __device__ __forceinline__ T big();
 template <> __device__ __forceinline__ float big<float>() { return 3.0e38f; }

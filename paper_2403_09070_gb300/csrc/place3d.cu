@@ -283,12 +283,13 @@ void launch_wl(place3d_handle *h, const Bucket &b, int G, int PPL, cudaStream_t 
                                                         acc, h->scal);
     return;
   }
-  const int blocks = grid_for((long long)b.count * G, 256);
-#define P3D_WL(GG, PP)                                                                                     \
-  if (G == GG && PPL == PP) {                                                                              \
-    k_wl_group<T, GG, PP><<<blocks, 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, \
-                                                 acc, h->scal);                                            \
-    return;                                                                                                \
+  constexpr int BS = wl_block<T>();
+  const int blocks = grid_for((long long)b.count * G, BS);
+#define P3D_WL(GG, PP)                                                                                    \
+  if (G == GG && PPL == PP) {                                                                             \
+    k_wl_group<T, GG, PP><<<blocks, BS, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, \
+                                                acc, h->scal);                                            \
+    return;                                                                                               \
   }
   P3D_WL(1, 2) P3D_WL(1, 4) P3D_WL(2, 2) P3D_WL(4, 1) P3D_WL(2, 4) P3D_WL(8, 1) P3D_WL(4, 4)
   P3D_WL(16, 1) P3D_WL(8, 4) P3D_WL(32, 1) P3D_WL(16, 4) P3D_WL(32, 2) P3D_WL(32, 4)

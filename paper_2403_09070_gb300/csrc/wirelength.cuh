@@ -23,19 +23,18 @@ template <typename T> struct WlC {
 };
 
 template <typename T> struct Pin {
-  int inst, slot;
+  int inst;
   bool top;
   T px, py, pz;  // pin on its current die
   T qx, qy;      // the same pin if its instance were on the other die
 };
 
 template <typename T>
-__device__ __forceinline__ Pin<T> load_pin(int p, int slot, const int *__restrict__ pin_inst,
+__device__ __forceinline__ Pin<T> load_pin(int p, const int *__restrict__ pin_inst,
                                            const V4<T> *__restrict__ off,
                                            const V4<T> *__restrict__ pos, const WlC<T> &c) {
   Pin<T> q;
   q.inst = __ldg(pin_inst + p);
-  q.slot = slot;
   const V4<T> o = off[p];  // (bot x, bot y, top x, top y)
   const V4<T> s = pos[q.inst];
   q.top = s.z > c.zmid;
@@ -90,13 +89,14 @@ template <typename T> struct NetExt {
     zmx = -big<T>();
     zmn = big<T>();
   }
-  __device__ __forceinline__ void add(const Pin<T> &p) {
+  // slot: the pin's index within its net (identifies the extreme pins)
+  __device__ __forceinline__ void add(const Pin<T> &p, int slot) {
     if (p.top) {
-      e[0][1].add(p.px, p.slot);
-      e[1][1].add(p.py, p.slot);
+      e[0][1].add(p.px, slot);
+      e[1][1].add(p.py, slot);
     } else {
-      e[0][0].add(p.px, p.slot);
-      e[1][0].add(p.py, p.slot);
+      e[0][0].add(p.px, slot);
+      e[1][0].add(p.py, slot);
     }
     ntop += p.top ? 1 : 0;
     n += 1;
@@ -231,8 +231,8 @@ __device__ __forceinline__ AxisNet<T> axis_net(int a, const NetExt<T> &X, const 
       const Ext<T> &e = X.e[a][s];
       mxA = e.mx1 > mxA ? e.mx1 : mxA;
       mnA = e.mn1 < mnA ? e.mn1 : mnA;
-      r.iSs[s] = T(1) / S.v[a][s][0];
-      r.iSm[s] = T(1) / S.v[a][s][2];
+      r.iSs[s] = r_rcp(S.v[a][s][0]);
+      r.iSm[s] = r_rcp(S.v[a][s][2]);
       r.Ms[s] = S.v[a][s][1] * r.iSs[s];
       r.ms[s] = S.v[a][s][3] * r.iSm[s];
       p[s] = r.Ms[s] - r.ms[s];
@@ -252,8 +252,8 @@ __device__ __forceinline__ AxisNet<T> axis_net(int a, const NetExt<T> &X, const 
       NM += S.v[a][s][3] * r.h[s];
     }
   }
-  r.iSP = T(1) / SP;
-  r.iSM = T(1) / SM;
+  r.iSP = r_rcp(SP);
+  r.iSM = r_rcp(SM);
   r.M = NP * r.iSP;
   r.m = NM * r.iSM;
   const T pall = r.M - r.m;
@@ -276,8 +276,8 @@ __device__ __forceinline__ NetScal<T> net_scalars(const NetExt<T> &X, const Sums
   NetScal<T> r;
   r.ax[0] = axis_net(0, X, S, c);
   r.ax[1] = axis_net(1, X, S, c);
-  r.izS1 = T(1) / S.z[0];
-  r.izS2 = T(1) / S.z[2];
+  r.izS1 = r_rcp(S.z[0]);
+  r.izS2 = r_rcp(S.z[2]);
   r.zM = S.z[1] * r.izS1;
   r.zm = S.z[3] * r.izS2;
   r.pz = r.zM - r.zm;
@@ -317,7 +317,7 @@ __device__ __forceinline__ T moved_sel(bool s, const Ext<T> &e1, const Ext<T> &e
 
 // Per-pin outputs (gx, gy, fd, waz) -> instance accumulators.
 template <typename T>
-__device__ __forceinline__ void pin_outputs(const Pin<T> &p, const T (&ex)[6], const NetExt<T> &X,
+__device__ __forceinline__ void pin_outputs(const Pin<T> &p, int slot, const T (&ex)[6], const NetExt<T> &X,
                                             const Sums<T> &S, const NetScal<T> &N,
                                             const WlC<T> &c, V4<T> *__restrict__ acc) {
   const bool s = p.top;
@@ -337,8 +337,8 @@ __device__ __forceinline__ void pin_outputs(const Pin<T> &p, const T (&ex)[6], c
   }
   const T gz = wa_grad(p.pz, ex[4], N.izS1, N.zM, ex[5], N.izS2, N.zm, c.inv_gz);
   const int ns = s ? X.ntop : X.n - X.ntop, no = X.n - ns;
-  const T wm = moved_sel(s, X.e[0][1], X.e[0][0], ns, no, p.slot, p.qx) +
-               moved_sel(s, X.e[1][1], X.e[1][0], ns, no, p.slot, p.qy);
+  const T wm = moved_sel(s, X.e[0][1], X.e[0][0], ns, no, slot, p.qx) +
+               moved_sel(s, X.e[1][1], X.e[1][0], ns, no, slot, p.qy);
   const T fd = c.fd_scale * (s ? (N.wcur - wm) : (wm - N.wcur));
   acc_add(acc + p.inst, g[0], g[1], fd, gz);
 }
@@ -353,7 +353,7 @@ template <typename T>
 __device__ __forceinline__ T wa_pair(T va, T vb, T inv_g, T &ga) {
   const T L = va > vb ? va - vb : vb - va;
   const T e = r_exp(-L * inv_g);
-  const T i1e = T(1) / (T(1) + e);
+  const T i1e = r_rcp(T(1) + e);
   const T th = (T(1) - e) * i1e;
   const T der = th + T(2) * L * inv_g * e * i1e * i1e;
   ga = va >= vb ? der : -der;
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(256) k_wl_pair(int net0, int nnets, const int 
   T vals[4] = {0, 0, 0, 0};
   if (t < nnets) {
     const int s0 = __ldg(net_start + net0 + t);
-    const Pin<T> a = load_pin(s0, 0, pin_inst, off, pos, c), b = load_pin(s0 + 1, 1, pin_inst, off, pos, c);
+    const Pin<T> a = load_pin(s0, pin_inst, off, pos, c), b = load_pin(s0 + 1, pin_inst, off, pos, c);
     T gx, gy, gz;
     const T wx = wa_pair(a.px, b.px, c.inv_g, gx);
     const T wy = wa_pair(a.py, b.py, c.inv_g, gy);
@@ -391,14 +391,96 @@ __global__ void __launch_bounds__(256) k_wl_pair(int net0, int nnets, const int 
 }
 
 // ---- nets of degree <= G*PPL, one group of G lanes per net ----
+// Block size of the group kernel: 128 threads (FP32), 64 (FP64).
+template <typename T> __host__ __device__ constexpr int wl_block() { return sizeof(T) == 8 ? 64 : 128; }
+
+// Per-net values staged in shared memory, one column per group (structure of
+// arrays: lanes of different groups read consecutive words, lanes of one
+// group read the same word).  Staging them keeps the per-pin loop's register
+// footprint to the pins themselves, which doubles the resident warps.
+enum : int {
+  F_EXT = 0,    // [(a*2+s)*4 + {0: max1, 1: max2, 2: min1, 3: min2}], a = axis, s = side (0 bottom, 1 top)
+  F_Z = 16,     // +0 max z, +1 min z (the z shifts)
+  F_COEF = 18,  // [(a*2+s)*4 + {A, B, C, D}]: dW/dv = e+ A (1 + (v-B)/g) - e- C (1 - (v-D)/g)
+  F_ZC = 34,    // +0 1/S+z, +1 M_z, +2 1/S-z, +3 m_z
+  F_WCUR = 38,  // exact W_Bi of the net (eq. wl-obj)
+  F_COUNT = 39
+};
+enum : int { I_ARG = 0, I_NTOP = 8, I_N = 9, I_COUNT = 10 };  // I_ARG + (a*2+s)*2 + {argmax, argmin}
+
+template <typename T, int GR> struct WlShared {
+  T f[F_COUNT][GR];
+  int i[I_COUNT][GR];
+};
+
+template <typename T, int GR>
+__device__ __forceinline__ void stage_ext(WlShared<T, GR> &sh, int grp, const NetExt<T> &X) {
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const Ext<T> &e = X.e[a][s];
+      const int b = (a * 2 + s) * 4;
+      sh.f[F_EXT + b + 0][grp] = e.mx1;
+      sh.f[F_EXT + b + 1][grp] = e.mx2;
+      sh.f[F_EXT + b + 2][grp] = e.mn1;
+      sh.f[F_EXT + b + 3][grp] = e.mn2;
+      sh.i[I_ARG + (a * 2 + s) * 2 + 0][grp] = e.amx;
+      sh.i[I_ARG + (a * 2 + s) * 2 + 1][grp] = e.amn;
+    }
+  sh.f[F_Z + 0][grp] = X.zmx;
+  sh.f[F_Z + 1][grp] = X.zmn;
+  sh.i[I_NTOP][grp] = X.ntop;
+  sh.i[I_N][grp] = X.n;
+}
+
+// Exponentials of one pin with the shifts read from the staged extremes.
+template <typename T, int GR>
+__device__ __forceinline__ void pin_exps_sh(const Pin<T> &p, const WlShared<T, GR> &sh, int grp, const WlC<T> &c,
+                                            T (&ex)[6]) {
+  const int s = p.top ? 1 : 0;
+  const T xmx = sh.f[F_EXT + (0 + s) * 4 + 0][grp], xmn = sh.f[F_EXT + (0 + s) * 4 + 2][grp];
+  const T ymx = sh.f[F_EXT + (2 + s) * 4 + 0][grp], ymn = sh.f[F_EXT + (2 + s) * 4 + 2][grp];
+  ex[0] = r_exp((p.px - xmx) * c.inv_g);
+  ex[1] = r_exp((xmn - p.px) * c.inv_g);
+  ex[2] = r_exp((p.py - ymx) * c.inv_g);
+  ex[3] = r_exp((ymn - p.py) * c.inv_g);
+  ex[4] = r_exp((p.pz - sh.f[F_Z + 0][grp]) * c.inv_gz);
+  ex[5] = r_exp((sh.f[F_Z + 1][grp] - p.pz) * c.inv_gz);
+}
+
+// W_e on one axis after the pin (side s, index slot) moves to the other die
+// at coordinate v: moved_sel with the extremes read from shared memory.
+template <typename T, int GR>
+__device__ __forceinline__ T moved_sh(const WlShared<T, GR> &sh, int grp, int a, int s, int ns, int no, int slot,
+                                      T v) {
+  const int bs = F_EXT + (a * 2 + s) * 4, bo = F_EXT + (a * 2 + (1 - s)) * 4;
+  const T smx1 = sh.f[bs + 0][grp], smx2 = sh.f[bs + 1][grp], smn1 = sh.f[bs + 2][grp], smn2 = sh.f[bs + 3][grp];
+  const int samx = sh.i[I_ARG + (a * 2 + s) * 2 + 0][grp], samn = sh.i[I_ARG + (a * 2 + s) * 2 + 1][grp];
+  const T omx = sh.f[bo + 0][grp], omn = sh.f[bo + 2][grp];
+  const bool keep = ns > 1;
+  const T smax = slot == samx ? smx2 : smx1, smin = slot == samn ? smn2 : smn1;
+  const T ps = keep ? smax - smin : T(0);
+  const T omax = no ? (omx > v ? omx : v) : v;
+  const T omin = no ? (omn < v ? omn : v) : v;
+  const T po = omax - omin;
+  const T amax = keep ? (smax > omax ? smax : omax) : omax;
+  const T amin = keep ? (smin < omin ? smin : omin) : omin;
+  const T hall = amax - amin;
+  return hall > ps + po ? hall : ps + po;
+}
+
 template <typename T, int G, int PPL>
-__global__ void __launch_bounds__(256) k_wl_group(int net0, int nnets, const int *__restrict__ net_start,
-                                                  const int *__restrict__ pin_inst,
-                                                  const V4<T> *__restrict__ off,
-                                                  const V4<T> *__restrict__ pos, WlC<T> c,
-                                                  V4<T> *__restrict__ acc, double *__restrict__ scal) {
+__global__ void __launch_bounds__(wl_block<T>()) k_wl_group(int net0, int nnets, const int *__restrict__ net_start,
+                                                            const int *__restrict__ pin_inst,
+                                                            const V4<T> *__restrict__ off,
+                                                            const V4<T> *__restrict__ pos, WlC<T> c,
+                                                            V4<T> *__restrict__ acc, double *__restrict__ scal) {
+  constexpr int GR = wl_block<T>() / G;  // groups (nets) per block
+  __shared__ WlShared<T, GR> sh;
   const int lane = threadIdx.x & (G - 1);
-  const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int grp = threadIdx.x / G;
+  const int gid = blockIdx.x * GR + grp;
   const bool valid = gid < nnets;
   int s0 = 0, d = 0;
   if (valid) {
@@ -407,44 +489,103 @@ __global__ void __launch_bounds__(256) k_wl_group(int net0, int nnets, const int
   }
   Pin<T> pin[PPL];
   bool has[PPL];
-  NetExt<T> X;
-  X.init();
+  {
+    NetExt<T> X;
+    X.init();
 #pragma unroll
-  for (int r = 0; r < PPL; ++r) {
-    const int k = lane + r * G;
-    has[r] = k < d;
-    if (has[r]) {
-      pin[r] = load_pin(s0 + k, k, pin_inst, off, pos, c);
-      X.add(pin[r]);
+    for (int r = 0; r < PPL; ++r) {
+      const int k = lane + r * G;
+      has[r] = k < d;
+      if (has[r]) {
+        pin[r] = load_pin(s0 + k, pin_inst, off, pos, c);
+        X.add(pin[r], k);
+      }
     }
+    X.template shfl_reduce<G>();
+    if (lane == 0) stage_ext(sh, grp, X);
   }
-  X.template shfl_reduce<G>();
-  Sums<T> S;
-  S.init();
-#pragma unroll
-  for (int r = 0; r < PPL; ++r)
-    if (has[r]) {
-      T ex[6];
-      pin_exps(pin[r], X, c, ex);
-      sums_add(S, pin[r], ex);
-    }
-  S.template shfl_reduce<G>();
+  __syncwarp();
   T vals[4] = {0, 0, 0, 0};
-  if (d >= 2) {
-    const NetScal<T> N = net_scalars(X, S, c);
+  {
+    Sums<T> S;
+    S.init();
 #pragma unroll
     for (int r = 0; r < PPL; ++r)
       if (has[r]) {
-        T ex[6];  // recomputed: keeping them live across the reductions costs registers
-        pin_exps(pin[r], X, c, ex);
-        pin_outputs(pin[r], ex, X, S, N, c, acc);
+        T ex[6];
+        pin_exps_sh(pin[r], sh, grp, c, ex);
+        sums_add(S, pin[r], ex);
       }
-    if (lane == 0) {
+    S.template shfl_reduce<G>();
+    if (d >= 2 && lane == 0) {
+      // net scalars (eq. wl-obj branch, WA averages), staged as per-side coefficients
+      NetExt<T> X;
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          Ext<T> &e = X.e[a][q];
+          const int b = F_EXT + (a * 2 + q) * 4;
+          e.mx1 = sh.f[b + 0][grp];
+          e.mx2 = sh.f[b + 1][grp];
+          e.mn1 = sh.f[b + 2][grp];
+          e.mn2 = sh.f[b + 3][grp];
+          e.amx = e.amn = 0;
+        }
+      X.zmx = sh.f[F_Z + 0][grp];
+      X.zmn = sh.f[F_Z + 1][grp];
+      X.ntop = sh.i[I_NTOP][grp];
+      X.n = sh.i[I_N][grp];
+      const NetScal<T> N = net_scalars(X, S, c);
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const AxisNet<T> &A = N.ax[a];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int b = F_COEF + (a * 2 + q) * 4;
+          sh.f[b + 0][grp] = A.all ? A.f[q] * A.iSP : A.iSs[q];
+          sh.f[b + 1][grp] = A.all ? A.M : A.Ms[q];
+          sh.f[b + 2][grp] = A.all ? A.h[q] * A.iSM : A.iSm[q];
+          sh.f[b + 3][grp] = A.all ? A.m : A.ms[q];
+        }
+      }
+      sh.f[F_ZC + 0][grp] = N.izS1;
+      sh.f[F_ZC + 1][grp] = N.zM;
+      sh.f[F_ZC + 2][grp] = N.izS2;
+      sh.f[F_ZC + 3][grp] = N.zm;
+      sh.f[F_WCUR][grp] = N.wcur;
       vals[0] = N.ax[0].what + N.ax[1].what;
       vals[1] = N.pz;
       vals[2] = N.wcur;
       vals[3] = (X.ntop > 0 && X.ntop < X.n) ? T(1) : T(0);
     }
+  }
+  __syncwarp();
+  if (d >= 2) {
+    const int ntop = sh.i[I_NTOP][grp], n = sh.i[I_N][grp];
+    const T wcur = sh.f[F_WCUR][grp];
+#pragma unroll
+    for (int r = 0; r < PPL; ++r)
+      if (has[r]) {
+        const Pin<T> &p = pin[r];
+        T ex[6];  // recomputed: keeping them live across the reductions costs registers
+        pin_exps_sh(p, sh, grp, c, ex);
+        const int s = p.top ? 1 : 0;
+        T g[2];
+        const T v[2] = {p.px, p.py};
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const int b = F_COEF + (a * 2 + s) * 4;
+          const T A = sh.f[b + 0][grp], B = sh.f[b + 1][grp], C = sh.f[b + 2][grp], D = sh.f[b + 3][grp];
+          g[a] = (ex[2 * a] * A) * (T(1) + (v[a] - B) * c.inv_g) - (ex[2 * a + 1] * C) * (T(1) - (v[a] - D) * c.inv_g);
+        }
+        const T gz = wa_grad(p.pz, ex[4], sh.f[F_ZC + 0][grp], sh.f[F_ZC + 1][grp], ex[5], sh.f[F_ZC + 2][grp],
+                             sh.f[F_ZC + 3][grp], c.inv_gz);
+        const int ns = s ? ntop : n - ntop, no = n - ns, slot = lane + r * G;
+        const T wm = moved_sh(sh, grp, 0, s, ns, no, slot, p.qx) + moved_sh(sh, grp, 1, s, ns, no, slot, p.qy);
+        const T fd = c.fd_scale * (s ? (wcur - wm) : (wm - wcur));
+        acc_add(acc + p.inst, g[0], g[1], fd, gz);
+      }
   }
   block_sum_atomic<4>(vals, scal + S_WL_BI);
 }
@@ -463,7 +604,7 @@ __global__ void __launch_bounds__(256) k_wl_block(int net0, const int *__restric
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   NetExt<T> X;
   X.init();
-  for (int k = tid; k < d; k += blockDim.x) X.add(load_pin(s0 + k, k, pin_inst, off, pos, c));
+  for (int k = tid; k < d; k += blockDim.x) X.add(load_pin(s0 + k, pin_inst, off, pos, c), k);
   X.template shfl_reduce<32>();
   if (lane == 0) sx[warp] = X;
   __syncthreads();
@@ -475,7 +616,7 @@ __global__ void __launch_bounds__(256) k_wl_block(int net0, const int *__restric
   Sums<T> S;
   S.init();
   for (int k = tid; k < d; k += blockDim.x) {
-    const Pin<T> p = load_pin(s0 + k, k, pin_inst, off, pos, c);
+    const Pin<T> p = load_pin(s0 + k, pin_inst, off, pos, c);
     T ex[6];
     pin_exps(p, X, c, ex);
     sums_add(S, p, ex);
@@ -490,10 +631,10 @@ __global__ void __launch_bounds__(256) k_wl_block(int net0, const int *__restric
   S = ss[0];
   const NetScal<T> N = net_scalars(X, S, c);
   for (int k = tid; k < d; k += blockDim.x) {
-    const Pin<T> p = load_pin(s0 + k, k, pin_inst, off, pos, c);
+    const Pin<T> p = load_pin(s0 + k, pin_inst, off, pos, c);
     T ex[6];
     pin_exps(p, X, c, ex);
-    pin_outputs(p, ex, X, S, N, c, acc);
+    pin_outputs(p, k, ex, X, S, N, c, acc);
   }
   if (tid == 0) {
     atomicAdd(scal + S_WL_BI, (double)N.ax[0].what + (double)N.ax[1].what);
