@@ -39,6 +39,7 @@ class Problem(C.Structure):
         ("xl", C.c_double), ("yl", C.c_double), ("xh", C.c_double), ("yh", C.c_double),
         ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
         ("gamma", C.c_double), ("gamma_z", C.c_double), ("alpha", C.c_double), ("lam", C.c_double),
+        ("is_hbt", C.c_void_p), ("mode", C.c_int), ("lam_layer", C.c_double * 3),
     ]
 
 
@@ -66,6 +67,7 @@ def lib():
         L.orc_wirelength.argtypes = [P, vp, vp, vp, C.c_int, vp, vp, vp, vp, vp]
         L.orc_eval.argtypes = [P, vp, vp, vp, C.c_int, C.c_int, vp, vp, vp, vp]
         L.orc_filler_plan.argtypes = [P, vp, d, d, vp]
+        L.orc_eval2d.argtypes = [P, vp, vp, vp, C.c_int, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -85,6 +87,8 @@ class Oracle:
             z_fixed=np.ascontiguousarray(prob["z_fixed"], dtype=np.uint8),
             net_start=np.ascontiguousarray(prob["net_start"], dtype=np.int32),
             pin_inst=np.ascontiguousarray(prob["pin_inst"], dtype=np.int32),
+            is_hbt=(np.ascontiguousarray(prob["is_hbt"], dtype=np.uint8) if prob.get("is_hbt") is not None
+                    else None),
             **{k: f64(k) for k in ("w_bot", "h_bot", "w_top", "h_top",
                                    "off_bx", "off_by", "off_tx", "off_ty")})
         k = self._keep
@@ -96,7 +100,9 @@ class Oracle:
             _ptr(k["off_bx"]), _ptr(k["off_by"]), _ptr(k["off_tx"]), _ptr(k["off_ty"]),
             float(prob["xl"]), float(prob["yl"]), float(prob["xh"]), float(prob["yh"]),
             int(prob["nx"]), int(prob["ny"]), int(prob["nz"]),
-            float(prob["gamma"]), float(prob.get("gamma_z", 0.0)), 0.0, float(prob["lam"]))
+            float(prob["gamma"]), float(prob.get("gamma_z", 0.0)), 0.0, float(prob["lam"]),
+            _ptr(k["is_hbt"]), int(prob.get("mode", 0)),
+            (C.c_double * 3)(*[float(v) for v in prob.get("lam_layer", (prob["lam"],) * 3)]))
         g = self.geometry()
         self.s.alpha = float(alpha) if alpha is not None else self.alpha_default()
         self.nb = int(prob["nx"]) * int(prob["ny"]) * int(prob["nz"])
@@ -144,6 +150,20 @@ class Oracle:
         d.update(n_top=int(o[8]), n_bot=int(o[9]), n_free=int(o[10]))
         return d
 
+    def eval2d(self, x, y, z, density_mode: int = 1, grads: bool = True) -> dict:
+        """Multi-die 2D objective and gradient (eq. 2d-place); the problem
+        has mode = 1, nz = 3 and optionally is_hbt / lam_layer."""
+        x, y, z = self._xyz(x, y, z)
+        out = np.zeros(7)
+        gx = np.zeros(self.n) if grads else None
+        gy = np.zeros(self.n) if grads else None
+        lib().orc_eval2d(C.byref(self.s), _ptr(x), _ptr(y), _ptr(z), int(density_mode), _ptr(out),
+                         _ptr(gx), _ptr(gy))
+        keys = ("obj", "wl", "e_bot", "e_top", "e_hbt", "hpwl_d2d", "n_cross")
+        r = dict(zip(keys, out.tolist()))
+        r["gx"], r["gy"] = gx, gy
+        return r
+
     def density_direct(self, x, y, z):
         x, y, z = self._xyz(x, y, z)
         rho = np.zeros(self.shape)
@@ -176,10 +196,12 @@ class Oracle:
     def poisson(self, rho):
         rho = np.ascontiguousarray(rho, dtype=np.float64)
         outs = {k: np.zeros(self.shape) for k in ("a", "psi", "phi", "ex", "ey", "ez")}
-        e = np.zeros(1)
+        e = np.zeros(max(self.shape[0], 1))
         lib().orc_poisson(C.byref(self.s), _ptr(rho), *[_ptr(outs[k]) for k in
                                                          ("a", "psi", "phi", "ex", "ey", "ez")], _ptr(e))
         outs["energy"] = float(e[0])
+        if self.s.mode == 1:
+            outs["energy_layers"] = e.tolist()  # 2D mode: one energy per layer
         return outs
 
     def poisson_series_direct(self, rho):

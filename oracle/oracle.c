@@ -60,13 +60,21 @@ double orc_alpha(double dx, double dz, double beta, double w_hbt, double rh_top,
  * std cells: eq. std-size-tech (size of the die the cell sits on).
  * macros: eq. macro-size-tech, linear in z (R9).
  * omega and stretched size: Sec. IV-A local smoothness (R1). */
+static int is_hbt(const orc_problem *p, int i) {
+  return p->mode == 1 && p->is_hbt && p->is_hbt[i];
+}
+
 static void attr_one(const orc_problem *p, const double g[6], int i, double zi,
                      int *delta, double *w, double *h, double *sw, double *sh,
                      double *om) {
   double dz = g[5];
   int top = zi - 0.5 * dz > 0.0;
   double ww, hh;
-  if (p->is_macro[i]) {
+  if (is_hbt(p, i)) { /* 2D mode: an HBT has one footprint (Sec. V-B) */
+    top = 0;
+    ww = p->w_bot[i];
+    hh = p->h_bot[i];
+  } else if (p->is_macro[i] && p->mode != 1) {
     double t = 2.0 * zi / dz - 0.5; /* weight of the top-die size */
     if (t < 0.0) t = 0.0;
     if (t > 1.0) t = 1.0;
@@ -125,6 +133,11 @@ static void box_of(const orc_problem *p, const double g[6], int i,
   b[3] = y[i] + 0.5 * sh;
   b[4] = z[i] - 0.25 * g[5]; /* depth d_z/2 (Sec. III-A) */
   b[5] = z[i] + 0.25 * g[5];
+  if (p->mode == 1) { /* 2D mode: the instance fills its layer's one bin in z */
+    int layer = is_hbt(p, i) ? 2 : (z[i] - 0.5 * g[5] > 0.0);
+    b[4] = layer * g[2];
+    b[5] = (layer + 1) * g[2];
+  }
 }
 
 /* Eq. density-map-accum: rho_b = sum_i omega_i vol(D_i cap b) / vol(b). */
@@ -307,6 +320,25 @@ void orc_poisson(const orc_problem *p, const double *rho, double *a_out,
                  double *ez, double *energy) {
   double g[6];
   orc_geometry(p, g);
+  if (p->mode == 1) {
+    /* eq. 2d-place: each layer an independent 2D field.  A one-layer 3D
+     * solve is the 2D cosine series (the only z index is 0, E_z = 0); its
+     * energy 1/2 w_b h_b d_b N sum c a^2/omega^2 is d_b times the 2D energy
+     * 1/2 A_b sum rho phi.  energy[l] receives layer l's. */
+    orc_problem q = *p;
+    q.mode = 0;
+    q.nz = 1;
+    const size_t pl = (size_t)p->nx * p->ny;
+    for (int l = 0; l < p->nz; ++l) {
+      double e = 0.0;
+#define ORC_AT(ptr) ((ptr) ? (ptr) + l * pl : NULL)
+      orc_poisson(&q, rho + l * pl, ORC_AT(a_out), ORC_AT(psi_out), ORC_AT(phi), ORC_AT(ex), ORC_AT(ey),
+                  ORC_AT(ez), &e);
+#undef ORC_AT
+      if (energy) energy[l] = e / g[2];
+    }
+    return;
+  }
   const int nx = p->nx, ny = p->ny, nz = p->nz;
   const size_t nb = (size_t)nx * ny * nz;
   double *Fx = basis(nx, g[3], 0), *Fy = basis(ny, g[4], 0), *Fz = basis(nz, g[5], 0);
@@ -866,4 +898,103 @@ void orc_filler_plan(const orc_problem *p, const double *z, double u_top,
   out[8] = unit_t > 0.0 ? floor(vf_t / unit_t + 0.5) : 0.0;
   out[9] = unit_b > 0.0 ? floor(vf_b / unit_b + 0.5) : 0.0;
   out[10] = unit_fr > 0.0 ? floor(vfr / unit_fr + 0.5) : 0.0;
+}
+
+/* ---------------- multi-die 2D mode (eq. 2d-place) ---------------- */
+
+/* D2D wirelength of eq. exact-wirelength smoothed by eq. wa-model-approx,
+ * partition fixed by z: per net, WA(top pins + HBT pins) + WA(bottom pins +
+ * HBT pins) per axis.  out = {sum W^, exact D2D HPWL, #crossing nets}.
+ * Pin position: instance centre + its die's offset (bottom offset for HBTs). */
+static void wirelength2d(const orc_problem *p, const double *x, const double *y,
+                         const double *z, double out[3], double *gx, double *gy) {
+  double g[6];
+  orc_geometry(p, g);
+  const double dz = g[5];
+  int dmax_ = 1;
+  for (int e = 0; e < p->n_net; ++e) {
+    int d = p->net_start[e + 1] - p->net_start[e];
+    if (d > dmax_) dmax_ = d;
+  }
+  double *px = malloc(sizeof(double) * dmax_), *py = malloc(sizeof(double) * dmax_);
+  double *gpx = malloc(sizeof(double) * dmax_), *gpy = malloc(sizeof(double) * dmax_);
+  unsigned char *top = malloc(dmax_), *bot = malloc(dmax_);
+  memset(gx, 0, sizeof(double) * p->n_inst);
+  memset(gy, 0, sizeof(double) * p->n_inst);
+  double wsum = 0, hsum = 0, ncross = 0;
+  for (int e = 0; e < p->n_net; ++e) {
+    const int s0 = p->net_start[e], d = p->net_start[e + 1] - s0;
+    int nt = 0, nb = 0;
+    for (int k = 0; k < d; ++k) {
+      const int i = p->pin_inst[s0 + k];
+      const int h = is_hbt(p, i);
+      const int t = !h && z[i] - 0.5 * dz > 0.0;
+      px[k] = x[i] + (t ? p->off_tx[s0 + k] : p->off_bx[s0 + k]);
+      py[k] = y[i] + (t ? p->off_ty[s0 + k] : p->off_by[s0 + k]);
+      top[k] = (unsigned char)(h || t);
+      bot[k] = (unsigned char)(h || !t);
+      nt += !h && t;
+      nb += !h && !t;
+    }
+    if (nt > 0 && nb > 0) ncross += 1.0;
+    for (int side = 0; side < 2; ++side) {
+      const unsigned char *m = side ? top : bot;
+      for (int k = 0; k < d; ++k) gpx[k] = gpy[k] = 0.0;
+      wsum += wa_axis(px, m, d, p->gamma, gpx) + wa_axis(py, m, d, p->gamma, gpy);
+      hsum += hp_axis(px, m, d) + hp_axis(py, m, d);
+      for (int k = 0; k < d; ++k)
+        if (m[k]) {
+          gx[p->pin_inst[s0 + k]] += gpx[k];
+          gy[p->pin_inst[s0 + k]] += gpy[k];
+        }
+    }
+  }
+  out[0] = wsum;
+  out[1] = hsum;
+  out[2] = ncross;
+  free(px); free(py); free(gpx); free(gpy); free(top); free(bot);
+}
+
+void orc_eval2d(const orc_problem *p, const double *x, const double *y,
+                const double *z, int density_mode, double out[7], double *gx,
+                double *gy) {
+  const int n = p->n_inst;
+  const size_t nb = (size_t)p->nx * p->ny * p->nz;
+  double g[6];
+  orc_geometry(p, g);
+  double wl[3];
+  double *wgx = malloc(sizeof(double) * (n ? n : 1)), *wgy = malloc(sizeof(double) * (n ? n : 1));
+  wirelength2d(p, x, y, z, wl, wgx, wgy);
+  double *rho = malloc(sizeof(double) * nb);
+  if (density_mode == 0) {
+    orc_density_direct(p, x, y, z, rho);
+  } else {
+    int64_t *q = malloc(sizeof(int64_t) * nb);
+    orc_density_fixed(p, x, y, z, density_mode == 2, q);
+    for (size_t b = 0; b < nb; ++b) rho[b] = (double)q[b] * (1.0 / 68719476736.0);
+    free(q);
+  }
+  double *ex = malloc(sizeof(double) * nb), *ey = malloc(sizeof(double) * nb);
+  double *ez = malloc(sizeof(double) * nb);
+  double energy[3] = {0, 0, 0};
+  orc_poisson(p, rho, NULL, NULL, NULL, ex, ey, ez, energy);
+  double *dgx = malloc(sizeof(double) * (n ? n : 1)), *dgy = malloc(sizeof(double) * (n ? n : 1));
+  double *dgz = malloc(sizeof(double) * (n ? n : 1));
+  /* the gather's vol(D cap b) spans the whole layer depth d_b: area = vol / d_b */
+  orc_density_grad_gather(p, x, y, z, ex, ey, ez, dgx, dgy, dgz);
+  if (gx && gy)
+    for (int i = 0; i < n; ++i) {
+      const int layer = is_hbt(p, i) ? 2 : (z[i] - 0.5 * g[5] > 0.0);
+      const double lam = p->lam_layer[layer] / g[2];
+      gx[i] = wgx[i] + lam * dgx[i];
+      gy[i] = wgy[i] + lam * dgy[i];
+    }
+  out[0] = wl[0] + p->lam_layer[0] * energy[0] + p->lam_layer[1] * energy[1] + p->lam_layer[2] * energy[2];
+  out[1] = wl[0];
+  out[2] = energy[0];
+  out[3] = energy[1];
+  out[4] = energy[2];
+  out[5] = wl[1];
+  out[6] = wl[2];
+  free(wgx); free(wgy); free(rho); free(ex); free(ey); free(ez); free(dgx); free(dgy); free(dgz);
 }

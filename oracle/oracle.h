@@ -32,6 +32,14 @@ typedef struct {
   double xl, yl, xh, yh;
   int nx, ny, nz;
   double gamma, gamma_z, alpha, lambda;
+  /* Multi-die 2D mode (Sec. V-B "multi-die 2D global placement", eq.
+   * 2d-place): mode = 1, nz = 3 layers (0 bottom die, 1 top die, 2 HBT
+   * layer), is_hbt marks the hybrid bonding terminals (instances of the HBT
+   * layer, footprint w_bot x h_bot, pins counted in both partial nets),
+   * lam_layer = (lambda-, lambda+, lambda') per layer.  mode = 0: 3D. */
+  const unsigned char *is_hbt; /* [n_inst] or NULL */
+  int mode;
+  double lam_layer[3];
 } orc_problem;
 
 /* Region and bin geometry (Sec. II-A, Sec. V-A: d_b=(w_b+h_b)/2, d_z=N_z d_b).
@@ -73,7 +81,9 @@ void orc_density_fixed(const orc_problem *p, const double *x, const double *y,
 /* Spectral solve of eq. 3d-poisson-equation, separable per-axis form of eqs.
  * density-coef, poisson-sol-potential, possion-sol-force with the cosine
  * series weights c_0=1, c_j=2.  Any output pointer may be NULL.
- * energy = 1/2 vol(b) N sum c_j c_k c_l a^2/omega^2 (spectral form). */
+ * energy = 1/2 vol(b) N sum c_j c_k c_l a^2/omega^2 (spectral form).
+ * mode 1 (2D): one 2D solve per layer, E_z = 0, energy[l] = 1/2 A_b
+ * sum_b rho_b phi_b of layer l (energy then points to nz values). */
 void orc_poisson(const orc_problem *p, const double *rho, double *a,
                  double *psi, double *phi, double *ex, double *ey, double *ez,
                  double *energy);
@@ -131,6 +141,21 @@ void orc_wirelength(const orc_problem *p, const double *x, const double *y,
  * out = {vol_a, vol_f+, vol_f-, vol_fr, w+, h+, w-, h-, n+, n-, n_fr}. */
 void orc_filler_plan(const orc_problem *p, const double *z, double u_top,
                      double u_bot, double out[11]);
+
+/* Multi-die 2D evaluation (eq. 2d-place).  The partition is fixed: delta_i
+ * = 1[z_i > d_z/2] for non-HBT instances.  Per net, the D2D wirelength
+ * (eq. exact-wirelength, smoothed by eq. wa-model-approx) is the WA span of
+ * the top partial net plus that of the bottom partial net, each including
+ * the net's HBT pins (a net on one die is its own partial net).  Each layer
+ * is an independent 2D electrostatic field: rho_l by eq. density-map-accum
+ * in 2D (area overlap, local smoothness), potential of the 2D cosine series,
+ * energy U_l = 1/2 A_b sum_b rho_b phi_b, force -omega sum_b area(D cap b)
+ * E_b.  Instance sizes are their die's (macros too); HBTs are w_bot x h_bot.
+ * density_mode as in orc_eval.  out = {obj, sum W^, U-, U+, U', exact D2D
+ * HPWL, #crossing nets}.  gx, gy may be NULL. */
+void orc_eval2d(const orc_problem *p, const double *x, const double *y,
+                const double *z, int density_mode, double out[7], double *gx,
+                double *gy);
 
 /* Full objective and gradient (a1..a11).  density_mode: 0 = direct FP64
  * density, 1 = fixed-point replica in double, 2 = fixed-point replica in

@@ -281,3 +281,73 @@ def make_batch(count: int = 24, seed: int = 4, n_min: int = 5000, n_max: int = 3
                       2 if nxy <= 128 else 4, seed * 1000 + k)
         out.append(make_problem(wl))
     return out
+
+
+def to_problem2d(prob: dict, x=None, y=None, z=None, hbt_xy=None, seed: int = 0, lam_layer=None) -> dict:
+    """The multi-die 2D form of a 3D problem at positions (x, y, z) (default
+    the problem's own): the partition is the one z gives (top iff z > d_z/2
+    of the 3D grid), the grid keeps N_x x N_y with N_z = 3 layers (bottom die,
+    top die, HBT layer), and every net with pins on both dies gets one HBT
+    instance (is_hbt = 1, a w_hbt x w_hbt square, no offsets) whose pin ends
+    that net's pin list.  hbt_xy: (x, y) arrays of the HBT centres in
+    crossing-net order, or None for uniform random centres in the region.
+    z is rewritten to d_z/4 (bottom) or 3 d_z/4 (top) of the 3-layer grid.
+    This only assembles arrays; it computes nothing of the method."""
+    x = np.asarray(prob["x"] if x is None else x, np.float64)
+    y = np.asarray(prob["y"] if y is None else y, np.float64)
+    z = np.asarray(prob["z"] if z is None else z, np.float64)
+    n = int(prob["n_inst"])
+    zlo3, zhi3 = depth_range(prob)
+    top = z > 0.5 * (zlo3 + zhi3)
+    ns = np.asarray(prob["net_start"], np.int64)
+    pi = np.asarray(prob["pin_inst"], np.int64)
+    deg = np.diff(ns)
+    net_of = np.repeat(np.arange(deg.size), deg)
+    t_cnt = np.bincount(net_of, weights=top[pi].astype(np.float64), minlength=deg.size)
+    cross = np.nonzero((t_cnt > 0) & (t_cnt < deg))[0]
+    nh = cross.size
+    rng = np.random.default_rng(seed)
+    if hbt_xy is None:
+        hx = prob["xl"] + rng.random(nh) * (prob["xh"] - prob["xl"])
+        hy = prob["yl"] + rng.random(nh) * (prob["yh"] - prob["yl"])
+    else:
+        hx, hy = (np.asarray(a, np.float64) for a in hbt_xy)
+    # netlist: the HBT pin appended to each crossing net
+    extra = np.zeros(deg.size, np.int64)
+    extra[cross] = 1
+    new_deg = deg + extra
+    new_ns = np.zeros(deg.size + 1, np.int64)
+    np.cumsum(new_deg, out=new_ns[1:])
+    P2 = int(new_ns[-1])
+    new_pi = np.empty(P2, np.int64)
+    offs = {k: np.zeros(P2) for k in ("off_bx", "off_by", "off_tx", "off_ty")}
+    dst = np.repeat(new_ns[:-1], deg) + (np.arange(pi.size) - np.repeat(ns[:-1], deg))
+    new_pi[dst] = pi
+    for k in offs:
+        offs[k][dst] = np.asarray(prob[k], np.float64)
+    new_pi[new_ns[cross + 1] - 1] = n + np.arange(nh)
+    w = float(prob.get("w_hbt", 1.0))
+    wb = (prob["xh"] - prob["xl"]) / prob["nx"]
+    hb = (prob["yh"] - prob["yl"]) / prob["ny"]
+    dz2 = 3 * 0.5 * (wb + hb)
+    out = dict(prob)
+    for k in ("w_bot", "h_bot", "w_top", "h_top"):
+        out[k] = np.concatenate([np.asarray(prob[k], np.float64), np.full(nh, w)])
+    out["is_macro"] = np.concatenate([np.asarray(prob["is_macro"], np.uint8), np.zeros(nh, np.uint8)])
+    zf = prob.get("z_fixed")
+    out["z_fixed"] = np.concatenate([np.zeros(n, np.uint8) if zf is None else np.asarray(zf, np.uint8),
+                                     np.zeros(nh, np.uint8)])
+    out["is_hbt"] = np.concatenate([np.zeros(n, np.uint8), np.ones(nh, np.uint8)])
+    out["n_inst"] = n + nh
+    out["net_start"] = new_ns.astype(np.int32)
+    out["pin_inst"] = new_pi.astype(np.int32)
+    out["n_pin"] = P2
+    out.update(offs)
+    out["nz"] = 3
+    out["mode"] = 1
+    out["lam_layer"] = tuple(lam_layer) if lam_layer is not None else (prob["lam"],) * 3
+    out["x"] = np.concatenate([x, hx])
+    out["y"] = np.concatenate([y, hy])
+    out["z"] = np.concatenate([np.where(top, 0.75 * dz2, 0.25 * dz2), np.full(nh, 0.5 * dz2)])
+    out["hbt_nets"] = cross.astype(np.int64)
+    return out
