@@ -174,7 +174,10 @@ def _oracle_worker(args):
     times = []
     for _ in range(count):
         t0 = time.perf_counter()
-        o.eval(p["x"], p["y"], p["z"], density_mode=0, fd_mode=1)
+        if p.get("mode", 0) == 1:
+            o.eval2d(p["x"], p["y"], p["z"], density_mode=0)
+        else:
+            o.eval(p["x"], p["y"], p["z"], density_mode=0, fd_mode=1)
         times.append(time.perf_counter() - t0)
     return times
 
@@ -233,10 +236,18 @@ FILLER_U = 0.8  # maximum utilisation of each die for the "<base>_fillers" workl
 
 
 def make_workload(name: str) -> dict:
-    """A named synthetic problem; "<base>_fillers" appends the dummy fillers
+    """A named synthetic problem.  "<base>_fillers" appends the dummy fillers
     of eqs. filler-vol / free-filler-vol (u+ = u- = 0.8) to <base>, spread
-    uniformly over the region (a mid-placement state)."""
-    from paper_2403_09070_gb300 import fillers, synth
+    uniformly over the region (a mid-placement state).  "<base>_2d" is the
+    multi-die 2D problem (eq. 2d-place) of <base>'s placement: partition from
+    z, one HBT per crossing net at its optimal-region centre; "<base>_2d_fillers"
+    adds the dies' fillers (die area minus instance area, spread uniformly)."""
+    from paper_2403_09070_gb300 import fillers, place2d, synth
+    if name.endswith("_2d_fillers"):
+        p = synth.make_problem(name[:-len("_2d_fillers")])
+        return place2d.from_3d(p, fillers=True, seed=11)
+    if name.endswith("_2d"):
+        return place2d.from_3d(synth.make_problem(name[:-len("_2d")]), fillers=False)
     if name.endswith("_fillers"):
         p = synth.make_problem(name[:-len("_fillers")])
         return fillers.insert(p, FILLER_U, FILLER_U, seed=11, positions="uniform")
@@ -245,11 +256,21 @@ def make_workload(name: str) -> dict:
 
 def _workload_desc(name, prob=None):
     from paper_2403_09070_gb300 import synth
-    base = name[:-len("_fillers")] if name.endswith("_fillers") else name
+    base = name
+    for suf in ("_2d_fillers", "_2d", "_fillers"):
+        if base.endswith(suf):
+            base = base[:-len(suf)]
+            break
     w = synth.WORKLOADS[base]
     d = (f"{name}: {w.n_std} std cells + {w.n_macro} macros, {w.n_net} nets (+{w.n_hifanout} high-fanout), "
          f"{w.die:g}x{w.die:g} dies, {w.nx}x{w.ny}x{w.nz} bins")
-    if prob is not None and "fillers" in prob:
+    if prob is not None and prob.get("mode", 0) == 1:
+        d += (f"; multi-die 2D (eq. 2d-place): {int(prob['is_hbt'].sum())} HBTs at optimal-region centres, "
+              f"{prob['nx']}x{prob['ny']} bins x 3 layers")
+        if "fillers" in prob:
+            f = prob["fillers"]
+            d += f", {f['n_top']} top / {f['n_bot']} bottom die fillers"
+    elif prob is not None and "fillers" in prob:
         f = prob["fillers"]
         d += (f" + {f['n_top']} top / {f['n_bot']} bottom z-fixed and {f['n_free']} free fillers "
               f"(u+ = u- = {FILLER_U})")

@@ -67,8 +67,12 @@ extern "C" {
  * gather them through shared-memory windows (a counting sort by tile, then
  * one block per chunk of a tile), instead of one thread per cell with global
  * int64 atomics and global field gathers.  Same results; which is faster
- * depends on the cell order and density (see the design notes). */
+ * depends on the cell order and density.  Ignored in 2D mode. */
 #define PLACE3D_FLAG_TILES 16
+
+/* ---- placement mode (place3d_problem.mode) ---- */
+#define PLACE3D_MODE_3D 0 /* 3D mixed-size placement, eq. analytical-placement */
+#define PLACE3D_MODE_2D 1 /* multi-die 2D placement, eq. 2d-place */
 
 /* ---- dtype and memory kind of caller buffers ---- */
 #define PLACE3D_F64 0
@@ -117,6 +121,19 @@ typedef struct place3d_problem {
   double alpha, lambda;
   int32_t precision; /* PLACE3D_FP64 | PLACE3D_FP32 | PLACE3D_FP32_TC */
   int32_t flags;     /* PLACE3D_FLAG_* */
+  /* Multi-die 2D global placement (Sec. V-B, eq. 2d-place) when mode =
+   * PLACE3D_MODE_2D; zero-initialise these three for the 3D placer.
+   * In 2D mode the grid has nz = 3 layers (0 bottom die, 1 top die, 2 HBT
+   * layer), each an independent 2D electrostatic field; the partition is
+   * fixed: a non-HBT instance is on the top die iff z > d_z/2 (d_z = 3 d_b),
+   * its footprint is that die's (macros too).  is_hbt marks the hybrid
+   * bonding terminals: instances of the HBT layer with footprint w_bot x
+   * h_bot whose pins (one per crossing net, offsets normally 0) belong to
+   * both partial nets (eq. exact-wirelength).  lam_layer weights the three
+   * layers' energies; lambda is not used.  There is no z-gradient (0). */
+  int32_t mode;           /* PLACE3D_MODE_3D (0) | PLACE3D_MODE_2D (1) */
+  const uint8_t *is_hbt;  /* [n_inst] or NULL; 2D mode only */
+  double lam_layer[3];    /* 2D mode: (lambda-, lambda+, lambda') */
 } place3d_problem;
 
 /* Scalars of one evaluation (FP64). */
@@ -129,6 +146,10 @@ typedef struct place3d_result {
   double n_cross;  /* #crossing nets = sum_e C_e (Sec. II-B), i.e. #HBTs */
   double g_scale;  /* (S_x + S_y) / (2 S_z) of eq. fda-normalize (0 if S_z = 0) */
   double s_x, s_y, s_z; /* L1 norms of the WL gradient in x, y and of eq. fda-grad */
+  /* 2D mode: U of the bottom, top and HBT layers (1/2 A_b sum rho phi each);
+   * obj = wl_bi + sum_l lam_layer[l] energy_layer[l], energy = their sum,
+   * hpwl_d2d = exact D2D HPWL with the HBTs (eq. exact-wirelength).  3D: 0. */
+  double energy_layer[3];
 } place3d_result;
 
 typedef struct place3d_handle place3d_handle;
@@ -230,6 +251,11 @@ int place3d_result_to_device(place3d_handle *h, double *dst);
  * Errors: INVALID_ARG (gamma <= 0 or a non-finite value). */
 int place3d_set_params(place3d_handle *h, double gamma, double gamma_z,
                        double alpha, double lambda);
+
+/* 2D mode: set the three layers' density weights (lambda-, lambda+,
+ * lambda') for the following evaluations.  Errors: INVALID_ARG (3D handle or
+ * a non-finite weight). */
+int place3d_set_layer_weights(place3d_handle *h, const double lam[3]);
 
 /* Read an intermediate map of the last evaluation into dst (host or device,
  * [N_z][N_y][N_x] with x fastest):

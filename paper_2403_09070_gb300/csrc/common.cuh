@@ -150,6 +150,9 @@ enum Scalar {
   S_SX,
   S_SY,
   S_SZ,
+  S_EL0,  // 2D mode: per-layer energy sums (bottom, top, HBT layer)
+  S_EL1,
+  S_EL2,
   S_COUNT
 };
 

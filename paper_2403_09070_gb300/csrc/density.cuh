@@ -15,6 +15,7 @@ template <typename T> struct DensC {
   T zmid, qz, tz;    // d_z/2, d_z/4, 2/d_z
   T fnx, fny, fnz;   // N_x, N_y, N_z as T
   int nx, ny, nz;
+  int mode2d;        // 1: multi-die 2D (eq. 2d-place): layer = HBT ? 2 : top, die sizes, no z extent
 };
 
 constexpr double kFixedScale = 68719476736.0;  // 2^36 counts per unit density
@@ -29,12 +30,18 @@ template <typename T> struct Box {
 // movable range) and local smoothness (omega, stretched footprint).  Every
 // step is one IEEE-rounded operation in the order the fixed-point contract
 // states, so that quantised contributions are reproducible bit for bit.
+// 2D mode (c.mode2d): the partition is fixed, every instance (macros too)
+// has its die's size, an HBT (hbt) its bottom-table size, and the cuboid
+// fills exactly its layer's bin in z: [layer, layer + 1) in bin units.
 template <typename T>
 __device__ __forceinline__ Box<T> inst_box(const DensC<T> &c, T X, T Y, T Z, const V4<T> &sz,
-                                           bool macro) {
-  const bool top = Z > c.zmid;
+                                           bool macro, bool hbt = false) {
+  const bool top = !hbt && Z > c.zmid;
   T w, h;
-  if (macro) {
+  if (hbt) {
+    w = sz.x;
+    h = sz.y;
+  } else if (macro && !c.mode2d) {
     T t = rn_sub(rn_mul(Z, c.tz), T(0.5));
     if (t < T(0)) t = T(0);
     if (t > T(1)) t = T(1);
@@ -55,8 +62,14 @@ __device__ __forceinline__ Box<T> inst_box(const DensC<T> &c, T X, T Y, T Z, con
   b.hi[0] = rn_mul(rn_add(dx, hw), c.iwb);
   b.lo[1] = rn_mul(rn_sub(dy, hh), c.ihb);
   b.hi[1] = rn_mul(rn_add(dy, hh), c.ihb);
-  b.lo[2] = rn_mul(rn_sub(Z, c.qz), c.idb);
-  b.hi[2] = rn_mul(rn_add(Z, c.qz), c.idb);
+  if (c.mode2d) {
+    const int layer = hbt ? 2 : (top ? 1 : 0);
+    b.lo[2] = (T)layer;
+    b.hi[2] = (T)(layer + 1);
+  } else {
+    b.lo[2] = rn_mul(rn_sub(Z, c.qz), c.idb);
+    b.hi[2] = rn_mul(rn_add(Z, c.qz), c.idb);
+  }
   return b;
 }
 
@@ -92,7 +105,7 @@ __global__ void __launch_bounds__(256) k_scatter_cells(int n, const V4<T> *__res
   const uint8_t f = flags[i];
   if (f & 1) return;  // macro: Theorem 1 path
   const V4<T> p = pos[i];
-  const Box<T> b = inst_box(c, p.x, p.y, p.z, size[i], false);
+  const Box<T> b = inst_box(c, p.x, p.y, p.z, size[i], false, (f & 4) != 0);
   T cl[3], chh[3];
   int b0[3], b1[3];
   if (!clip_axis(b.lo[0], b.hi[0], c.fnx, c.nx, cl[0], chh[0], b0[0], b1[0])) return;
@@ -314,9 +327,11 @@ __global__ void __launch_bounds__(256) k_macro_gather_direct(const int *__restri
 
 // Final assembly constants.
 template <typename T> struct FinalC {
-  T lam, alpha, volb;
+  T lam, alpha, volb;  // volb: bin volume (2D mode: bin area)
   const double *scal;  // device scalars (S_x, S_y, S_z for g)
   T g;                 // filled per block from scal
+  int mode2d;          // 2D mode: per-layer lambda, no z-gradient
+  T lam_l[3];          // 2D mode: (lambda-, lambda+, lambda')
 };
 
 __device__ __forceinline__ double g_scale_of(const double *scal) {
@@ -344,6 +359,7 @@ __global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint8_t f = flags[i];
+  const V4<T> p = pos[i];
   T dgx = 0, dgy = 0, dgz = 0;
   if (f & 1) {
     const int m = macro_slot[i];
@@ -351,8 +367,7 @@ __global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ 
     dgy = (T)(-(double)fc.volb * mgrad[m * 3 + 1]);
     dgz = (T)(-(double)fc.volb * mgrad[m * 3 + 2]);
   } else {
-    const V4<T> p = pos[i];
-    const Box<T> b = inst_box(c, p.x, p.y, p.z, size[i], false);
+    const Box<T> b = inst_box(c, p.x, p.y, p.z, size[i], false, (f & 4) != 0);
     T cl[3], chh[3];
     int b0[3], b1[3];
     if (clip_axis(b.lo[0], b.hi[0], c.fnx, c.nx, cl[0], chh[0], b0[0], b1[0]) &&
@@ -381,10 +396,12 @@ __global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ 
   }
   const V4<T> a = acc[i];
   const T g = fc.g;
-  T ozg = g * a.z + fc.alpha * a.w + fc.lam * dgz;
-  if (f & 2) ozg = T(0);
-  gx[i] = (TO)(a.x + fc.lam * dgx);
-  gy[i] = (TO)(a.y + fc.lam * dgy);
+  T lam = fc.lam;
+  if (fc.mode2d) lam = fc.lam_l[(f & 4) ? 2 : (p.z > c.zmid ? 1 : 0)];
+  T ozg = g * a.z + fc.alpha * a.w + lam * dgz;
+  if ((f & 2) || fc.mode2d) ozg = T(0);
+  gx[i] = (TO)(a.x + lam * dgx);
+  gy[i] = (TO)(a.y + lam * dgy);
   gz[i] = (TO)ozg;
 }
 

@@ -142,6 +142,7 @@ extern "C" int place3d_density_map_noalloc(int n_inst, const double *x, const do
   c.nx = nx;
   c.ny = ny;
   c.nz = nz;
+  c.mode2d = 0;
   SoA a{x, y, z, w_bot, h_bot, w_top, h_top, is_macro};
   // the scratch keeps the previous call's contents: clear both maps first
   if (cudaMemsetAsync(scratch, 0, 2 * nb * sizeof(long long), s) != cudaSuccess) return PLACE3D_ERR_CUDA;

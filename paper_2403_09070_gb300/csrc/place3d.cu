@@ -64,6 +64,8 @@ struct StageEv {
 
 struct place3d_handle {
   int device = 0;
+  bool mode2d = false;                 // multi-die 2D placement (eq. 2d-place)
+  double lam_layer[3] = {0, 0, 0};     // 2D mode: density weights of the three layers
   cudaStream_t stream = nullptr, side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int precision = 0, flags = 0;
@@ -104,6 +106,9 @@ struct place3d_handle {
   p3d_tc::TcPlan *tc = nullptr;
   // CUDA graph of one evaluation (place3d_eval_graph)
   cudaGraphExec_t gexec = nullptr;
+  // bumped by every change that a captured graph bakes in (gamma, lambda,
+  // alpha, layer weights, reduction forms); graphs recapture when it moved
+  unsigned version = 0, gversion = 0;
   cudaStream_t cap_stream = nullptr;
   const void *gptr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int gdtype = -1;
@@ -228,6 +233,7 @@ template <typename T> DensC<T> dens_consts(const place3d_handle *h, double xl, d
   c.nx = h->nx;
   c.ny = h->ny;
   c.nz = h->nz;
+  c.mode2d = h->mode2d ? 1 : 0;
   return c;
 }
 
@@ -302,6 +308,7 @@ template <typename T> WlC<T> wl_consts(const place3d_handle *h) {
   c.inv_g = (T)(1.0 / h->gamma);
   c.inv_gz = (T)(1.0 / (h->gamma_z > 0 ? h->gamma_z : h->gamma));
   c.fd_scale = (T)(4.0 / h->dz);
+  c.mode2d = h->mode2d ? 1 : 0;
   return c;
 }
 
@@ -482,8 +489,10 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     FinalC<T> fc;
     fc.lam = (T)h->lambda;
     fc.alpha = (T)h->alpha;
-    fc.volb = (T)(h->wb * h->hb * h->db);
+    fc.volb = (T)(h->mode2d ? h->wb * h->hb : h->wb * h->hb * h->db);  // 2D: bin area
     fc.scal = h->scal;
+    fc.mode2d = h->mode2d ? 1 : 0;
+    for (int l = 0; l < 3; ++l) fc.lam_l[l] = (T)h->lam_layer[l];
     const bool direct = mem == PLACE3D_MEM_DEVICE && gx && gy && gz;
     const int odt = direct ? dtype : (sizeof(T) == 8 ? PLACE3D_F64 : PLACE3D_F32);
     void *ox = direct ? gx : h->gout;
@@ -537,6 +546,18 @@ void fill_result(const place3d_handle *h, place3d_result *r) {
   r->s_z = s[S_SZ];
   r->g_scale = s[S_SZ] > 0 ? (s[S_SX] + s[S_SY]) / (2.0 * s[S_SZ]) : 0.0;
   r->obj = r->wl_bi + h->alpha * r->wl_z + h->lambda * r->energy;
+  for (int l = 0; l < 3; ++l) r->energy_layer[l] = 0.0;
+  if (h->mode2d) {
+    // eq. 2d-place: U_l = 1/2 A_b N_x N_y sum c_j c_k a^2 / w^2 per layer
+    const double ab = h->wb * h->hb, nxy = (double)h->nx * h->ny;
+    r->energy = 0.0;
+    r->obj = r->wl_bi;
+    for (int l = 0; l < 3; ++l) {
+      r->energy_layer[l] = 0.5 * ab * nxy * s[S_EL0 + l];
+      r->energy += r->energy_layer[l];
+      r->obj += h->lam_layer[l] * r->energy_layer[l];
+    }
+  }
 }
 
 void free_all(place3d_handle *h) {
@@ -577,6 +598,7 @@ int upload_typed(place3d_handle *h, const place3d_problem *p, const std::vector<
   for (int e : order) {
     for (int q = p->net_start[e]; q < p->net_start[e + 1]; ++q, ++k) {
       pin[k] = p->pin_inst[q];
+      if (h->mode2d && p->is_hbt && p->is_hbt[pin[k]]) pin[k] = ~pin[k];  // HBT pin: both partial nets
       off[k].x = (T)p->pin_off_bot_x[q];
       off[k].y = (T)p->pin_off_bot_y[q];
       off[k].z = (T)p->pin_off_top_x[q];
@@ -634,6 +656,20 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
   const int n = p->n_inst;
   if (n > 0 && (!p->is_macro || !p->w_bot || !p->h_bot || !p->w_top || !p->h_top))
     return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL instance array");
+  if (p->mode != PLACE3D_MODE_3D && p->mode != PLACE3D_MODE_2D)
+    return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "unknown placement mode");
+  if (p->mode == PLACE3D_MODE_2D) {
+    if (p->nz != 3) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "2D mode needs nz = 3 layers");
+    for (int l = 0; l < 3; ++l)
+      if (!std::isfinite(p->lam_layer[l])) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "lam_layer must be finite");
+    if (p->is_hbt)
+      for (int i = 0; i < n; ++i)
+        if (p->is_hbt[i] && p->is_macro[i])
+          return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "an HBT cannot be a macro");
+  } else if (p->is_hbt) {
+    for (int i = 0; i < n; ++i)
+      if (p->is_hbt[i]) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "HBT instances need 2D mode");
+  }
   for (int i = 0; i < n; ++i)
     if (!(p->w_bot[i] >= 0) || !(p->h_bot[i] >= 0) || !(p->w_top[i] >= 0) || !(p->h_top[i] >= 0) ||
         !std::isfinite(p->w_bot[i] + p->h_bot[i] + p->w_top[i] + p->h_top[i]))
@@ -687,6 +723,8 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
   std::memset(h->stage_launch, 0, sizeof(h->stage_launch));
   h->xl = p->xl;
   h->yl = p->yl;
+  h->mode2d = p->mode == PLACE3D_MODE_2D;
+  for (int l = 0; l < 3; ++l) h->lam_layer[l] = h->mode2d ? p->lam_layer[l] : 0.0;
   auto bail = [&](int code) {
     free_all(h);
     g_thread_err = h->err;
@@ -711,7 +749,10 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
     if (cls[k].empty()) continue;
     int dmax = 0;
     for (int e : cls[k]) dmax = std::max(dmax, p->net_start[e + 1] - p->net_start[e]);
-    h->buckets.push_back({(int)order.size(), (int)cls[k].size(), dmax, kDefault[k][0], kDefault[k][1]});
+    // 2D mode has no closed form for 2-pin nets (one lane, two pins instead)
+    const bool pair = kDefault[k][0] == 1 && kDefault[k][1] == 1;
+    h->buckets.push_back({(int)order.size(), (int)cls[k].size(), dmax, kDefault[k][0],
+                          pair && h->mode2d ? 2 : kDefault[k][1]});
     for (int e : cls[k]) {
       order.push_back(e);
       new_start.push_back(new_start.back() + (p->net_start[e + 1] - p->net_start[e]));
@@ -729,6 +770,7 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
       fl[i] |= 1;
     }
     if (p->z_fixed && p->z_fixed[i]) fl[i] |= 2;
+    if (h->mode2d && p->is_hbt && p->is_hbt[i]) fl[i] |= 4;
   }
   h->nm = (int)mids.size();
   // macro gather form: direct when the macros' bins (at their larger size) are
@@ -764,7 +806,7 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
     const size_t wbins = (size_t)h->tcfg.WX * h->tcfg.WY * p->nz;
     h->smem_scatter = wbins * 8;  // two 32-bit words per bin
     h->smem_final = wbins * 3 * (p->precision == PLACE3D_FP64 ? 8 : 4);
-    h->tiles = (p->flags & PLACE3D_FLAG_TILES) && R <= 8 && h->ntiles <= 8192 && n < (1 << 24) &&
+    h->tiles = (p->flags & PLACE3D_FLAG_TILES) && !h->mode2d && R <= 8 && h->ntiles <= 8192 && n < (1 << 24) &&
                h->smem_final <= 200 * 1024 && h->smem_scatter <= 200 * 1024;
     h->max_items = (n + kChunk - 1) / kChunk + h->ntiles;
   }
@@ -819,11 +861,13 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
   zc.nx = h->nx;
   zc.ny = h->ny;
   zc.nz = h->nz;
+  zc.mode2d = h->mode2d ? 1 : 0;
   const double pi = 3.14159265358979323846;
   zc.pi_dx = pi / h->dx;
   zc.pi_dy = pi / h->dy;
   zc.pi_dz = pi / h->dz;
-  zc.inv_n = 1.0 / (double)h->nb;
+  // 2D mode: each layer's coefficients are normalised by its own N_x N_y bins
+  zc.inv_n = 1.0 / (h->mode2d ? (double)h->nx * h->ny : (double)h->nb);
   zc.pi_dx_f = (float)zc.pi_dx;
   zc.pi_dy_f = (float)zc.pi_dy;
   zc.pi_dz_f = (float)zc.pi_dz;
@@ -1097,6 +1141,17 @@ int place3d_set_params(place3d_handle *h, double gamma, double gamma_z, double a
   h->gamma_z = gamma_z;
   h->alpha = alpha;
   h->lambda = lambda;
+  ++h->version;
+  return PLACE3D_OK;
+}
+
+int place3d_set_layer_weights(place3d_handle *h, const double lam[3]) {
+  if (!h || !lam) return fail(h, PLACE3D_ERR_INVALID_ARG, "NULL argument");
+  if (!h->mode2d) return fail(h, PLACE3D_ERR_INVALID_ARG, "layer weights need a 2D-mode handle");
+  for (int l = 0; l < 3; ++l)
+    if (!std::isfinite(lam[l])) return fail(h, PLACE3D_ERR_INVALID_ARG, "layer weights must be finite");
+  for (int l = 0; l < 3; ++l) h->lam_layer[l] = lam[l];
+  ++h->version;
   return PLACE3D_OK;
 }
 
@@ -1116,7 +1171,7 @@ int place3d_autotune(place3d_handle *h, int repeats) {
     for (int f = 0; f < kNumForms; ++f) {
       const int G = kForms[f][0], PPL = kForms[f][1];
       const bool pair = G == 1 && PPL == 1;
-      if (pair ? b.dmax != 2 : (G * PPL < b.dmax || G * PPL > 4 * std::max(b.dmax, 8))) continue;
+      if (pair ? (b.dmax != 2 || h->mode2d) : (G * PPL < b.dmax || G * PPL > 4 * std::max(b.dmax, 8))) continue;
       for (int r = 0; r <= repeats; ++r) {  // first run warms up
         if (r == 1) cudaEventRecord(e0, w);
         if (h->precision == PLACE3D_FP64)
@@ -1133,6 +1188,7 @@ int place3d_autotune(place3d_handle *h, int repeats) {
     b.G = bg;
     b.PPL = bp;
   }
+  ++h->version;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   P3D_CUDA(h, cudaGetLastError());
@@ -1144,9 +1200,11 @@ int place3d_set_wl_form(place3d_handle *h, int bucket, int lanes, int pins) {
   Bucket &b = h->buckets[bucket];
   if (b.G == 0) return lanes == 0 && pins == 0 ? PLACE3D_OK : fail(h, PLACE3D_ERR_INVALID_ARG, "block-form bucket");
   for (int f = 0; f < kNumForms; ++f)
-    if (kForms[f][0] == lanes && kForms[f][1] == pins && (lanes * pins >= b.dmax || (lanes == 1 && pins == 1 && b.dmax == 2))) {
+    if (kForms[f][0] == lanes && kForms[f][1] == pins &&
+        (lanes * pins >= b.dmax || (lanes == 1 && pins == 1 && b.dmax == 2 && !h->mode2d))) {
       b.G = lanes;
       b.PPL = pins;
+      ++h->version;
       return PLACE3D_OK;
     }
   return fail(h, PLACE3D_ERR_INVALID_ARG, "unsupported form for this bucket");
@@ -1192,7 +1250,7 @@ int place3d_eval_graph(place3d_handle *h, const void *x, const void *y, const vo
   if (dtype != PLACE3D_F64 && dtype != PLACE3D_F32) return fail(h, PLACE3D_ERR_INVALID_ARG, "bad dtype");
   P3D_CUDA(h, cudaSetDevice(h->device));
   const void *ptr[6] = {x, y, z, gx, gy, gz};
-  bool same = h->gexec && h->gdtype == dtype;
+  bool same = h->gexec && h->gdtype == dtype && h->gversion == h->version;
   for (int k = 0; k < 6 && same; ++k) same = h->gptr[k] == ptr[k];
   if (!same) {
     if (h->gexec) {
@@ -1215,6 +1273,7 @@ int place3d_eval_graph(place3d_handle *h, const void *x, const void *y, const vo
     if (ei != cudaSuccess) return cuda_fail(h, ei, "cudaGraphInstantiate");
     for (int k = 0; k < 6; ++k) h->gptr[k] = ptr[k];
     h->gdtype = dtype;
+    h->gversion = h->version;
   }
   P3D_CUDA(h, cudaGraphLaunch(h->gexec, h->stream));
   h->have_result = true;
@@ -1267,6 +1326,7 @@ struct place3d_batch {
   cudaEvent_t fork = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<const void *> ptrs;
+  std::vector<unsigned> versions;  // each handle's parameter version at capture
   int dtype = -1, device = 0;
   std::string err;
 };
@@ -1325,7 +1385,9 @@ int place3d_batch_eval(place3d_batch *b, const void *const *xs, const void *cons
       ptr.push_back(pi[k]);
     }
   }
-  if (!b->exec || b->dtype != dtype || b->ptrs != ptr) {
+  std::vector<unsigned> vers;
+  for (auto *h : b->hs) vers.push_back(h->version);
+  if (!b->exec || b->dtype != dtype || b->ptrs != ptr || b->versions != vers) {
     if (b->exec) {
       cudaGraphExecDestroy(b->exec);
       b->exec = nullptr;
@@ -1354,6 +1416,7 @@ int place3d_batch_eval(place3d_batch *b, const void *const *xs, const void *cons
     cudaGraphDestroy(graph);
     if (ei != cudaSuccess) return PLACE3D_ERR_CUDA;
     b->ptrs = ptr;
+    b->versions = vers;
     b->dtype = dtype;
   }
   if (cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(cuda_stream)) != cudaSuccess) return PLACE3D_ERR_CUDA;

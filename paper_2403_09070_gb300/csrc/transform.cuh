@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmGroup<T> g) {
 constexpr int kMaxNz = 16;
 struct ZStageC {
   int nx, ny, nz;
+  int mode2d;                  // 1: each layer an independent 2D field (eq. 2d-place)
   double pi_dx, pi_dy, pi_dz;  // pi/d_x, pi/d_y, pi/d_z
   double inv_n;                // 1/N
   float pi_dx_f, pi_dy_f, pi_dz_f, inv_n_f;  // the same, rounded to FP32
@@ -119,12 +120,36 @@ template <> struct ZPar<float> {
 };
 
 // All arithmetic in T (FP32 threads stay off the FP64 pipe); the energy sum
-// is widened to FP64 per warp.
+// is widened to FP64 per warp.  2D mode (zc->mode2d, N_z = 3 layers): no z
+// transform, psi = c_j c_k a / (w_j^2 + w_k^2) per layer with a = (1/(N_x
+// N_y)) T2, E_z = 0 (Szpsi = 0), one energy sum per layer (esum + 3..5 =
+// S_EL0..S_EL2 relative to S_ESUM).
 template <typename T, int NZM, typename Out>
 __global__ void __launch_bounds__(256) k_zstage(const ZStageC *__restrict__ zc, const T *__restrict__ in,
                                                 Out czpsi, Out szpsi, double *__restrict__ esum) {
   const int nx = zc->nx, ny = zc->ny, nz = zc->nz;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (zc->mode2d) {
+    T el[3] = {0, 0, 0};
+    if (t < nx * ny) {
+      const int j = t % nx, k = t / nx;
+      const size_t plane = (size_t)nx * ny;
+      const T wj = (T)j * ZPar<T>::pdx(zc), wk = (T)k * ZPar<T>::pdy(zc);
+      const T w2 = wj * wj + wk * wk;
+      const T cw = (j | k) ? (j ? T(2) : T(1)) * (k ? T(2) : T(1)) / w2 : T(0);
+      const T invn = ZPar<T>::invn(zc);
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        const T a = in[l * plane + t] * invn;
+        const T psi = cw * a;
+        el[l] = cw * a * a;
+        czpsi.put(l * plane + t, psi);
+        szpsi.put(l * plane + t, T(0));
+      }
+    }
+    block_sum_atomic<3>(el, esum + (S_EL0 - S_ESUM));
+    return;
+  }
   T e = 0;
   if (t < nx * ny) {
     const int j = t % nx, k = t / nx;

@@ -20,11 +20,13 @@ template <typename T> struct WlC {
   T inv_g;     // 1/gamma
   T inv_gz;    // 1/gamma_z
   T fd_scale;  // 4/d_z (eq. fda-grad)
+  int mode2d;  // multi-die 2D (eq. 2d-place): W = WA(top + HBT) + WA(bottom + HBT), no z terms
 };
 
 template <typename T> struct Pin {
   int inst;
   bool top;
+  bool hbt;      // 2D mode: the net's HBT, a member of both partial nets
   T px, py, pz;  // pin on its current die
   T qx, qy;      // the same pin if its instance were on the other die
 };
@@ -34,10 +36,12 @@ __device__ __forceinline__ Pin<T> load_pin(int p, const int *__restrict__ pin_in
                                            const V4<T> *__restrict__ off,
                                            const V4<T> *__restrict__ pos, const WlC<T> &c) {
   Pin<T> q;
-  q.inst = __ldg(pin_inst + p);
+  const int raw = __ldg(pin_inst + p);  // HBT pins are stored as ~instance (2D mode)
+  q.hbt = raw < 0;
+  q.inst = q.hbt ? ~raw : raw;
   const V4<T> o = off[p];  // (bot x, bot y, top x, top y)
   const V4<T> s = pos[q.inst];
-  q.top = s.z > c.zmid;
+  q.top = !q.hbt && s.z > c.zmid;
   q.px = s.x + (q.top ? o.z : o.x);
   q.py = s.y + (q.top ? o.w : o.y);
   q.qx = s.x + (q.top ? o.x : o.z);
@@ -91,6 +95,13 @@ template <typename T> struct NetExt {
   }
   // slot: the pin's index within its net (identifies the extreme pins)
   __device__ __forceinline__ void add(const Pin<T> &p, int slot) {
+    if (p.hbt) {  // both partial nets; not counted as a die's pin
+      e[0][0].add(p.px, slot);
+      e[1][0].add(p.py, slot);
+      e[0][1].add(p.px, slot);
+      e[1][1].add(p.py, slot);
+      return;
+    }
     if (p.top) {
       e[0][1].add(p.px, slot);
       e[1][1].add(p.py, slot);
@@ -175,8 +186,7 @@ template <typename T> struct Sums {
 // extremes in x, y and by the net's extremes in z).
 template <typename T>
 __device__ __forceinline__ void pin_exps(const Pin<T> &p, const NetExt<T> &X, const WlC<T> &c,
-                                         T (&ex)[6]) {
-  const bool s = p.top;
+                                         T (&ex)[6], bool s) {
   const T xmx = s ? X.e[0][1].mx1 : X.e[0][0].mx1, xmn = s ? X.e[0][1].mn1 : X.e[0][0].mn1;
   const T ymx = s ? X.e[1][1].mx1 : X.e[1][0].mx1, ymn = s ? X.e[1][1].mn1 : X.e[1][0].mn1;
   ex[0] = r_exp((p.px - xmx) * c.inv_g);
@@ -188,22 +198,41 @@ __device__ __forceinline__ void pin_exps(const Pin<T> &p, const NetExt<T> &X, co
 }
 
 template <typename T>
-__device__ __forceinline__ void sums_add(Sums<T> &S, const Pin<T> &p, const T (&ex)[6]) {
+__device__ __forceinline__ void sums_add(Sums<T> &S, const Pin<T> &p, const T (&ex)[6], bool top) {
   const T v[4] = {ex[0], p.px * ex[0], ex[1], p.px * ex[1]};
   const T w[4] = {ex[2], p.py * ex[2], ex[3], p.py * ex[3]};
-  // predicated adds into the pin's side (no dynamic indexing: stays in registers)
+  // predicated adds into side `top` (no dynamic indexing: stays in registers)
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    S.v[0][1][k] += p.top ? v[k] : T(0);
-    S.v[0][0][k] += p.top ? T(0) : v[k];
-    S.v[1][1][k] += p.top ? w[k] : T(0);
-    S.v[1][0][k] += p.top ? T(0) : w[k];
+    S.v[0][1][k] += top ? v[k] : T(0);
+    S.v[0][0][k] += top ? T(0) : v[k];
+    S.v[1][1][k] += top ? w[k] : T(0);
+    S.v[1][0][k] += top ? T(0) : w[k];
   }
-  S.z[0] += ex[4];
-  S.z[1] += p.pz * ex[4];
-  S.z[2] += ex[5];
-  S.z[3] += p.pz * ex[5];
+  if (!p.hbt) {  // an HBT has no depth
+    S.z[0] += ex[4];
+    S.z[1] += p.pz * ex[4];
+    S.z[2] += ex[5];
+    S.z[3] += p.pz * ex[5];
+  }
 }
+
+// Sums of one pin: its side's, or both partial nets' for an HBT (2D mode).
+template <typename T>
+__device__ __forceinline__ void pin_sums(Sums<T> &S, const Pin<T> &p, const NetExt<T> &X, const WlC<T> &c) {
+  T ex[6];
+  if (p.hbt) {
+    pin_exps(p, X, c, ex, false);
+    sums_add(S, p, ex, false);
+    pin_exps(p, X, c, ex, true);
+    sums_add(S, p, ex, true);
+  } else {
+    pin_exps(p, X, c, ex, p.top);
+    sums_add(S, p, ex, p.top);
+  }
+}
+
+
 
 // Per-net results of one axis.
 template <typename T> struct AxisNet {
@@ -257,10 +286,10 @@ __device__ __forceinline__ AxisNet<T> axis_net(int a, const NetExt<T> &X, const 
   r.M = NP * r.iSP;
   r.m = NM * r.iSM;
   const T pall = r.M - r.m;
-  r.all = pall >= p[0] + p[1];
+  r.all = !c.mode2d && pall >= p[0] + p[1];  // 2D mode: always the two partial nets
   r.what = r.all ? pall : p[0] + p[1];
   const T hall = mxA - mnA;
-  r.wexact = hall > hp[0] + hp[1] ? hall : hp[0] + hp[1];
+  r.wexact = (!c.mode2d && hall > hp[0] + hp[1]) ? hall : hp[0] + hp[1];
   return r;
 }
 
@@ -341,6 +370,27 @@ __device__ __forceinline__ void pin_outputs(const Pin<T> &p, int slot, const T (
                moved_sel(s, X.e[1][1], X.e[1][0], ns, no, slot, p.qy);
   const T fd = c.fd_scale * (s ? (N.wcur - wm) : (wm - N.wcur));
   acc_add(acc + p.inst, g[0], g[1], fd, gz);
+}
+
+// 2D mode (eq. 2d-place): gradient of WA(top + HBT) + WA(bottom + HBT) at
+// one pin (both partial nets for an HBT); no FD and no z terms.
+template <typename T>
+__device__ __forceinline__ void pin_outputs_2d(const Pin<T> &p, const NetExt<T> &X, const NetScal<T> &N,
+                                               const WlC<T> &c, V4<T> *__restrict__ acc) {
+  T g[2] = {T(0), T(0)};
+  const T v[2] = {p.px, p.py};
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    if (!(p.hbt || (side == 1) == p.top)) continue;
+    T ex[6];
+    pin_exps(p, X, c, ex, side == 1);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const AxisNet<T> &A = N.ax[a];
+      g[a] += wa_grad(v[a], ex[2 * a], A.iSs[side], A.Ms[side], ex[2 * a + 1], A.iSm[side], A.ms[side], c.inv_g);
+    }
+  }
+  acc_add(acc + p.inst, g[0], g[1], T(0), T(0));
 }
 
 // ---- 2-pin nets, one thread per net, closed form ----
@@ -437,8 +487,8 @@ __device__ __forceinline__ void stage_ext(WlShared<T, GR> &sh, int grp, const Ne
 // Exponentials of one pin with the shifts read from the staged extremes.
 template <typename T, int GR>
 __device__ __forceinline__ void pin_exps_sh(const Pin<T> &p, const WlShared<T, GR> &sh, int grp, const WlC<T> &c,
-                                            T (&ex)[6]) {
-  const int s = p.top ? 1 : 0;
+                                            T (&ex)[6], bool side) {
+  const int s = side ? 1 : 0;
   const T xmx = sh.f[F_EXT + (0 + s) * 4 + 0][grp], xmn = sh.f[F_EXT + (0 + s) * 4 + 2][grp];
   const T ymx = sh.f[F_EXT + (2 + s) * 4 + 0][grp], ymn = sh.f[F_EXT + (2 + s) * 4 + 2][grp];
   ex[0] = r_exp((p.px - xmx) * c.inv_g);
@@ -513,8 +563,16 @@ __global__ void __launch_bounds__(wl_block<T>()) k_wl_group(int net0, int nnets,
     for (int r = 0; r < PPL; ++r)
       if (has[r]) {
         T ex[6];
-        pin_exps_sh(pin[r], sh, grp, c, ex);
-        sums_add(S, pin[r], ex);
+        const Pin<T> &q = pin[r];
+        if (q.hbt) {  // 2D mode: a member of both partial nets
+          pin_exps_sh(q, sh, grp, c, ex, false);
+          sums_add(S, q, ex, false);
+          pin_exps_sh(q, sh, grp, c, ex, true);
+          sums_add(S, q, ex, true);
+        } else {
+          pin_exps_sh(q, sh, grp, c, ex, q.top);
+          sums_add(S, q, ex, q.top);
+        }
       }
     S.template shfl_reduce<G>();
     if (d >= 2 && lane == 0) {
@@ -555,13 +613,36 @@ __global__ void __launch_bounds__(wl_block<T>()) k_wl_group(int net0, int nnets,
       sh.f[F_ZC + 3][grp] = N.zm;
       sh.f[F_WCUR][grp] = N.wcur;
       vals[0] = N.ax[0].what + N.ax[1].what;
-      vals[1] = N.pz;
+      vals[1] = c.mode2d ? T(0) : N.pz;
       vals[2] = N.wcur;
       vals[3] = (X.ntop > 0 && X.ntop < X.n) ? T(1) : T(0);
     }
   }
   __syncwarp();
-  if (d >= 2) {
+  if (d >= 2 && c.mode2d) {
+    // 2D mode: split-branch coefficients of each partial net, no FD, no z
+#pragma unroll
+    for (int r = 0; r < PPL; ++r)
+      if (has[r]) {
+        const Pin<T> &p = pin[r];
+        T g[2] = {T(0), T(0)};
+        const T v[2] = {p.px, p.py};
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          if (!(p.hbt || (side == 1) == p.top)) continue;
+          T ex[6];
+          pin_exps_sh(p, sh, grp, c, ex, side == 1);
+#pragma unroll
+          for (int a = 0; a < 2; ++a) {
+            const int b = F_COEF + (a * 2 + side) * 4;
+            const T A = sh.f[b + 0][grp], B = sh.f[b + 1][grp], C = sh.f[b + 2][grp], D = sh.f[b + 3][grp];
+            g[a] += (ex[2 * a] * A) * (T(1) + (v[a] - B) * c.inv_g) -
+                    (ex[2 * a + 1] * C) * (T(1) - (v[a] - D) * c.inv_g);
+          }
+        }
+        acc_add(acc + p.inst, g[0], g[1], T(0), T(0));
+      }
+  } else if (d >= 2) {
     const int ntop = sh.i[I_NTOP][grp], n = sh.i[I_N][grp];
     const T wcur = sh.f[F_WCUR][grp];
 #pragma unroll
@@ -569,7 +650,7 @@ __global__ void __launch_bounds__(wl_block<T>()) k_wl_group(int net0, int nnets,
       if (has[r]) {
         const Pin<T> &p = pin[r];
         T ex[6];  // recomputed: keeping them live across the reductions costs registers
-        pin_exps_sh(p, sh, grp, c, ex);
+        pin_exps_sh(p, sh, grp, c, ex, p.top);
         const int s = p.top ? 1 : 0;
         T g[2];
         const T v[2] = {p.px, p.py};
@@ -615,12 +696,7 @@ __global__ void __launch_bounds__(256) k_wl_block(int net0, const int *__restric
   X = sx[0];
   Sums<T> S;
   S.init();
-  for (int k = tid; k < d; k += blockDim.x) {
-    const Pin<T> p = load_pin(s0 + k, pin_inst, off, pos, c);
-    T ex[6];
-    pin_exps(p, X, c, ex);
-    sums_add(S, p, ex);
-  }
+  for (int k = tid; k < d; k += blockDim.x) pin_sums(S, load_pin(s0 + k, pin_inst, off, pos, c), X, c);
   S.template shfl_reduce<32>();
   if (lane == 0) ss[warp] = S;
   __syncthreads();
@@ -632,13 +708,17 @@ __global__ void __launch_bounds__(256) k_wl_block(int net0, const int *__restric
   const NetScal<T> N = net_scalars(X, S, c);
   for (int k = tid; k < d; k += blockDim.x) {
     const Pin<T> p = load_pin(s0 + k, pin_inst, off, pos, c);
-    T ex[6];
-    pin_exps(p, X, c, ex);
-    pin_outputs(p, k, ex, X, S, N, c, acc);
+    if (c.mode2d) {
+      pin_outputs_2d(p, X, N, c, acc);
+    } else {
+      T ex[6];
+      pin_exps(p, X, c, ex, p.top);
+      pin_outputs(p, k, ex, X, S, N, c, acc);
+    }
   }
   if (tid == 0) {
     atomicAdd(scal + S_WL_BI, (double)N.ax[0].what + (double)N.ax[1].what);
-    atomicAdd(scal + S_WL_Z, (double)N.pz);
+    if (!c.mode2d) atomicAdd(scal + S_WL_Z, (double)N.pz);
     atomicAdd(scal + S_HPWL, (double)N.wcur);
     if (X.ntop > 0 && X.ntop < X.n) atomicAdd(scal + S_NCROSS, 1.0);
   }

@@ -25,6 +25,7 @@ FLAG_MACRO_GATHER_SCAN, FLAG_MACRO_GATHER_DIRECT, FLAG_SERIAL, FLAG_TILES = 2, 4
 WL_FORMS = ((1, 1), (1, 2), (1, 4), (2, 2), (4, 1), (2, 4), (8, 1), (4, 4), (16, 1), (8, 4), (32, 1), (16, 4), (32, 2),
             (32, 4))
 MAP_RHO_FIXED, MAP_EX, MAP_EY, MAP_EZ = 0, 1, 2, 3
+MODE_3D, MODE_2D = 0, 1
 ERRORS = {-1: "INVALID_ARG", -2: "BAD_CSR", -3: "OUT_OF_RANGE", -4: "CUDA", -5: "OOM", -6: "TIMEOUT",
           -7: "UNSUPPORTED"}
 
@@ -46,15 +47,18 @@ class _Problem(C.Structure):
         ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
         ("gamma", C.c_double), ("gamma_z", C.c_double), ("alpha", C.c_double), ("lam", C.c_double),
         ("precision", C.c_int32), ("flags", C.c_int32),
+        ("mode", C.c_int32), ("is_hbt", C.c_void_p), ("lam_layer", C.c_double * 3),
     ]
 
 
 class Result(C.Structure):
     _fields_ = [(k, C.c_double) for k in ("obj", "wl_bi", "wl_z", "energy", "hpwl_d2d", "n_cross",
-                                           "g_scale", "s_x", "s_y", "s_z")]
+                                           "g_scale", "s_x", "s_y", "s_z")] + [("energy_layer", C.c_double * 3)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_[:-1]}
+        d["energy_layer"] = list(self.energy_layer)
+        return d
 
 
 EXPORTS = ("place3d_create", "place3d_geometry", "place3d_alpha", "place3d_set_positions",
@@ -63,7 +67,7 @@ EXPORTS = ("place3d_create", "place3d_geometry", "place3d_alpha", "place3d_set_p
            "place3d_stage_times", "place3d_launches_per_eval", "place3d_last_error", "place3d_destroy",
            "place3d_density_map_noalloc", "place3d_tc_selftest", "place3d_autotune", "place3d_wl_forms",
            "place3d_set_wl_form", "place3d_result_to_device", "place3d_set_params", "place3d_eval_graph",
-           "place3d_batch_create", "place3d_batch_eval", "place3d_batch_destroy")
+           "place3d_batch_create", "place3d_batch_eval", "place3d_batch_destroy", "place3d_set_layer_weights")
 NOALLOC_MAX_BINS = 262144
 
 _lib = None
@@ -113,6 +117,7 @@ def load_library(build_if_missing: bool = True):
     L.place3d_batch_destroy.argtypes = [vp]
     L.place3d_batch_destroy.restype = None
     L.place3d_set_params.argtypes = [vp, d, d, d, d]
+    L.place3d_set_layer_weights.argtypes = [vp, vp]
     L.place3d_wl_forms.argtypes = [vp, vp, vp, vp, i32]
     L.place3d_tc_selftest.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp]
     L.place3d_density_map_noalloc.argtypes = [i32] + [vp] * 8 + [d] * 4 + [i32] * 3 + [vp, vp]
@@ -188,6 +193,10 @@ class Place3D:
         p.lam = float(prob["lam"])
         p.precision = int(precision)
         p.flags = int(flags)
+        p.mode = int(prob.get("mode", MODE_3D))
+        p.is_hbt = arr("is_hbt", np.uint8) if prob.get("is_hbt") is not None else None
+        p.lam_layer = (C.c_double * 3)(*[float(v) for v in prob.get("lam_layer", (prob["lam"],) * 3)])
+        self.mode = p.mode
         if stream is not None and hasattr(stream, "cuda_stream"):
             stream = stream.cuda_stream
         h = C.c_void_p()
@@ -256,6 +265,10 @@ class Place3D:
     def set_params(self, gamma: float, gamma_z: float, alpha: float, lam: float):
         self._check(self._L.place3d_set_params(self._h, float(gamma), float(gamma_z), float(alpha), float(lam)))
         self.alpha = float(alpha)
+
+    def set_layer_weights(self, lam_bot: float, lam_top: float, lam_hbt: float):
+        """2D mode: the density weights (lambda-, lambda+, lambda') of eq. 2d-place."""
+        self._check(self._L.place3d_set_layer_weights(self._h, (C.c_double * 3)(lam_bot, lam_top, lam_hbt)))
 
     def eval_graph(self, x, y, z, gx, gy, gz):
         """Pack + evaluate as one CUDA-graph launch (CUDA tensors; the graph is

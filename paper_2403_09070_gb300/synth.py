@@ -243,6 +243,8 @@ def append_fillers(prob: dict, fp: dict, seed: int = 0, positions: str = "center
     zf0 = prob.get("z_fixed")
     zf0 = np.zeros(n0, np.uint8) if zf0 is None else np.asarray(zf0, np.uint8)
     out["z_fixed"] = np.concatenate([zf0, np.ones(nt + nb, np.uint8), np.zeros(nf, np.uint8)])
+    if prob.get("is_hbt") is not None:  # a 2D problem: fillers are not HBTs
+        out["is_hbt"] = np.concatenate([np.asarray(prob["is_hbt"], np.uint8), np.zeros(nfill, np.uint8)])
     xl, yl, xh, yh = prob["xl"], prob["yl"], prob["xh"], prob["yh"]
     fz = np.empty(nfill)
     fz[:nt] = zhi
