@@ -37,7 +37,7 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="place3d", choices=["place3d", "reference"])
     ap.add_argument("--workload", default="cells_1m", help="cells_2k|cells_200k|cells_1m|cells_4m_skewed|batch24")
@@ -604,12 +604,20 @@ def _fp64_plain(prob, torch, P, steps=5, warmup=2):
 
 
 def _profiled_traffic(stage, workload, precision):
-    """DRAM bytes per evaluation of a stage from the committed ncu summary of
-    the current kernels, if one exists (profiles/traffic.json), else None."""
+    """DRAM bytes (read + write) per evaluation of a stage's kernels from the
+    committed ncu launch list (profiles/traffic.json), or None when there is
+    none or when any source file it lists has changed since the capture
+    (its SHA-256 no longer matches)."""
+    import hashlib
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        return t[workload][precision][stage]
-    except (OSError, ValueError, KeyError):
+        e = t[workload][precision][stage]
+        for path, digest in e["sources"].items():
+            with open(os.path.join(ROOT, path), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != digest:
+                    return None
+        return e["bytes_per_eval"]
+    except (OSError, ValueError, KeyError, TypeError):
         return None
 
 
