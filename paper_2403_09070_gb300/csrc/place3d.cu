@@ -67,7 +67,11 @@ struct place3d_handle {
   bool mode2d = false;                 // multi-die 2D placement (eq. 2d-place)
   double lam_layer[3] = {0, 0, 0};     // 2D mode: density weights of the three layers
   cudaStream_t stream = nullptr, side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_dens = nullptr;
+  // the density path (the critical chain into the final gather) runs on a
+  // greatest-priority stream so that its kernels take SMs first; the
+  // wirelength path fills the rest
+  cudaStream_t dens = nullptr;
   int precision = 0, flags = 0;
   bool macro_direct = true;  // bin-parallel direct macro gather (else Theorem 1 suffix sums)
   // tile-bucketed scatter / gather
@@ -390,12 +394,14 @@ void launch_final_tiles(place3d_handle *h, cudaStream_t s, const DensC<T> &dc, c
 }
 
 template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void *gz, int dtype, int mem) {
-  cudaStream_t s = h->stream, w = (h->flags & PLACE3D_FLAG_SERIAL) ? h->stream : h->side;
+  const bool serial = (h->flags & PLACE3D_FLAG_SERIAL) != 0;
+  cudaStream_t caller = h->stream, s = serial ? caller : h->dens, w = serial ? caller : h->side;
   const int n = h->n;
   const DensC<T> dc = dens_consts<T>(h, h->xl, h->yl);
   h->launches = 0;
-  P3D_CUDA(h, cudaMemsetAsync(h->scal, 0, sizeof(double) * S_COUNT, s));
-  P3D_CUDA(h, cudaEventRecord(h->ev_fork, s));
+  P3D_CUDA(h, cudaMemsetAsync(h->scal, 0, sizeof(double) * S_COUNT, caller));  // before the fork: both paths add
+  P3D_CUDA(h, cudaEventRecord(h->ev_fork, caller));
+  if (s != caller) P3D_CUDA(h, cudaStreamWaitEvent(s, h->ev_fork, 0));
   // ---------------- wirelength path (side stream) ----------------
   P3D_CUDA(h, cudaStreamWaitEvent(w, h->ev_fork, 0));
   {
@@ -527,6 +533,10 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
       P3D_CUDA(h, cudaMemcpyAsync(gz, oz, (size_t)n * tb, k, s));
     }
   }
+  if (s != caller) {
+    P3D_CUDA(h, cudaEventRecord(h->ev_dens, s));
+    P3D_CUDA(h, cudaStreamWaitEvent(caller, h->ev_dens, 0));
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
   if (h->profiling) h->prof_evals++;
@@ -573,7 +583,9 @@ void free_all(place3d_handle *h) {
   for (auto &e : h->ev_live) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_dens) cudaEventDestroy(h->ev_dens);
   if (h->side) cudaStreamDestroy(h->side);
+  if (h->dens) cudaStreamDestroy(h->dens);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
 }
@@ -841,9 +853,13 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
       return bail(e == cudaErrorMemoryAllocation ? PLACE3D_ERR_OOM : PLACE3D_ERR_CUDA);
     }
   }
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&h->dens, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_dens, cudaEventDisableTiming) != cudaSuccess) {
     fail(h, PLACE3D_ERR_CUDA, "stream/event creation failed");
     return bail(PLACE3D_ERR_CUDA);
   }
@@ -1109,9 +1125,22 @@ int place3d_copy_wl_parts(place3d_handle *h, double *gx, double *gy, double *gfd
 
 // Result scalars on the device (one thread): obj, wl_bi, wl_z, energy,
 // hpwl_d2d, n_cross, g_scale, s_x, s_y, s_z (the place3d_result order).
-__global__ void k_result(const double *__restrict__ s, double alpha, double lambda, double ef, double *__restrict__ out) {
-  const double energy = ef * s[S_ESUM];
-  out[0] = s[S_WL_BI] + alpha * s[S_WL_Z] + lambda * energy;
+// 2D mode (l2 != NULL): energy = sum of the layer energies ef * S_EL*, obj = wl + sum_l l2[l] U_l.
+struct Lam3 {
+  double v[3];
+};
+__global__ void k_result(const double *__restrict__ s, double alpha, double lambda, double ef, int mode2d, Lam3 l2,
+                         double *__restrict__ out) {
+  double energy = ef * s[S_ESUM], obj = s[S_WL_BI] + alpha * s[S_WL_Z] + lambda * energy;
+  if (mode2d) {
+    energy = 0.0;
+    obj = s[S_WL_BI];
+    for (int l = 0; l < 3; ++l) {
+      energy += ef * s[S_EL0 + l];
+      obj += l2.v[l] * ef * s[S_EL0 + l];
+    }
+  }
+  out[0] = obj;
   out[1] = s[S_WL_BI];
   out[2] = s[S_WL_Z];
   out[3] = energy;
@@ -1126,8 +1155,10 @@ __global__ void k_result(const double *__restrict__ s, double alpha, double lamb
 int place3d_result_to_device(place3d_handle *h, double *dst) {
   if (!h || !dst) return fail(h, PLACE3D_ERR_INVALID_ARG, "NULL argument");
   P3D_CUDA(h, cudaSetDevice(h->device));
-  const double ef = 0.5 * (h->wb * h->hb * h->db) * (double)h->nb;
-  k_result<<<1, 1, 0, h->stream>>>(h->scal, h->alpha, h->lambda, ef, dst);
+  const double ef = h->mode2d ? 0.5 * (h->wb * h->hb) * (double)h->nx * h->ny
+                              : 0.5 * (h->wb * h->hb * h->db) * (double)h->nb;
+  Lam3 l2{{h->lam_layer[0], h->lam_layer[1], h->lam_layer[2]}};
+  k_result<<<1, 1, 0, h->stream>>>(h->scal, h->alpha, h->lambda, ef, h->mode2d ? 1 : 0, l2, dst);
   P3D_CUDA(h, cudaGetLastError());
   return PLACE3D_OK;
 }
@@ -1438,6 +1469,7 @@ void place3d_destroy(place3d_handle *h) {
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
   if (h->side) cudaStreamSynchronize(h->side);
+  if (h->dens) cudaStreamSynchronize(h->dens);
   free_all(h);
   delete h;
 }

@@ -124,3 +124,18 @@ def test_graph_recaptures_after_set_params():
     assert rg["obj"] == pytest.approx(re["obj"], rel=1e-12)
     for a, b in zip(gg, ge):
         assert rel_max(a, b) < 1e-12
+
+
+def test_2d_result_to_device_matches_host_result():
+    from paper_2403_09070_gb300 import place3d as P
+    q = _problem2d()
+    with P.Place3D(q, precision="fp32") as h:
+        h.set_positions(*(np.asarray(q[k], np.float32) for k in ("x", "y", "z")))
+        r = h.eval(*[np.zeros(q["n_inst"], np.float32) for _ in range(3)])
+        dev = torch.zeros(10, dtype=torch.float64, device="cuda")
+        h.result_to_device(dev)
+        v = dev.cpu().numpy()
+    keys = ("obj", "wl_bi", "wl_z", "energy", "hpwl_d2d", "n_cross")
+    for k, got in zip(keys, v[:6]):
+        assert got == pytest.approx(r[k], rel=1e-12), k
+    assert r["energy"] == pytest.approx(sum(r["energy_layer"]), rel=1e-12)
