@@ -123,6 +123,57 @@ __device__ __forceinline__ void block_sum_atomic(T (&v)[NV], double *dst) {
   }
 }
 
+// Warp-wide sum of NV values stored (plain store) into this warp's row
+// part[global warp][NV]; k_sum_parts adds the rows up later.  No block
+// barrier and no atomics: a block-wide reduction at the end of a kernel makes
+// every warp wait for the block's slowest one, and thousands of FP64 atomics
+// to the same words serialise in the L2.  One-dimensional grids with whole
+// warps; every lane must call it.
+template <int NV, typename T>
+__device__ __forceinline__ void warp_sum_part(T (&v)[NV], double *__restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const size_t row = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    T s = v[k];
+#pragma unroll
+    for (int m = 16; m; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    if (lane == 0) part[row * NV + k] = (double)s;
+  }
+}
+
+// dst[k] += sum over rows r < rows of part[r][NV] (FP64): a grid-stride
+// pass, one block reduction and one atomic per block and value.
+constexpr int kSumBlocks = 64;
+template <int NV>
+__global__ void __launch_bounds__(256) k_sum_parts(const double *__restrict__ part, int rows,
+                                                   double *__restrict__ dst) {
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] += part[(size_t)r * NV + k];
+  __shared__ double red[8][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = acc[k];
+#pragma unroll
+    for (int m = 16; m; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    if (lane == 0) red[warp][k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < 8; ++w) s += red[w][k];
+      if (s != 0.0) atomicAdd(dst + k, s);
+    }
+  }
+}
+
 // Map writers: plain values, or an FP32 value split into two BF16 planes
 // (hi = bf16(v), lo = bf16(v - hi); lo plane `plane` elements after hi) for
 // the tensor-core products.

@@ -101,6 +101,10 @@ struct place3d_handle {
   void *mats = nullptr;
   size_t mat_off[5] = {0, 0, 0, 0, 0};  // Fx, Fy, Bx(=[Sx;Cx]), Cy, Sy (elements)
   double *suffix = nullptr, *mgrad = nullptr, *scal = nullptr;
+  // per-block partial sums of the scalars (rows of 4 / 3 doubles), added up
+  // once per path by k_sum_parts: wirelength kernels then norms (part_w),
+  // the z stage (part_d)
+  double *part_w = nullptr, *part_d = nullptr;
   ZStageC *zc = nullptr;
   void *gout = nullptr;  // internal gradient output [3][n] (handle precision)
   void *stage_in = nullptr;  // staging for host positions [3][n] doubles
@@ -280,30 +284,34 @@ void launch_gemm(place3d_handle *h, cudaStream_t s, std::initializer_list<GemmPr
   count_launch(h, stage);
 }
 
+// Launches one bucket's wirelength kernel; the group and pair forms write
+// one row of 4 partial sums per warp at part (returns the row count), the
+// block form adds its per-net sums to the scalars directly (returns 0).
 template <typename T>
-void launch_wl(place3d_handle *h, const Bucket &b, int G, int PPL, cudaStream_t w, const WlC<T> &c) {
+int launch_wl(place3d_handle *h, const Bucket &b, int G, int PPL, cudaStream_t w, const WlC<T> &c, double *part) {
   V4<T> *acc = as<V4<T>>(h->acc);
   const V4<T> *pos = as<V4<T>>(h->pos), *off = as<V4<T>>(h->off);
   if (G == 0) {
     k_wl_block<T><<<b.count, 256, 0, w>>>(b.first, h->net_start, h->pin_inst, off, pos, c, acc, h->scal);
-    return;
+    return 0;
   }
   if (G == 1 && PPL == 1) {  // 2-pin nets, closed form
     k_wl_pair<T><<<grid_for(b.count, 256), 256, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c,
-                                                        acc, h->scal);
-    return;
+                                                        acc, part);
+    return grid_for(b.count, 256) * (256 / 32);
   }
   constexpr int BS = wl_block<T>();
   const int blocks = grid_for((long long)b.count * G, BS);
 #define P3D_WL(GG, PP)                                                                                    \
   if (G == GG && PPL == PP) {                                                                             \
     k_wl_group<T, GG, PP><<<blocks, BS, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, \
-                                                acc, h->scal);                                            \
-    return;                                                                                               \
+                                                acc, part);                                               \
+    return blocks * (BS / 32);                                                                            \
   }
   P3D_WL(1, 2) P3D_WL(1, 4) P3D_WL(2, 2) P3D_WL(4, 1) P3D_WL(2, 4) P3D_WL(8, 1) P3D_WL(4, 4)
   P3D_WL(16, 1) P3D_WL(8, 4) P3D_WL(32, 1) P3D_WL(16, 4) P3D_WL(32, 2) P3D_WL(32, 4)
 #undef P3D_WL
+  return 0;
 }
 
 template <typename T> WlC<T> wl_consts(const place3d_handle *h) {
@@ -314,6 +322,20 @@ template <typename T> WlC<T> wl_consts(const place3d_handle *h) {
   c.fd_scale = (T)(4.0 / h->dz);
   c.mode2d = h->mode2d ? 1 : 0;
   return c;
+}
+
+// Add the z stage's per-block energy rows into the scalars (one per layer in 2D mode).
+int sum_grid(int rows) { return std::max(1, std::min(kSumBlocks, grid_for(rows, 256))); }
+
+// Add the z stage's per-warp energy rows (blocks of 256 threads) into the
+// scalars (one per layer in 2D mode).
+void sum_energy(place3d_handle *h, cudaStream_t s, int blocks) {
+  const int rows = blocks * 8;
+  if (h->mode2d)
+    k_sum_parts<3><<<sum_grid(rows), 256, 0, s>>>(h->part_d, rows, h->scal + S_EL0);
+  else
+    k_sum_parts<1><<<sum_grid(rows), 256, 0, s>>>(h->part_d, rows, h->scal + S_ESUM);
+  count_launch(h, ST_ZSTAGE);
 }
 
 // The spectral solve: rho -> E_x, E_y, E_z (and the energy sum).
@@ -333,7 +355,7 @@ template <typename T> void run_transforms(place3d_handle *h, cudaStream_t s) {
     const int g = grid_for(pl, 256);
     const T *t2 = as<T>(h->t2);
     const OutPlain<T> cz{as<T>(h->czpsi)}, sz{as<T>(h->szpsi)};
-    double *es = h->scal + S_ESUM;
+    double *es = h->part_d;
     if (nz <= 2)
       k_zstage<T, 2><<<g, 256, 0, s>>>(h->zc, t2, cz, sz, es);
     else if (nz <= 4)
@@ -343,6 +365,7 @@ template <typename T> void run_transforms(place3d_handle *h, cudaStream_t s) {
     else
       k_zstage<T, 16><<<g, 256, 0, s>>>(h->zc, t2, cz, sz, es);
     count_launch(h, ST_ZSTAGE);
+    sum_energy(h, s, g);
   }
   {
     StageScope sc(h, ST_INV, s);
@@ -367,8 +390,9 @@ void run_transforms_tc(place3d_handle *h, cudaStream_t s) {
   }
   {
     StageScope sc(h, ST_ZSTAGE, s);
-    const int k = p3d_tc::zstage(h->tc, s, h->scal + S_ESUM);
+    const int k = p3d_tc::zstage(h->tc, s, h->part_d);
     for (int i = 0; i < k; ++i) count_launch(h, ST_ZSTAGE);
+    sum_energy(h, s, (int)(((long long)h->nx * h->ny + 255) / 256));
   }
   {
     StageScope sc(h, ST_INV, s);
@@ -408,14 +432,22 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     StageScope sc(h, ST_WIRELENGTH, w);
     P3D_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(V4<T>) * (size_t)std::max(n, 1), w));
     const WlC<T> c = wl_consts<T>(h);
+    int rows = 0;
     for (const Bucket &b : h->buckets) {
-      launch_wl<T>(h, b, b.G, b.PPL, w, c);
+      rows += launch_wl<T>(h, b, b.G, b.PPL, w, c, h->part_w + 4 * (size_t)rows);
+      count_launch(h, ST_WIRELENGTH);
+    }
+    if (rows > 0) {
+      k_sum_parts<4><<<sum_grid(rows), 256, 0, w>>>(h->part_w, rows, h->scal + S_WL_BI);
       count_launch(h, ST_WIRELENGTH);
     }
   }
   {
     StageScope sc(h, ST_NORMS, w);
-    k_norms<T><<<std::min(grid_for(std::max(n, 1), 256), 1216), 256, 0, w>>>(n, as<V4<T>>(h->acc), h->scal);
+    const int gn = std::min(grid_for(std::max(n, 1), 256), 1216);
+    k_norms<T><<<gn, 256, 0, w>>>(n, as<V4<T>>(h->acc), h->part_w);
+    k_sum_parts<3><<<sum_grid(gn * 8), 256, 0, w>>>(h->part_w, gn * 8, h->scal + S_SX);
+    count_launch(h, ST_NORMS);
     count_launch(h, ST_NORMS);
   }
   P3D_CUDA(h, cudaEventRecord(h->ev_join, w));
@@ -575,6 +607,7 @@ void free_all(place3d_handle *h) {
                   h->net_start, h->pin_inst, h->q, h->corner, h->rho, h->t1, h->t2, h->czpsi,
                   h->szpsi, h->xinv, h->x2, h->e4, h->mats, h->suffix, h->mgrad,
                   h->scal, h->zc, h->gout, h->stage_in, h->check_flag, h->tkey, h->titems,
+                  h->part_w, h->part_d,
                   h->tcount, h->tstart, h->tnitems, h->trec, h->g4};
   for (void *b : bufs)
     if (b) cudaFree(b);
@@ -851,6 +884,20 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
     if (e != cudaSuccess) {
       cuda_fail(h, e, "cudaMalloc");
       return bail(e == cudaErrorMemoryAllocation ? PLACE3D_ERR_OOM : PLACE3D_ERR_CUDA);
+    }
+  }
+  {
+    // partial-sum rows (one per warp) for the largest grids any bucket form
+    // may use (G <= 32)
+    const int bs = h->precision == PLACE3D_FP64 ? wl_block<double>() : wl_block<float>();
+    size_t rw = 1216 * 8;  // k_norms
+    for (const Bucket &b : h->buckets)
+      rw += (size_t)std::max(grid_for((long long)b.count * 32, bs) * (bs / 32), grid_for(b.count, 256) * 8);
+    const size_t rd = (size_t)std::max(grid_for((long long)h->nx * h->ny, 256), 1) * 8;
+    if (cudaMalloc(&h->part_w, sizeof(double) * 4 * rw) != cudaSuccess ||
+        cudaMalloc(&h->part_d, sizeof(double) * 3 * rd) != cudaSuccess) {
+      fail(h, PLACE3D_ERR_OOM, "cudaMalloc (partial-sum rows)");
+      return bail(PLACE3D_ERR_OOM);
     }
   }
   int prio_lo = 0, prio_hi = 0;
@@ -1206,9 +1253,9 @@ int place3d_autotune(place3d_handle *h, int repeats) {
       for (int r = 0; r <= repeats; ++r) {  // first run warms up
         if (r == 1) cudaEventRecord(e0, w);
         if (h->precision == PLACE3D_FP64)
-          launch_wl<double>(h, b, G, PPL, w, wl_consts<double>(h));
+          launch_wl<double>(h, b, G, PPL, w, wl_consts<double>(h), h->part_w);
         else
-          launch_wl<float>(h, b, G, PPL, w, wl_consts<float>(h));
+          launch_wl<float>(h, b, G, PPL, w, wl_consts<float>(h), h->part_w);
       }
       cudaEventRecord(e1, w);
       P3D_CUDA(h, cudaEventSynchronize(e1));

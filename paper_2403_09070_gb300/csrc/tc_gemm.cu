@@ -539,18 +539,18 @@ int forward(TcPlan *p, cudaStream_t s) {
   return 2;
 }
 
-int zstage(TcPlan *p, cudaStream_t s, double *esum) {
+int zstage(TcPlan *p, cudaStream_t s, double *part) {
   const int pl = p->nx * p->ny;
   const int g = (pl + 255) / 256;
   const OutSplit cz{p->cz, (long long)p->nb}, sz{p->sz, (long long)p->nb};
   if (p->nz <= 2)
-    k_zstage<float, 2><<<g, 256, 0, s>>>(p->zc, p->t2, cz, sz, esum);
+    k_zstage<float, 2><<<g, 256, 0, s>>>(p->zc, p->t2, cz, sz, part);
   else if (p->nz <= 4)
-    k_zstage<float, 4><<<g, 256, 0, s>>>(p->zc, p->t2, cz, sz, esum);
+    k_zstage<float, 4><<<g, 256, 0, s>>>(p->zc, p->t2, cz, sz, part);
   else if (p->nz <= 8)
-    k_zstage<float, 8><<<g, 256, 0, s>>>(p->zc, p->t2, cz, sz, esum);
+    k_zstage<float, 8><<<g, 256, 0, s>>>(p->zc, p->t2, cz, sz, part);
   else
-    k_zstage<float, 16><<<g, 256, 0, s>>>(p->zc, p->t2, cz, sz, esum);
+    k_zstage<float, 16><<<g, 256, 0, s>>>(p->zc, p->t2, cz, sz, part);
   return 1;
 }
 

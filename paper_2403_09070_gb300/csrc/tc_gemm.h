@@ -25,7 +25,7 @@ void densify(TcPlan *p, cudaStream_t s, int nxy, int nz, const long long *q, con
 // Forward x and y products; z stage (scaling, energy, z transforms);
 // inverse x and y products into the interleaved field map e4.  Each returns its launch count.
 int forward(TcPlan *p, cudaStream_t s);
-int zstage(TcPlan *p, cudaStream_t s, double *esum);
+int zstage(TcPlan *p, cudaStream_t s, double *part);  // per-block energy rows (see k_zstage)
 int inverse(TcPlan *p, cudaStream_t s);
 // Error code left by a bounded wait of the tensor-core kernel (0 = none);
 // synchronises with the device.

@@ -122,11 +122,12 @@ template <> struct ZPar<float> {
 // All arithmetic in T (FP32 threads stay off the FP64 pipe); the energy sum
 // is widened to FP64 per warp.  2D mode (zc->mode2d, N_z = 3 layers): no z
 // transform, psi = c_j c_k a / (w_j^2 + w_k^2) per layer with a = (1/(N_x
-// N_y)) T2, E_z = 0 (Szpsi = 0), one energy sum per layer (esum + 3..5 =
-// S_EL0..S_EL2 relative to S_ESUM).
+// N_y)) T2, E_z = 0 (Szpsi = 0), one energy sum per layer.  The block
+// sums go to part[block][1] (3D) or part[block][3] (2D), added up by
+// k_sum_parts into S_ESUM or S_EL0..S_EL2.
 template <typename T, int NZM, typename Out>
 __global__ void __launch_bounds__(256) k_zstage(const ZStageC *__restrict__ zc, const T *__restrict__ in,
-                                                Out czpsi, Out szpsi, double *__restrict__ esum) {
+                                                Out czpsi, Out szpsi, double *__restrict__ part) {
   const int nx = zc->nx, ny = zc->ny, nz = zc->nz;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (zc->mode2d) {
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(256) k_zstage(const ZStageC *__restrict__ zc, 
         szpsi.put(l * plane + t, T(0));
       }
     }
-    block_sum_atomic<3>(el, esum + (S_EL0 - S_ESUM));
+    warp_sum_part<3>(el, part);  // per-layer energy rows
     return;
   }
   T e = 0;
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(256) k_zstage(const ZStageC *__restrict__ zc, 
     }
   }
   T v1[1] = {e};
-  block_sum_atomic<1>(v1, esum);
+  warp_sum_part<1>(v1, part);  // energy rows
 }
 
 }  // namespace p3d

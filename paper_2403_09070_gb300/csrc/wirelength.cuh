@@ -414,7 +414,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_wl_pair(int net0, int nnets, const int *__restrict__ net_start,
                                                  const int *__restrict__ pin_inst, const V4<T> *__restrict__ off,
                                                  const V4<T> *__restrict__ pos, WlC<T> c, V4<T> *__restrict__ acc,
-                                                 double *__restrict__ scal) {
+                                                 double *__restrict__ part) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   T vals[4] = {0, 0, 0, 0};
   if (t < nnets) {
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(256) k_wl_pair(int net0, int nnets, const int 
     vals[2] = W;
     vals[3] = a.top != b.top ? T(1) : T(0);
   }
-  block_sum_atomic<4>(vals, scal + S_WL_BI);
+  warp_sum_part<4>(vals, part);  // (W^_Bi, p^(z), W_Bi, crossing) rows
 }
 
 // ---- nets of degree <= G*PPL, one group of G lanes per net ----
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(wl_block<T>()) k_wl_group(int net0, int nnets,
                                                             const int *__restrict__ pin_inst,
                                                             const V4<T> *__restrict__ off,
                                                             const V4<T> *__restrict__ pos, WlC<T> c,
-                                                            V4<T> *__restrict__ acc, double *__restrict__ scal) {
+                                                            V4<T> *__restrict__ acc, double *__restrict__ part) {
   constexpr int GR = wl_block<T>() / G;  // groups (nets) per block
   __shared__ WlShared<T, GR> sh;
   const int lane = threadIdx.x & (G - 1);
@@ -668,7 +668,7 @@ __global__ void __launch_bounds__(wl_block<T>()) k_wl_group(int net0, int nnets,
         acc_add(acc + p.inst, g[0], g[1], fd, gz);
       }
   }
-  block_sum_atomic<4>(vals, scal + S_WL_BI);
+  warp_sum_part<4>(vals, part);  // (W^_Bi, p^(z), W_Bi, crossing) rows
 }
 
 // ---- high-fanout nets: one block (256 threads) per net, three passes ----
@@ -726,7 +726,7 @@ __global__ void __launch_bounds__(256) k_wl_block(int net0, const int *__restric
 
 // ---- a9: L1 norms S_x, S_y, S_z of the wirelength gradient (FP64) ----
 template <typename T>
-__global__ void __launch_bounds__(256) k_norms(int n, const V4<T> *__restrict__ acc, double *__restrict__ scal) {
+__global__ void __launch_bounds__(256) k_norms(int n, const V4<T> *__restrict__ acc, double *__restrict__ part) {
   T v[3] = {0, 0, 0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const V4<T> a = acc[i];
@@ -734,7 +734,7 @@ __global__ void __launch_bounds__(256) k_norms(int n, const V4<T> *__restrict__ 
     v[1] += fabs(a.y);
     v[2] += fabs(a.z);
   }
-  block_sum_atomic<3>(v, scal + S_SX);
+  warp_sum_part<3>(v, part);  // (S_x, S_y, S_z) rows
 }
 
 }  // namespace p3d
