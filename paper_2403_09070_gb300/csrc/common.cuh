@@ -144,7 +144,7 @@ __device__ __forceinline__ void warp_sum_part(T (&v)[NV], double *__restrict__ p
 
 // dst[k] += sum over rows r < rows of part[r][NV] (FP64): a grid-stride
 // pass, one block reduction and one atomic per block and value.
-constexpr int kSumBlocks = 64;
+constexpr int kSumBlocks = 256;
 template <int NV>
 __global__ void __launch_bounds__(256) k_sum_parts(const double *__restrict__ part, int rows,
                                                    double *__restrict__ dst) {

@@ -410,15 +410,17 @@ __device__ __forceinline__ T wa_pair(T va, T vb, T inv_g, T &ga) {
   return L * th;
 }
 
+// The bucket's nets all have two pins, stored back to back from pin0: net t
+// holds pins pin0 + 2t and pin0 + 2t + 1 (no net_start load on the chain).
 template <typename T>
-__global__ void __launch_bounds__(256) k_wl_pair(int net0, int nnets, const int *__restrict__ net_start,
+__global__ void __launch_bounds__(256) k_wl_pair(int pin0, int nnets,
                                                  const int *__restrict__ pin_inst, const V4<T> *__restrict__ off,
                                                  const V4<T> *__restrict__ pos, WlC<T> c, V4<T> *__restrict__ acc,
                                                  double *__restrict__ part) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   T vals[4] = {0, 0, 0, 0};
   if (t < nnets) {
-    const int s0 = __ldg(net_start + net0 + t);
+    const int s0 = pin0 + 2 * t;
     const Pin<T> a = load_pin(s0, pin_inst, off, pos, c), b = load_pin(s0 + 1, pin_inst, off, pos, c);
     T gx, gy, gz;
     const T wx = wa_pair(a.px, b.px, c.inv_g, gx);
