@@ -49,6 +49,14 @@ __device__ __forceinline__ long long r_rint(double a) { return __double2ll_rn(a)
 // WA terms are); FP64 mode the full-precision one.
 __device__ __forceinline__ float r_exp(float a) { return __expf(a); }
 __device__ __forceinline__ double r_exp(double a) { return exp(a); }
+// 2^a: the hardware's approximate base-2 exponential in FP32 (the same unit
+// __expf uses, without its scaling multiply), exp2 in FP64.
+__device__ __forceinline__ float r_exp2(float a) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+__device__ __forceinline__ double r_exp2(double a) { return exp2(a); }
 // 1/a for the wirelength's WA sums (a in [1, #pins]): the fast approximate
 // division in FP32 (a few ulp, far inside the FP32 path's tolerance), IEEE
 // division in FP64.

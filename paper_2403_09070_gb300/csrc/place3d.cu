@@ -320,6 +320,8 @@ template <typename T> WlC<T> wl_consts(const place3d_handle *h) {
   c.inv_g = (T)(1.0 / h->gamma);
   c.inv_gz = (T)(1.0 / (h->gamma_z > 0 ? h->gamma_z : h->gamma));
   c.fd_scale = (T)(4.0 / h->dz);
+  c.inv_g2 = (T)(1.4426950408889634 / h->gamma);
+  c.inv_gz2 = (T)(1.4426950408889634 / (h->gamma_z > 0 ? h->gamma_z : h->gamma));
   c.mode2d = h->mode2d ? 1 : 0;
   return c;
 }

@@ -20,6 +20,7 @@ template <typename T> struct WlC {
   T inv_g;     // 1/gamma
   T inv_gz;    // 1/gamma_z
   T fd_scale;  // 4/d_z (eq. fda-grad)
+  T inv_g2, inv_gz2;  // log2(e)/gamma, log2(e)/gamma_z: exp(v/gamma) = 2^(v inv_g2)
   int mode2d;  // multi-die 2D (eq. 2d-place): W = WA(top + HBT) + WA(bottom + HBT), no z terms
 };
 
@@ -189,12 +190,12 @@ __device__ __forceinline__ void pin_exps(const Pin<T> &p, const NetExt<T> &X, co
                                          T (&ex)[6], bool s) {
   const T xmx = s ? X.e[0][1].mx1 : X.e[0][0].mx1, xmn = s ? X.e[0][1].mn1 : X.e[0][0].mn1;
   const T ymx = s ? X.e[1][1].mx1 : X.e[1][0].mx1, ymn = s ? X.e[1][1].mn1 : X.e[1][0].mn1;
-  ex[0] = r_exp((p.px - xmx) * c.inv_g);
-  ex[1] = r_exp((xmn - p.px) * c.inv_g);
-  ex[2] = r_exp((p.py - ymx) * c.inv_g);
-  ex[3] = r_exp((ymn - p.py) * c.inv_g);
-  ex[4] = r_exp((p.pz - X.zmx) * c.inv_gz);
-  ex[5] = r_exp((X.zmn - p.pz) * c.inv_gz);
+  ex[0] = r_exp2((p.px - xmx) * c.inv_g2);
+  ex[1] = r_exp2((xmn - p.px) * c.inv_g2);
+  ex[2] = r_exp2((p.py - ymx) * c.inv_g2);
+  ex[3] = r_exp2((ymn - p.py) * c.inv_g2);
+  ex[4] = r_exp2((p.pz - X.zmx) * c.inv_gz2);
+  ex[5] = r_exp2((X.zmn - p.pz) * c.inv_gz2);
 }
 
 template <typename T>
@@ -273,8 +274,8 @@ __device__ __forceinline__ AxisNet<T> axis_net(int a, const NetExt<T> &X, const 
   for (int s = 0; s < 2; ++s) {
     r.f[s] = r.h[s] = T(0);
     if (has[s]) {
-      r.f[s] = r_exp((X.e[a][s].mx1 - mxA) * c.inv_g);
-      r.h[s] = r_exp((mnA - X.e[a][s].mn1) * c.inv_g);
+      r.f[s] = r_exp2((X.e[a][s].mx1 - mxA) * c.inv_g2);
+      r.h[s] = r_exp2((mnA - X.e[a][s].mn1) * c.inv_g2);
       SP += S.v[a][s][0] * r.f[s];
       NP += S.v[a][s][1] * r.f[s];
       SM += S.v[a][s][2] * r.h[s];
@@ -493,12 +494,12 @@ __device__ __forceinline__ void pin_exps_sh(const Pin<T> &p, const WlShared<T, G
   const int s = side ? 1 : 0;
   const T xmx = sh.f[F_EXT + (0 + s) * 4 + 0][grp], xmn = sh.f[F_EXT + (0 + s) * 4 + 2][grp];
   const T ymx = sh.f[F_EXT + (2 + s) * 4 + 0][grp], ymn = sh.f[F_EXT + (2 + s) * 4 + 2][grp];
-  ex[0] = r_exp((p.px - xmx) * c.inv_g);
-  ex[1] = r_exp((xmn - p.px) * c.inv_g);
-  ex[2] = r_exp((p.py - ymx) * c.inv_g);
-  ex[3] = r_exp((ymn - p.py) * c.inv_g);
-  ex[4] = r_exp((p.pz - sh.f[F_Z + 0][grp]) * c.inv_gz);
-  ex[5] = r_exp((sh.f[F_Z + 1][grp] - p.pz) * c.inv_gz);
+  ex[0] = r_exp2((p.px - xmx) * c.inv_g2);
+  ex[1] = r_exp2((xmn - p.px) * c.inv_g2);
+  ex[2] = r_exp2((p.py - ymx) * c.inv_g2);
+  ex[3] = r_exp2((ymn - p.py) * c.inv_g2);
+  ex[4] = r_exp2((p.pz - sh.f[F_Z + 0][grp]) * c.inv_gz2);
+  ex[5] = r_exp2((sh.f[F_Z + 1][grp] - p.pz) * c.inv_gz2);
 }
 
 // W_e on one axis after the pin (side s, index slot) moves to the other die
