@@ -79,8 +79,9 @@ class NesterovPlacer:
             a_new = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * a * a))
             v_new = self._project(u_new + ((a - 1.0) / a_new) * (u_new - u))
             f_new, g_new = self._grad(v_new)
-            dv = float(torch.linalg.vector_norm(v_new - v))
-            dg = float(torch.linalg.vector_norm(g_new - gv))
+            # Lipschitz step-size estimate in FP64 (the positions and gradients may be FP32)
+            dv = float(torch.linalg.vector_norm((v_new - v).double()))
+            dg = float(torch.linalg.vector_norm((g_new - gv).double()))
             if dg > 0 and dv > 0:
                 step = dv / dg  # inverse Lipschitz estimate
             u, v, gv, a = u_new, v_new, g_new, a_new

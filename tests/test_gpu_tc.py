@@ -99,3 +99,21 @@ def test_fp32_tc_cells_200k_with_fillers():
     q = synth.append_fillers(p, fp, seed=7, positions="uniform")
     assert q["n_inst"] > 4_000_000
     _check_tc(q, q["x"], q["y"], q["z"])
+
+
+def test_fp32_tc_large_skewed_configuration():
+    """4M cells + 200 macros, 4.2M nets plus 200 high-fanout nets of 2k-20k
+    pins (one block per net), 1024x1024x4 bins, FP32_TC with autotuned forms,
+    against the full FP64 oracle (about a minute of CPU time)."""
+    p = synth.make_problem("cells_4m_skewed")
+    assert np.diff(p["net_start"]).max() >= 2000
+    x32, y32, z32 = (np.asarray(p[k], np.float32).astype(np.float64) for k in ("x", "y", "z"))
+    g = run_gpu(p, x32, y32, z32, "fp32_tc", autotune=True)
+    assert any(f[1] == 0 for f in g["forms"])  # the block form ran
+    o, r = run_oracle(p, x32, y32, z32, g["alpha"], density_mode=0)
+    assert np.array_equal(g["q"], o.density_fixed(x32, y32, z32, use_float=True))
+    assert g["res"]["obj"] == pytest.approx(r["obj"], rel=2e-5)
+    assert g["res"]["n_cross"] == r["n_cross"]
+    assert g["res"]["hpwl_d2d"] == pytest.approx(r["hpwl_d2d"], rel=1e-6)
+    for k in ("gx", "gy", "gz"):
+        assert rel_l2(g[k], r[k]) < 1e-4, (k, rel_l2(g[k], r[k]))
