@@ -200,15 +200,21 @@ __device__ __forceinline__ void pin_exps(const Pin<T> &p, const NetExt<T> &X, co
 
 template <typename T>
 __device__ __forceinline__ void sums_add(Sums<T> &S, const Pin<T> &p, const T (&ex)[6], bool top) {
-  const T v[4] = {ex[0], p.px * ex[0], ex[1], p.px * ex[1]};
-  const T w[4] = {ex[2], p.py * ex[2], ex[3], p.py * ex[3]};
-  // predicated adds into side `top` (no dynamic indexing: stays in registers)
+  // masked fused multiply-adds into side `top` (no dynamic indexing, no
+  // selects): the other side's weights are exactly 0
+  const T mt = top ? T(1) : T(0), mb = T(1) - mt;
+  const T xt = mt * p.px, xb = mb * p.px, yt = mt * p.py, yb = mb * p.py;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    S.v[0][1][k] += top ? v[k] : T(0);
-    S.v[0][0][k] += top ? T(0) : v[k];
-    S.v[1][1][k] += top ? w[k] : T(0);
-    S.v[1][0][k] += top ? T(0) : w[k];
+  for (int q = 0; q < 2; ++q) {  // q = 0: the + exponential, 1: the - one
+    const T ea = ex[q], eb = ex[2 + q];
+    S.v[0][1][2 * q] = fma(mt, ea, S.v[0][1][2 * q]);
+    S.v[0][0][2 * q] = fma(mb, ea, S.v[0][0][2 * q]);
+    S.v[0][1][2 * q + 1] = fma(xt, ea, S.v[0][1][2 * q + 1]);
+    S.v[0][0][2 * q + 1] = fma(xb, ea, S.v[0][0][2 * q + 1]);
+    S.v[1][1][2 * q] = fma(mt, eb, S.v[1][1][2 * q]);
+    S.v[1][0][2 * q] = fma(mb, eb, S.v[1][0][2 * q]);
+    S.v[1][1][2 * q + 1] = fma(yt, eb, S.v[1][1][2 * q + 1]);
+    S.v[1][0][2 * q + 1] = fma(yb, eb, S.v[1][0][2 * q + 1]);
   }
   if (!p.hbt) {  // an HBT has no depth
     S.z[0] += ex[4];
