@@ -115,6 +115,11 @@ struct place3d_handle {
   p3d_tc::TcPlan *tc = nullptr;
   // CUDA graph of one evaluation (place3d_eval_graph)
   cudaGraphExec_t gexec = nullptr;
+  // place3d_eval_objective_and_grad's own graph of the evaluation (positions
+  // already packed), keyed by its output buffers and the parameter version
+  cudaGraphExec_t egexec = nullptr;
+  const void *egptr[3] = {nullptr, nullptr, nullptr};
+  unsigned egversion = 0;
   // bumped by every change that a captured graph bakes in (gamma, lambda,
   // alpha, layer weights, reduction forms); graphs recapture when it moved
   unsigned version = 0, gversion = 0;
@@ -622,6 +627,7 @@ void free_all(place3d_handle *h) {
   if (h->side) cudaStreamDestroy(h->side);
   if (h->dens) cudaStreamDestroy(h->dens);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->egexec) cudaGraphExecDestroy(h->egexec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
 }
 
@@ -1061,6 +1067,43 @@ int place3d_set_positions(place3d_handle *h, const void *x, const void *y, const
   return PLACE3D_OK;
 }
 
+// Evaluate (positions already packed) as one CUDA-graph launch on the
+// handle's stream, writing the gradient into tgt (device arrays of the
+// handle's dtype); recaptured when tgt or the parameter version changes.
+static int eval_via_graph(place3d_handle *h, void *const tgt[3]) {
+  const bool same = h->egexec && h->egversion == h->version && h->egptr[0] == tgt[0] && h->egptr[1] == tgt[1] &&
+                    h->egptr[2] == tgt[2];
+  if (!same) {
+    if (h->egexec) {
+      cudaGraphExecDestroy(h->egexec);
+      h->egexec = nullptr;
+    }
+    if (!h->cap_stream) P3D_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    P3D_CUDA(h, cudaStreamSynchronize(h->stream));
+    cudaStream_t keep = h->stream;
+    h->stream = h->cap_stream;
+    P3D_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int hdt = h->precision == PLACE3D_FP64 ? PLACE3D_F64 : PLACE3D_F32;
+    const int rc = h->precision == PLACE3D_FP64 ? eval_impl<double>(h, tgt[0], tgt[1], tgt[2], hdt, PLACE3D_MEM_DEVICE)
+                                                : eval_impl<float>(h, tgt[0], tgt[1], tgt[2], hdt, PLACE3D_MEM_DEVICE);
+    h->stream = keep;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (rc != PLACE3D_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    const cudaError_t ei = cudaGraphInstantiate(&h->egexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return cuda_fail(h, ei, "cudaGraphInstantiate");
+    for (int k = 0; k < 3; ++k) h->egptr[k] = tgt[k];
+    h->egversion = h->version;
+  }
+  P3D_CUDA(h, cudaGraphLaunch(h->egexec, h->stream));
+  return PLACE3D_OK;
+}
+
 int place3d_eval_objective_and_grad(place3d_handle *h, place3d_result *out, void *gx, void *gy, void *gz,
                                     int dtype, int mem) {
   if (!h) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL handle");
@@ -1069,9 +1112,24 @@ int place3d_eval_objective_and_grad(place3d_handle *h, place3d_result *out, void
   if (ng && ((dtype != PLACE3D_F64 && dtype != PLACE3D_F32) || (mem != PLACE3D_MEM_HOST && mem != PLACE3D_MEM_DEVICE)))
     return fail(h, PLACE3D_ERR_INVALID_ARG, "bad dtype or memory kind");
   P3D_CUDA(h, cudaSetDevice(h->device));
-  const int rc = h->precision == PLACE3D_FP64 ? eval_impl<double>(h, gx, gy, gz, dtype, mem)
-                                              : eval_impl<float>(h, gx, gy, gz, dtype, mem);
-  if (rc != PLACE3D_OK) return rc;
+  const int hdt = h->precision == PLACE3D_FP64 ? PLACE3D_F64 : PLACE3D_F32;
+  if (!h->profiling && (!ng || dtype == hdt)) {
+    // one graph launch into the handle's own gradient buffer (a fixed
+    // target: no recapture when the caller's arrays move), then copies
+    const size_t es = h->esz, n = (size_t)h->n;
+    void *tgt[3] = {h->gout, (char *)h->gout + n * es, (char *)h->gout + 2 * n * es};
+    const int rc = eval_via_graph(h, tgt);
+    if (rc != PLACE3D_OK) return rc;
+    if (ng && n > 0) {
+      const cudaMemcpyKind kind = mem == PLACE3D_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+      for (int k = 0; k < 3; ++k)
+        P3D_CUDA(h, cudaMemcpyAsync(k == 0 ? gx : k == 1 ? gy : gz, tgt[k], n * es, kind, h->stream));
+    }
+  } else {
+    const int rc = h->precision == PLACE3D_FP64 ? eval_impl<double>(h, gx, gy, gz, dtype, mem)
+                                                : eval_impl<float>(h, gx, gy, gz, dtype, mem);
+    if (rc != PLACE3D_OK) return rc;
+  }
   h->have_result = true;
   if (out || (ng && mem == PLACE3D_MEM_HOST)) {
     P3D_CUDA(h, cudaMemcpyAsync(h->host_scal, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, h->stream));
