@@ -489,6 +489,30 @@ def main():
     launches = h.launches_per_eval() + 1  # + the position-packing kernel
     value = job_throughput(world, a.steps, total_ms)
 
+    # timed region C: the same evaluation on a handle whose two paths share one
+    # stream (PLACE3D_FLAG_SERIAL), per-stage CUDA events: each stage's kernels
+    # run alone, so a stage's time is its kernels' own launch durations (the
+    # roofline); region B's stage times are the concurrent ones
+    hs = P.Place3D(prob, precision=precision, device=local, stream=stream, flags=P.FLAG_SERIAL)
+    for bi, (_, G, PPL) in enumerate(h_forms):
+        hs.set_wl_form(bi, G, PPL)
+    hs.set_positions(*xyz)
+    for _ in range(max(a.warmup, 1)):
+        hs.eval(*grads, sync=False)
+    torch.cuda.synchronize()
+    hs.stage_times(reset=True)
+    hs.set_profiling(True)
+    torch.cuda.nvtx.range_push("timed_serial")
+    for _ in range(a.steps):
+        flush.zero_()
+        hs.set_positions(*xyz)
+        hs.eval(*grads, sync=False)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    hs.set_profiling(False)
+    st_serial = hs.stage_times(reset=True)
+    hs.close()
+
     # roofline of the dominant stage (per-stage CUDA events on the launching stream)
     alg = algorithmic(prob, precision)
     peaks = {}
@@ -498,17 +522,23 @@ def main():
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
-    evals = max(st["evals"], 1)
-    stages = {}
-    for name, (ms, nl) in st["stages"].items():
-        if nl == 0:
-            continue
-        t_eval = ms / evals
-        b = alg["bytes"].get(name, 0)
-        stages[name] = {"ms_per_eval": t_eval, "launches_per_eval": nl / evals,
-                        "alg_bytes": b, "gbs": b / (t_eval * 1e6) if t_eval > 0 and b else None}
-        if name in alg["flops"]:
-            stages[name]["tflops"] = alg["flops"][name] / (t_eval * 1e9) if t_eval > 0 else None
+
+    def stage_table(stt):
+        evals = max(stt["evals"], 1)
+        out = {}
+        for name, (ms, nl) in stt["stages"].items():
+            if nl == 0:
+                continue
+            t_eval = ms / evals
+            b = alg["bytes"].get(name, 0)
+            out[name] = {"ms_per_eval": t_eval, "launches_per_eval": nl / evals,
+                         "alg_bytes": b, "gbs": b / (t_eval * 1e6) if t_eval > 0 and b else None}
+            if name in alg["flops"]:
+                out[name]["tflops"] = alg["flops"][name] / (t_eval * 1e9) if t_eval > 0 else None
+        return out
+
+    stages_conc = stage_table(st)
+    stages = stage_table(st_serial)
     dom = max(stages, key=lambda k: stages[k]["ms_per_eval"])
     prof_traffic = _profiled_traffic(dom, a.workload, precision)
     if dom in ("transform_fwd", "transform_inv") and precision == "fp32_tc":
@@ -520,6 +550,9 @@ def main():
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                 "frac": ach / hbm_peak if ach else None, "traffic": prof_traffic,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
+    roof["timing"] = ("the stage's kernels timed alone (serial stream, CUDA events over K steps, L2 flushed "
+                      "between steps); "
+                      f"timed concurrently with the other path: {stages_conc.get(dom, {}).get('gbs')} GB/s")
 
     # end to end through the C ABI with pinned host buffers
     hx = [torch.tensor(prob[k], dtype=dt).pin_memory() for k in ("x", "y", "z")]
@@ -560,11 +593,14 @@ def main():
             "gpu_launches": launches * a.steps,
             "roofline": roof,
             "stages": stages,
+            "stages_concurrent": stages_conc,
             "clocks": clocks,
             "objective": res["obj"],
             "timed_path": "separate launches" if a.no_graph else "CUDA graph (pack + evaluation)",
             "separate_launches_evals_per_s": alt_rate,
-            "stages_from": "timed region of separate launches with per-stage CUDA events (same workload, K steps)",
+            "stages_from": ("stages: a PLACE3D_FLAG_SERIAL handle, each stage's kernels alone, per-stage CUDA events "
+                            "over K steps (L2 flushed between steps); stages_concurrent: the separate-launch timed "
+                            "region, both paths concurrent"),
             "wl_forms": h_forms,
         }
         if cpu is not None:

@@ -139,3 +139,22 @@ def test_2d_result_to_device_matches_host_result():
     for k, got in zip(keys, v[:6]):
         assert got == pytest.approx(r[k], rel=1e-12), k
     assert r["energy"] == pytest.approx(sum(r["energy_layer"]), rel=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_2d_one_die_no_hbts(precision):
+    """Every instance on the bottom die: no crossing net, no HBT, the top and
+    HBT layers empty (zero energy), each net one partial net."""
+    p = synth.make_problem("cells_2k")
+    zlo, _ = synth.depth_range(p)
+    q = synth.to_problem2d(p, z=np.full(p["n_inst"], zlo), lam_layer=LAM)
+    assert len(q["hbt_nets"]) == 0 and q["n_inst"] == p["n_inst"]
+    r, g, qmap, (x, y, z) = _run(q, precision)
+    o = Oracle(q)
+    assert np.array_equal(qmap, o.density_fixed(x, y, z, use_float=precision != "fp64"))
+    ref = o.eval2d(x, y, z, density_mode=1 if precision == "fp64" else 0)
+    tol = 1e-9 if precision == "fp64" else 2e-5
+    assert r["obj"] == pytest.approx(ref["obj"], rel=tol)
+    assert r["n_cross"] == 0 and r["energy_layer"][1] == 0 and r["energy_layer"][2] == 0
+    assert r["energy_layer"][0] > 0
+    assert rel_l2(g[0], ref["gx"]) < (1e-9 if precision == "fp64" else 1e-4)
