@@ -344,6 +344,26 @@ int place3d_density_map_noalloc(int n_inst, const double *x, const double *y,
 int place3d_tc_selftest(int M, int N, int K, int batches, const float *A,
                         const float *W, float *out, int *wait_error);
 
+/* Failure-path self-test of the bounded waits (the paper has no counterpart;
+ * a test hook).  Runs one 128x64x64 tensor-core product whose TMA producer
+ * arms and loads nothing, with every mbarrier wait bounded by wait_cycles
+ * SM clocks (about wait_cycles / 2e9 seconds): the MMA thread's first wait
+ * runs out (or the epilogue's, whichever budget expires first), the CTA
+ * records the error code of that wait (1 operands, 2 free stage, 3
+ * accumulator), stops issuing work, frees its tensor memory and exits.
+ * Returns PLACE3D_ERR_TIMEOUT with *wait_error > 0; the CUDA context stays
+ * usable.
+ * UNSUPPORTED off sm_103; INVALID_ARG for wait_cycles <= 0. */
+int place3d_tc_timeout_selftest(long long wait_cycles, int *wait_error);
+
+/* Failure injection on the host (a test hook; the paper has no
+ * counterpart): with nth > 0, the nth device allocation made by a later
+ * place3d_create on the calling thread fails as if the device were out of
+ * memory (nothing is allocated for it).  place3d_create then returns
+ * PLACE3D_ERR_OOM and frees everything it had allocated.  nth <= 0 clears
+ * the hook; it also clears itself once it has fired. */
+void place3d_debug_fail_alloc(int nth);
+
 /* Last error message of the handle, or of the calling thread when h is NULL
  * (creation errors).  Never NULL. */
 const char *place3d_last_error(const place3d_handle *h);

@@ -2,6 +2,7 @@
 // matrices, and the evaluation schedule (density path on the caller's stream,
 // wirelength path on a second stream, joined before the final assembly).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -180,9 +181,11 @@ struct StageScope {
     ev.stage = st;
     ev.s = s;
     cudaEventRecord(ev.a, s);
+    nvtxRangePushA(kStageNames[st]);  // the stage's launches, for profilers (ncu --nvtx-include)
   }
   ~StageScope() {
     if (!h->profiling) return;
+    nvtxRangePop();
     cudaEventRecord(ev.b, s);
     h->ev_live.push_back(ev);
   }
@@ -194,6 +197,18 @@ void count_launch(place3d_handle *h, int stage) {
 }
 
 int grid_for(long long n, int block) { return (int)((n + block - 1) / block); }
+
+// Test hook (place3d_debug_fail_alloc): when positive, the n-th device
+// allocation of a later place3d_create on this thread reports
+// cudaErrorMemoryAllocation without allocating (a fake of the failing call).
+thread_local int g_fail_alloc = 0;
+cudaError_t p3d_malloc(void **p, size_t bytes) {
+  if (g_fail_alloc > 0 && --g_fail_alloc == 0) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
 
 // ---- position packing (and optional range checks) ----
 template <typename TI, typename T>
@@ -678,7 +693,10 @@ int upload_typed(place3d_handle *h, const place3d_problem *p, const std::vector<
   std::copy(Cx.begin(), Cx.end(), all.begin() + h->mat_off[2] + nx2);
   std::copy(Cy.begin(), Cy.end(), all.begin() + h->mat_off[3]);
   std::copy(Sy.begin(), Sy.end(), all.begin() + h->mat_off[4]);
-  P3D_CUDA(h, cudaMalloc(&h->mats, sizeof(T) * all.size()));
+  {
+    const cudaError_t e = p3d_malloc(&h->mats, sizeof(T) * all.size());
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");  // OOM for an allocation failure
+  }
   P3D_CUDA(h, cudaMemcpy(h->mats, all.data(), sizeof(T) * all.size(), cudaMemcpyHostToDevice));
   return PLACE3D_OK;
 }
@@ -686,6 +704,8 @@ int upload_typed(place3d_handle *h, const place3d_problem *p, const std::vector<
 }  // namespace
 
 extern "C" {
+
+void place3d_debug_fail_alloc(int nth) { g_fail_alloc = nth > 0 ? nth : 0; }
 
 double place3d_alpha(double dx, double dz, double beta, double w_hbt, double rh_top, double rh_bot) {
   const double eta = 2.0 * w_hbt / (rh_top + rh_bot);
@@ -888,7 +908,7 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
       {(void **)&h->tstart, sizeof(int) * (size_t)(h->ntiles + 1)},
       {(void **)&h->titems, sizeof(int2) * (size_t)std::max(h->max_items, 1)}, {(void **)&h->tnitems, sizeof(int)}};
   for (auto &a : allocs) {
-    cudaError_t e = cudaMalloc(a.p, a.bytes);
+    cudaError_t e = p3d_malloc(a.p, a.bytes);
     if (e != cudaSuccess) {
       cuda_fail(h, e, "cudaMalloc");
       return bail(e == cudaErrorMemoryAllocation ? PLACE3D_ERR_OOM : PLACE3D_ERR_CUDA);
@@ -902,8 +922,8 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
     for (const Bucket &b : h->buckets)
       rw += (size_t)std::max(grid_for((long long)b.count * 32, bs) * (bs / 32), grid_for(b.count, 256) * 8);
     const size_t rd = (size_t)std::max(grid_for((long long)h->nx * h->ny, 256), 1) * 8;
-    if (cudaMalloc(&h->part_w, sizeof(double) * 4 * rw) != cudaSuccess ||
-        cudaMalloc(&h->part_d, sizeof(double) * 3 * rd) != cudaSuccess) {
+    if (p3d_malloc((void **)&h->part_w, sizeof(double) * 4 * rw) != cudaSuccess ||
+        p3d_malloc((void **)&h->part_d, sizeof(double) * 3 * rd) != cudaSuccess) {
       fail(h, PLACE3D_ERR_OOM, "cudaMalloc (partial-sum rows)");
       return bail(PLACE3D_ERR_OOM);
     }

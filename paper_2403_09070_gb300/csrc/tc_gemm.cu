@@ -59,6 +59,8 @@ struct Group {
   int count;
   int tile_start[4];
   int *err;
+  long long wait_cycles;  // clock budget of every mbarrier wait (kWaitCycles)
+  int skip_loads;         // test hook: the producer arms and loads nothing, so the MMA's first wait runs out
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -154,11 +156,11 @@ constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN 
                             ((uint32_t)(BM >> 4) << 24);
 
 __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                             int *err, int code) {
+                                             int *err, int code, long long budget) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > budget) {
       *abort_flag = 1;
       atomicExch(err, code);
       return false;
@@ -207,9 +209,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Grou
       // ---- TMA producer ----
       const CUtensorMap *am = &g.amap[pi], *wm = &g.wmap[pi];
       int issued = 0;
-      for (int kb = 0; kb < nk; ++kb) {
+      for (int kb = 0; kb < (g.skip_loads ? 0 : nk); ++kb) {
         const int s = kb % STAGES, round = kb / STAGES;
-        if (kb >= STAGES && !wait_bounded(empty0 + 8 * s, (round - 1) & 1, abort_p, g.err, ERR_EMPTY)) break;
+        if (kb >= STAGES && !wait_bounded(empty0 + 8 * s, (round - 1) & 1, abort_p, g.err, ERR_EMPTY, g.wait_cycles))
+          break;
         const uint32_t st = smem_u32(smem + s * STAGE_BYTES), fb = full0 + 8 * s;
         mbar_expect_tx(fb, STAGE_BYTES);
         tma_load_4d(am, st, fb, kb * BK, m0, b, 0);
@@ -222,7 +225,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Grou
       for (int s = 0; s < STAGES && s < issued; ++s) {
         const int last = s + ((issued - 1 - s) / STAGES) * STAGES;
         const long long t0 = clock64();
-        while (!mbar_try_wait(full0 + 8 * s, (last / STAGES) & 1) && clock64() - t0 < kWaitCycles) {
+        while (!mbar_try_wait(full0 + 8 * s, (last / STAGES) & 1) && clock64() - t0 < g.wait_cycles) {
         }
       }
     }
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Grou
       // ---- MMA issuer ----
       for (int kb = 0; kb < nk; ++kb) {
         const int s = kb % STAGES, round = kb / STAGES;
-        if (!wait_bounded(full0 + 8 * s, round & 1, abort_p, g.err, ERR_FULL)) break;
+        if (!wait_bounded(full0 + 8 * s, round & 1, abort_p, g.err, ERR_FULL, g.wait_cycles)) break;
         tc_fence_after();
         const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES), a_lo = a_hi + A_BYTES;
         const uint32_t w_hi = a_hi + 2 * A_BYTES, w_lo = w_hi + W_BYTES;
@@ -249,7 +252,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Grou
     }
   } else {
     // ---- epilogue: TMEM -> registers -> global, transposed ----
-    const bool ok = wait_bounded(accf, 0, abort_p, g.err, ERR_ACC);
+    const bool ok = wait_bounded(accf, 0, abort_p, g.err, ERR_ACC, g.wait_cycles);
     tc_fence_after();
     const int q = warp & 3;  // this warp's TMEM lane quarter
     const int m = m0 + q * 32 + lane;
@@ -359,6 +362,8 @@ struct ProbSpec {
 static bool make_group(Group *g, std::initializer_list<ProbSpec> specs, int *err, std::string *why) {
   std::memset(g, 0, sizeof(Group));
   g->err = err;
+  g->wait_cycles = kWaitCycles;
+  g->skip_loads = 0;
   int tiles = 0;
   for (const ProbSpec &s : specs) {
     if (s.M % BM || s.N % BN || s.K % BK) {
@@ -603,6 +608,51 @@ extern "C" int place3d_tc_selftest(int M, int N, int K, int batches, const float
     launch(g, 0);
     if (cudaDeviceSynchronize() == cudaSuccess &&
         cudaMemcpy(out, dout, no * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      int e = 0;
+      cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost);
+      if (wait_error) *wait_error = e;
+      rc = e ? PLACE3D_ERR_TIMEOUT : PLACE3D_OK;
+    }
+  }
+  if (da) cudaFree(da);
+  if (dw) cudaFree(dw);
+  if (dout) cudaFree(dout);
+  if (err) cudaFree(err);
+  return rc;
+}
+
+// Failure-path self-test: a 128x64x64 product whose producer arms and loads
+// nothing, with every wait bounded by wait_cycles.  A wait runs out, the CTA
+// records its code, stops, frees its tensor memory and exits; the call
+// returns PLACE3D_ERR_TIMEOUT with *wait_error > 0 and the context stays
+// usable.
+extern "C" int place3d_tc_timeout_selftest(long long wait_cycles, int *wait_error) {
+  using namespace p3d_tc;
+  if (wait_cycles <= 0) return PLACE3D_ERR_INVALID_ARG;
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess ||
+      prop.major != 10 || prop.minor != 3)
+    return PLACE3D_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess)
+    return PLACE3D_ERR_CUDA;
+  const int M = BM, N = BN, K = BK;
+  std::vector<double> av((size_t)M * K, 0.0), wv((size_t)N * K, 0.0);
+  std::string why;
+  __nv_bfloat16 *da = nullptr, *dw = nullptr;
+  float *dout = nullptr;
+  int *err = nullptr;
+  int rc = PLACE3D_ERR_CUDA;
+  Group g;
+  if (upload_split(&da, av, &why) && upload_split(&dw, wv, &why) && dev_alloc(&dout, (size_t)N * M, &why) &&
+      dev_alloc(&err, 1, &why) && cudaMemset(err, 0, sizeof(int)) == cudaSuccess &&
+      make_group(&g, {{da, (long long)M * K, (long long)M * K, dw, (long long)N * K, dout, (long long)N * M, 0,
+                       OUT_F32, 1, M, N, K}},
+                 err, &why)) {
+    g.wait_cycles = wait_cycles;
+    g.skip_loads = 1;
+    launch(g, 0);
+    if (cudaDeviceSynchronize() == cudaSuccess) {
       int e = 0;
       cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost);
       if (wait_error) *wait_error = e;

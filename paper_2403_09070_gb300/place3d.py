@@ -67,7 +67,8 @@ EXPORTS = ("place3d_create", "place3d_geometry", "place3d_alpha", "place3d_set_p
            "place3d_stage_times", "place3d_launches_per_eval", "place3d_last_error", "place3d_destroy",
            "place3d_density_map_noalloc", "place3d_tc_selftest", "place3d_autotune", "place3d_wl_forms",
            "place3d_set_wl_form", "place3d_result_to_device", "place3d_set_params", "place3d_eval_graph",
-           "place3d_batch_create", "place3d_batch_eval", "place3d_batch_destroy", "place3d_set_layer_weights")
+           "place3d_batch_create", "place3d_batch_eval", "place3d_batch_destroy", "place3d_set_layer_weights",
+           "place3d_tc_timeout_selftest", "place3d_debug_fail_alloc")
 NOALLOC_MAX_BINS = 262144
 
 _lib = None
@@ -120,6 +121,9 @@ def load_library(build_if_missing: bool = True):
     L.place3d_set_layer_weights.argtypes = [vp, vp]
     L.place3d_wl_forms.argtypes = [vp, vp, vp, vp, i32]
     L.place3d_tc_selftest.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp]
+    L.place3d_tc_timeout_selftest.argtypes = [C.c_longlong, vp]
+    L.place3d_debug_fail_alloc.argtypes = [i32]
+    L.place3d_debug_fail_alloc.restype = None
     L.place3d_density_map_noalloc.argtypes = [i32] + [vp] * 8 + [d] * 4 + [i32] * 3 + [vp, vp]
     _lib = L
     return L
@@ -347,6 +351,21 @@ def density_map_noalloc(x, y, z, w_bot, h_bot, w_top, h_top, is_macro, region, g
                                        xl, yl, xh, yh, nx, ny, nz, rho.data_ptr(), C.c_void_p(stream or 0))
     if rc != 0:
         raise Place3DError(rc, "place3d_density_map_noalloc failed")
+
+
+def debug_fail_alloc(nth: int):
+    """Make the nth device allocation of the next create on this thread fail
+    as out of memory (nth <= 0 clears it)."""
+    load_library().place3d_debug_fail_alloc(int(nth))
+
+
+def tc_timeout_selftest(wait_cycles: int = 200_000_000):
+    """Run the tensor-core kernel with a producer that loads nothing and every
+    wait bounded by wait_cycles SM clocks; returns (status, wait error code)."""
+    L = load_library()
+    e = C.c_int(0)
+    rc = L.place3d_tc_timeout_selftest(int(wait_cycles), C.byref(e))
+    return rc, e.value
 
 
 def tc_selftest(A, W):

@@ -117,3 +117,18 @@ def test_fp32_tc_large_skewed_configuration():
     assert g["res"]["hpwl_d2d"] == pytest.approx(r["hpwl_d2d"], rel=1e-6)
     for k in ("gx", "gy", "gz"):
         assert rel_l2(g[k], r[k]) < 1e-4, (k, rel_l2(g[k], r[k]))
+
+
+def test_tc_bounded_wait_reports_timeout_and_context_survives():
+    """Failure detection without a fault: the producer arms nothing, the
+    bounded mbarrier wait runs out (about 0.1 s), the kernel returns an error
+    status the host reads, and the context still computes correctly."""
+    rc, code = P.tc_timeout_selftest(200_000_000)
+    assert rc == -6 and code in (1, 2, 3), (rc, code)
+    rng = np.random.default_rng(1)
+    A = rng.normal(size=(1, 128, 64)).astype(np.float32)
+    W = np.cos(np.pi * np.outer(np.arange(64), np.arange(64) + 0.5) / 64).astype(np.float32)
+    out, err = P.tc_selftest(A, W)
+    assert err == 0
+    ref = np.einsum("bmk,nk->bnm", A.astype(np.float64), W.astype(np.float64))
+    assert np.abs(out - ref).max() / np.abs(ref).max() < 2e-5
