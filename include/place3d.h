@@ -150,6 +150,10 @@ typedef struct place3d_result {
    * obj = wl_bi + sum_l lam_layer[l] energy_layer[l], energy = their sum,
    * hpwl_d2d = exact D2D HPWL with the HBTs (eq. exact-wirelength).  3D: 0. */
   double energy_layer[3];
+  /* Density overflow (the paper's OVFL, target density 1): sum over bins of
+   * max(rho_b - 1, 0) divided by the sum of rho_b (all instances, fillers
+   * included, in the fixed-point density of eq. density-map-accum). */
+  double overflow;
 } place3d_result;
 
 typedef struct place3d_handle place3d_handle;

@@ -212,6 +212,8 @@ enum Scalar {
   S_EL0,  // 2D mode: per-layer energy sums (bottom, top, HBT layer)
   S_EL1,
   S_EL2,
+  S_OVFL,  // sum over bins of max(rho - 1, 0) (density overflow, target density 1)
+  S_RHO,   // sum over bins of rho
   S_COUNT
 };
 

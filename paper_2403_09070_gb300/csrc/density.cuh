@@ -231,17 +231,26 @@ __global__ void __launch_bounds__(1024) k_scan_cols(int nx, int ny, TA *a) {
 // ---- density -> transform input: z prefix of the macro map + cell map ----
 // rho[z][y][x] = (q[z][y][x] + sum_{z' <= z} A[z'][y][x]) * 2^-36.
 // A may be NULL (no macros).  One thread per (y, x) column.
+// part != NULL: also the per-warp rows (sum of max(rho - 1, 0), sum of rho)
+// of the density overflow (target density 1).
 template <typename T, typename Out>
 __global__ void __launch_bounds__(256) k_densify(int nxy, int nz, const long long *__restrict__ q,
-                                                 const long long *__restrict__ A, Out rho) {
+                                                 const long long *__restrict__ A, Out rho,
+                                                 double *__restrict__ part = nullptr) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nxy) return;
-  long long acc = 0;
-  for (int z = 0; z < nz; ++z) {
-    const size_t id = (size_t)z * nxy + t;
-    if (A) acc += A[id];
-    rho.put(id, (T)(q[id] + acc) * (T)(1.0 / kFixedScale));
+  T v[2] = {0, 0};
+  if (t < nxy) {
+    long long acc = 0;
+    for (int z = 0; z < nz; ++z) {
+      const size_t id = (size_t)z * nxy + t;
+      if (A) acc += A[id];
+      const T r = (T)(q[id] + acc) * (T)(1.0 / kFixedScale);
+      rho.put(id, r);
+      v[0] += r > T(1) ? r - T(1) : T(0);
+      v[1] += r;
+    }
   }
+  if (part) warp_sum_part<2>(v, part);
 }
 
 // ---- a10 (macros): Theorem 1's adjoint, one thread per (macro, corner) ----

@@ -510,11 +510,15 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
       count_launch(h, ST_PREFIX);
     }
     if (h->tc) {
-      p3d_tc::densify(h->tc, s, h->nx * h->ny, h->nz, h->q, h->nm > 0 ? h->corner : nullptr);
+      p3d_tc::densify(h->tc, s, h->nx * h->ny, h->nz, h->q, h->nm > 0 ? h->corner : nullptr, h->part_d);
     } else {
       k_densify<T><<<grid_for((long long)h->nx * h->ny, 256), 256, 0, s>>>(
-          h->nx * h->ny, h->nz, h->q, h->nm > 0 ? h->corner : nullptr, OutPlain<T>{as<T>(h->rho)});
+          h->nx * h->ny, h->nz, h->q, h->nm > 0 ? h->corner : nullptr, OutPlain<T>{as<T>(h->rho)}, h->part_d);
     }
+    count_launch(h, ST_PREFIX);
+    // density overflow (sum of max(rho - 1, 0) and of rho) from densify's per-warp rows
+    const int orow = grid_for((long long)h->nx * h->ny, 256) * 8;
+    k_sum_parts<2><<<sum_grid(orow), 256, 0, s>>>(h->part_d, orow, h->scal + S_OVFL);
     count_launch(h, ST_PREFIX);
   }
   if (h->tc)
@@ -610,6 +614,7 @@ void fill_result(const place3d_handle *h, place3d_result *r) {
   r->s_z = s[S_SZ];
   r->g_scale = s[S_SZ] > 0 ? (s[S_SX] + s[S_SY]) / (2.0 * s[S_SZ]) : 0.0;
   r->obj = r->wl_bi + h->alpha * r->wl_z + h->lambda * r->energy;
+  r->overflow = s[S_RHO] > 0 ? s[S_OVFL] / s[S_RHO] : 0.0;
   for (int l = 0; l < 3; ++l) r->energy_layer[l] = 0.0;
   if (h->mode2d) {
     // eq. 2d-place: U_l = 1/2 A_b N_x N_y sum c_j c_k a^2 / w^2 per layer

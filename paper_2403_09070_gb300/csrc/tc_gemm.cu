@@ -534,8 +534,8 @@ TcPlan *create(int device, int nx, int ny, int nz, double dx, double dy, double 
   return p;
 }
 
-void densify(TcPlan *p, cudaStream_t s, int nxy, int nz, const long long *q, const long long *corner) {
-  k_densify<float><<<(nxy + 255) / 256, 256, 0, s>>>(nxy, nz, q, corner, OutSplit{p->rho, (long long)p->nb});
+void densify(TcPlan *p, cudaStream_t s, int nxy, int nz, const long long *q, const long long *corner, double *part) {
+  k_densify<float><<<(nxy + 255) / 256, 256, 0, s>>>(nxy, nz, q, corner, OutSplit{p->rho, (long long)p->nb}, part);
 }
 
 int forward(TcPlan *p, cudaStream_t s) {

@@ -21,7 +21,8 @@ struct TcPlan;
 TcPlan *create(int device, int nx, int ny, int nz, double dx, double dy, double dz, void *e4,
                const p3d::ZStageC *zc, std::string *why);
 // rho (cells + macro corners, z prefix) -> split-BF16 planes of the input.
-void densify(TcPlan *p, cudaStream_t s, int nxy, int nz, const long long *q, const long long *corner);
+// (part: the per-warp overflow rows, see k_densify)
+void densify(TcPlan *p, cudaStream_t s, int nxy, int nz, const long long *q, const long long *corner, double *part);
 // Forward x and y products; z stage (scaling, energy, z transforms);
 // inverse x and y products into the interleaved field map e4.  Each returns its launch count.
 int forward(TcPlan *p, cudaStream_t s);

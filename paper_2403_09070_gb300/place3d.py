@@ -53,10 +53,11 @@ class _Problem(C.Structure):
 
 class Result(C.Structure):
     _fields_ = [(k, C.c_double) for k in ("obj", "wl_bi", "wl_z", "energy", "hpwl_d2d", "n_cross",
-                                           "g_scale", "s_x", "s_y", "s_z")] + [("energy_layer", C.c_double * 3)]
+                                           "g_scale", "s_x", "s_y", "s_z")] + [("energy_layer", C.c_double * 3),
+                                                                                ("overflow", C.c_double)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_[:-1]}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "energy_layer"}
         d["energy_layer"] = list(self.energy_layer)
         return d
 

@@ -259,3 +259,21 @@ def test_fillers_cells_2k_fp32(positions):
     q = _with_fillers("cells_2k", (0.8, 0.7), positions)
     g, r = _check_fp32(q, q["x"], q["y"], q["z"])
     assert np.all(g["gz"][q["z_fixed"].astype(bool)] == 0.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_tc"])
+@pytest.mark.parametrize("positions", ["center", "uniform"])
+def test_density_overflow(precision, positions):
+    """The overflow by-product (sum of max(rho - 1, 0) over the sum of rho,
+    target density 1) against its definition on the oracle's fixed-point map."""
+    wl = "cells_200k" if precision == "fp32_tc" else "cells_2k"
+    p = synth.make_problem(wl, positions=positions)
+    dt = np.float64 if precision == "fp64" else np.float32
+    x, y, z = (np.asarray(p[k], dt).astype(np.float64) for k in ("x", "y", "z"))
+    g = run_gpu(p, x, y, z, precision, maps=False)
+    from oracle import Oracle
+    rho = Oracle(p).density_fixed(x, y, z, use_float=precision != "fp64") * Q
+    expect = np.maximum(rho - 1.0, 0.0).sum() / rho.sum()
+    assert g["res"]["overflow"] == pytest.approx(expect, rel=1e-10 if precision == "fp64" else 1e-5, abs=1e-12)
+    if positions == "center":
+        assert g["res"]["overflow"] > 0.05  # the clustered start overflows
