@@ -1092,17 +1092,34 @@ int place3d_set_positions(place3d_handle *h, const void *x, const void *y, const
   return PLACE3D_OK;
 }
 
+// Make *exec run `graph` (consumed).  An existing executable graph is
+// updated in place when the new capture has the same shape (a parameter or
+// buffer change only alters kernel arguments), which costs far less than a
+// fresh instantiation; otherwise it is replaced.
+static cudaError_t install_graph(cudaGraphExec_t *exec, cudaGraph_t graph) {
+  if (*exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(*exec, graph, &info) == cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return cudaSuccess;
+    }
+    (void)cudaGetLastError();
+    cudaGraphExecDestroy(*exec);
+    *exec = nullptr;
+  }
+  const cudaError_t e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  return e;
+}
+
 // Evaluate (positions already packed) as one CUDA-graph launch on the
 // handle's stream, writing the gradient into tgt (device arrays of the
-// handle's dtype); recaptured when tgt or the parameter version changes.
+// handle's dtype); recaptured (and the executable graph updated in place)
+// when tgt or the parameter version changes.
 static int eval_via_graph(place3d_handle *h, void *const tgt[3]) {
   const bool same = h->egexec && h->egversion == h->version && h->egptr[0] == tgt[0] && h->egptr[1] == tgt[1] &&
                     h->egptr[2] == tgt[2];
   if (!same) {
-    if (h->egexec) {
-      cudaGraphExecDestroy(h->egexec);
-      h->egexec = nullptr;
-    }
     if (!h->cap_stream) P3D_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     P3D_CUDA(h, cudaStreamSynchronize(h->stream));
     cudaStream_t keep = h->stream;
@@ -1119,8 +1136,7 @@ static int eval_via_graph(place3d_handle *h, void *const tgt[3]) {
       return rc;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
-    const cudaError_t ei = cudaGraphInstantiate(&h->egexec, graph, 0);
-    cudaGraphDestroy(graph);
+    const cudaError_t ei = install_graph(&h->egexec, graph);
     if (ei != cudaSuccess) return cuda_fail(h, ei, "cudaGraphInstantiate");
     for (int k = 0; k < 3; ++k) h->egptr[k] = tgt[k];
     h->egversion = h->version;
@@ -1418,10 +1434,6 @@ int place3d_eval_graph(place3d_handle *h, const void *x, const void *y, const vo
   bool same = h->gexec && h->gdtype == dtype && h->gversion == h->version;
   for (int k = 0; k < 6 && same; ++k) same = h->gptr[k] == ptr[k];
   if (!same) {
-    if (h->gexec) {
-      cudaGraphExecDestroy(h->gexec);
-      h->gexec = nullptr;
-    }
     if (!h->cap_stream) P3D_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     P3D_CUDA(h, cudaStreamSynchronize(h->stream));
     P3D_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -1433,8 +1445,7 @@ int place3d_eval_graph(place3d_handle *h, const void *x, const void *y, const vo
       return rc;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
-    const cudaError_t ei = cudaGraphInstantiate(&h->gexec, graph, 0);
-    cudaGraphDestroy(graph);
+    const cudaError_t ei = install_graph(&h->gexec, graph);
     if (ei != cudaSuccess) return cuda_fail(h, ei, "cudaGraphInstantiate");
     for (int k = 0; k < 6; ++k) h->gptr[k] = ptr[k];
     h->gdtype = dtype;
@@ -1553,10 +1564,6 @@ int place3d_batch_eval(place3d_batch *b, const void *const *xs, const void *cons
   std::vector<unsigned> vers;
   for (auto *h : b->hs) vers.push_back(h->version);
   if (!b->exec || b->dtype != dtype || b->ptrs != ptr || b->versions != vers) {
-    if (b->exec) {
-      cudaGraphExecDestroy(b->exec);
-      b->exec = nullptr;
-    }
     for (auto *h : b->hs)
       if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PLACE3D_ERR_CUDA;
     if (cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PLACE3D_ERR_CUDA;
@@ -1577,9 +1584,7 @@ int place3d_batch_eval(place3d_batch *b, const void *const *xs, const void *cons
       if (graph) cudaGraphDestroy(graph);
       return rc != PLACE3D_OK ? rc : PLACE3D_ERR_CUDA;
     }
-    const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ei != cudaSuccess) return PLACE3D_ERR_CUDA;
+    if (install_graph(&b->exec, graph) != cudaSuccess) return PLACE3D_ERR_CUDA;
     b->ptrs = ptr;
     b->versions = vers;
     b->dtype = dtype;

@@ -1,8 +1,8 @@
 """GPU parity of the multi-die 2D mode (eq. 2d-place) through the C ABI
 against the oracle: bit-exact fixed-point layer maps, FP64 within 1e-9, FP32
 and FP32_TC within 2e-5 (objective) and 1e-4 (gradient L2); HBT pins in
-both partial nets, per-layer weights, high-fanout nets, and CUDA-graph
-recapture after a parameter change."""
+both partial nets, per-layer weights, high-fanout nets, and CUDA graphs
+that see a parameter change made after their capture."""
 import numpy as np
 import pytest
 
@@ -84,9 +84,10 @@ def test_2d_cells_200k_tensor_cores():
     _check(_problem2d("cells_200k", seed=5), "fp32_tc")
 
 
-def test_2d_layer_weights_and_graph_recapture():
+def test_2d_layer_weights_seen_by_captured_graph():
     """set_layer_weights changes the objective by the weighted layer
-    energies, and a captured graph picks the new weights up."""
+    energies, and a graph captured before the change picks the new weights
+    up (it is re-captured and updated in place at its next launch)."""
     from paper_2403_09070_gb300 import place3d as P
     q = _problem2d()
     n = q["n_inst"]
@@ -103,10 +104,10 @@ def test_2d_layer_weights_and_graph_recapture():
                                           rel=1e-12)
 
 
-def test_graph_recaptures_after_set_params():
+def test_graph_sees_set_params():
     """3D mode: a graph captured before place3d_set_params evaluates with the
-    new gamma and lambda afterwards (the parameters are baked into the
-    captured launches)."""
+    new gamma and lambda afterwards (the parameters are kernel arguments: the
+    graph is re-captured and updated in place at its next launch)."""
     from paper_2403_09070_gb300 import place3d as P
     p = synth.make_problem("cells_2k")
     n = p["n_inst"]

@@ -64,3 +64,40 @@ def test_batch_of_uneven_instances_in_one_graph():
     b.close()
     for h in hs:
         h.close()
+
+
+def test_batch_sees_set_params_of_one_instance():
+    """A batch graph captured before place3d_set_params on one of its handles
+    evaluates that instance with the new gamma and lambda, the others
+    unchanged."""
+    probs = synth.make_batch(count=3, seed=11, n_min=3000, n_max=8000)
+    hs = [P.Place3D(p, precision="fp32") for p in probs]
+    xyz = [[torch.tensor(p[k], device="cuda", dtype=torch.float32) for k in ("x", "y", "z")] for p in probs]
+    gs = [[torch.empty(p["n_inst"], device="cuda", dtype=torch.float32) for _ in range(3)] for p in probs]
+    b = P.Batch(hs)
+    args = [[v[k] for v in xyz] for k in range(3)] + [[v[k] for v in gs] for k in range(3)]
+    b.eval(*args)
+    torch.cuda.synchronize()
+    before = [h.get_result()["obj"] for h in hs]
+    p1 = probs[1]
+    hs[1].set_params(gamma=1.5 * p1["gamma"], gamma_z=0.0, alpha=hs[1].alpha, lam=3 * p1["lam"])
+    b.eval(*args)
+    torch.cuda.synchronize()
+    for i, (p, h, v, g) in enumerate(zip(probs, hs, xyz, gs)):
+        r = h.get_result()
+        with P.Place3D(p, precision="fp32") as hr:
+            if i == 1:
+                hr.set_params(gamma=1.5 * p["gamma"], gamma_z=0.0, alpha=hr.alpha, lam=3 * p["lam"])
+            hr.set_positions(*(t.cpu().numpy() for t in v))
+            gref = [np.zeros(p["n_inst"], np.float32) for _ in range(3)]
+            ref = hr.eval(*gref)
+        assert r["obj"] == pytest.approx(ref["obj"], rel=1e-5)
+        if i != 1:
+            assert r["obj"] == pytest.approx(before[i], rel=1e-6)
+        else:
+            assert abs(r["obj"] - before[i]) > 1e-3 * abs(before[i])
+        for a, c in zip(g, gref):
+            np.testing.assert_allclose(a.cpu().numpy(), c, rtol=1e-4, atol=1e-4 * np.abs(c).max())
+    b.close()
+    for h in hs:
+        h.close()
