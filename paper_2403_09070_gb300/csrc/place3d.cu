@@ -322,11 +322,15 @@ int launch_wl(place3d_handle *h, const Bucket &b, int G, int PPL, cudaStream_t w
   }
   constexpr int BS = wl_block<T>();
   const int blocks = grid_for((long long)b.count * G, BS);
-#define P3D_WL(GG, PP)                                                                                    \
-  if (G == GG && PPL == PP) {                                                                             \
-    k_wl_group<T, GG, PP><<<blocks, BS, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, pos, c, \
-                                                acc, part);                                               \
-    return blocks * (BS / 32);                                                                            \
+#define P3D_WL(GG, PP)                                                                                  \
+  if (G == GG && PPL == PP) {                                                                           \
+    if (h->mode2d)                                                                                      \
+      k_wl_group<T, GG, PP, true><<<blocks, BS, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, \
+                                                        pos, c, acc, part);                             \
+    else                                                                                                \
+      k_wl_group<T, GG, PP, false><<<blocks, BS, 0, w>>>(b.first, b.count, h->net_start, h->pin_inst, off, \
+                                                         pos, c, acc, part);                            \
+    return blocks * (BS / 32);                                                                          \
   }
   P3D_WL(1, 2) P3D_WL(1, 4) P3D_WL(2, 2) P3D_WL(4, 1) P3D_WL(2, 4) P3D_WL(8, 1) P3D_WL(4, 4)
   P3D_WL(16, 1) P3D_WL(8, 4) P3D_WL(32, 1) P3D_WL(16, 4) P3D_WL(32, 2) P3D_WL(32, 4)
@@ -488,7 +492,7 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
                                                                     as<CellRec<T>>(h->trec), dc, h->tcfg, h->q);
       for (int k = 0; k < 4; ++k) count_launch(h, ST_SCATTER);
     } else if (n > 0) {
-      k_scatter_cells<T><<<grid_for(n, 256), 256, 0, s>>>(n, as<V4<T>>(h->pos), as<V4<T>>(h->size), h->flags_d,
+      k_scatter_cells<T><<<grid_for(2 * (long long)n, 256), 256, 0, s>>>(n, as<V4<T>>(h->pos), as<V4<T>>(h->size), h->flags_d,
                                                           dc, h->q);
       count_launch(h, ST_SCATTER);
     }

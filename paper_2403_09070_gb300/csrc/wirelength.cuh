@@ -32,13 +32,15 @@ template <typename T> struct Pin {
   T qx, qy;      // the same pin if its instance were on the other die
 };
 
-template <typename T>
+// HBTS: the netlist may hold HBT pins, stored as ~instance (2D mode only);
+// false compiles the 3D kernels without the HBT cases.
+template <typename T, bool HBTS = true>
 __device__ __forceinline__ Pin<T> load_pin(int p, const int *__restrict__ pin_inst,
                                            const V4<T> *__restrict__ off,
                                            const V4<T> *__restrict__ pos, const WlC<T> &c) {
   Pin<T> q;
-  const int raw = __ldg(pin_inst + p);  // HBT pins are stored as ~instance (2D mode)
-  q.hbt = raw < 0;
+  const int raw = __ldg(pin_inst + p);
+  q.hbt = HBTS && raw < 0;
   q.inst = q.hbt ? ~raw : raw;
   const V4<T> o = off[p];  // (bot x, bot y, top x, top y)
   const V4<T> s = pos[q.inst];
@@ -428,7 +430,8 @@ __global__ void __launch_bounds__(256) k_wl_pair(int pin0, int nnets,
   T vals[4] = {0, 0, 0, 0};
   if (t < nnets) {
     const int s0 = pin0 + 2 * t;
-    const Pin<T> a = load_pin(s0, pin_inst, off, pos, c), b = load_pin(s0 + 1, pin_inst, off, pos, c);
+    const Pin<T> a = load_pin<T, false>(s0, pin_inst, off, pos, c);
+    const Pin<T> b = load_pin<T, false>(s0 + 1, pin_inst, off, pos, c);
     T gx, gy, gz;
     const T wx = wa_pair(a.px, b.px, c.inv_g, gx);
     const T wy = wa_pair(a.py, b.py, c.inv_g, gy);
@@ -529,12 +532,16 @@ __device__ __forceinline__ T moved_sh(const WlShared<T, GR> &sh, int grp, int a,
   return hall > ps + po ? hall : ps + po;
 }
 
-template <typename T, int G, int PPL>
+// M2D: multi-die 2D mode (compile-time, so the 3D kernels carry none of the
+// HBT and partial-net-only cases).
+template <typename T, int G, int PPL, bool M2D>
 __global__ void __launch_bounds__(wl_block<T>()) k_wl_group(int net0, int nnets, const int *__restrict__ net_start,
                                                             const int *__restrict__ pin_inst,
                                                             const V4<T> *__restrict__ off,
-                                                            const V4<T> *__restrict__ pos, WlC<T> c,
+                                                            const V4<T> *__restrict__ pos, WlC<T> c0,
                                                             V4<T> *__restrict__ acc, double *__restrict__ part) {
+  WlC<T> c = c0;
+  c.mode2d = M2D ? 1 : 0;
   constexpr int GR = wl_block<T>() / G;  // groups (nets) per block
   __shared__ WlShared<T, GR> sh;
   const int lane = threadIdx.x & (G - 1);
@@ -556,7 +563,7 @@ __global__ void __launch_bounds__(wl_block<T>()) k_wl_group(int net0, int nnets,
       const int k = lane + r * G;
       has[r] = k < d;
       if (has[r]) {
-        pin[r] = load_pin(s0 + k, pin_inst, off, pos, c);
+        pin[r] = load_pin<T, M2D>(s0 + k, pin_inst, off, pos, c);
         X.add(pin[r], k);
       }
     }
@@ -573,7 +580,7 @@ __global__ void __launch_bounds__(wl_block<T>()) k_wl_group(int net0, int nnets,
       if (has[r]) {
         T ex[6];
         const Pin<T> &q = pin[r];
-        if (q.hbt) {  // 2D mode: a member of both partial nets
+        if (M2D && q.hbt) {  // 2D mode: a member of both partial nets
           pin_exps_sh(q, sh, grp, c, ex, false);
           sums_add(S, q, ex, false);
           pin_exps_sh(q, sh, grp, c, ex, true);
@@ -622,13 +629,13 @@ __global__ void __launch_bounds__(wl_block<T>()) k_wl_group(int net0, int nnets,
       sh.f[F_ZC + 3][grp] = N.zm;
       sh.f[F_WCUR][grp] = N.wcur;
       vals[0] = N.ax[0].what + N.ax[1].what;
-      vals[1] = c.mode2d ? T(0) : N.pz;
+      vals[1] = M2D ? T(0) : N.pz;
       vals[2] = N.wcur;
       vals[3] = (X.ntop > 0 && X.ntop < X.n) ? T(1) : T(0);
     }
   }
   __syncwarp();
-  if (d >= 2 && c.mode2d) {
+  if (M2D && d >= 2) {
     // 2D mode: split-branch coefficients of each partial net, no FD, no z
 #pragma unroll
     for (int r = 0; r < PPL; ++r)
@@ -651,7 +658,7 @@ __global__ void __launch_bounds__(wl_block<T>()) k_wl_group(int net0, int nnets,
         }
         acc_add(acc + p.inst, g[0], g[1], T(0), T(0));
       }
-  } else if (d >= 2) {
+  } else if (!M2D && d >= 2) {
     const int ntop = sh.i[I_NTOP][grp], n = sh.i[I_N][grp];
     const T wcur = sh.f[F_WCUR][grp];
 #pragma unroll
