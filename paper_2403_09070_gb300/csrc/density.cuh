@@ -184,7 +184,10 @@ __global__ void k_macro_corners(int nm, const int *__restrict__ macro_ids,
 // ---- eq. def-prefix-sum-3d: inclusive scan along x (one warp per row) ----
 // REV = true scans from the high end (suffix sums).  In/out may alias (with
 // istride = 1); istride is the input's element stride (4 for one component
-// of the interleaved field map).
+// of the interleaved field map).  The row goes in segments of 32 x kScanCh
+// elements: all (coalesced) loads of a segment are issued before the first
+// warp scan, so the segment waits for one load latency, not kScanCh.
+constexpr int kScanCh = 16;
 template <typename TI, typename TO, bool REV>
 __global__ void __launch_bounds__(256) k_scan_rows(int rows, int nx, const TI *in, int istride, TO *out) {
   const int lane = threadIdx.x & 31;
@@ -192,24 +195,35 @@ __global__ void __launch_bounds__(256) k_scan_rows(int rows, int nx, const TI *i
   if (row >= rows) return;
   const size_t off = (size_t)row * nx;
   TO carry = 0;
-  for (int base = 0; base < nx; base += 32) {
-    const int t = base + lane;
-    const int i = REV ? nx - 1 - t : t;
-    TO v = t < nx ? (TO)in[(off + i) * istride] : (TO)0;
+  for (int base = 0; base < nx; base += 32 * kScanCh) {
+    TO v[kScanCh];
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const TO u = __shfl_up_sync(0xffffffffu, v, d);
-      if (lane >= d) v += u;
+    for (int c = 0; c < kScanCh; ++c) {
+      const int t = base + c * 32 + lane;
+      v[c] = t < nx ? (TO)in[(off + (REV ? nx - 1 - t : t)) * istride] : (TO)0;
     }
-    v += carry;
-    if (t < nx) out[off + i] = v;
-    carry = __shfl_sync(0xffffffffu, v, 31);
+#pragma unroll
+    for (int c = 0; c < kScanCh; ++c) {
+      TO x = v[c];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const TO u = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += u;
+      }
+      x += carry;
+      const int t = base + c * 32 + lane;
+      if (t < nx) out[off + (REV ? nx - 1 - t : t)] = x;
+      carry = __shfl_sync(0xffffffffu, x, 31);
+    }
   }
 }
 
 // ---- inclusive scan along y, in place; block = 32 columns x W warps ----
 // Each warp scans a chunk of rows per column (lane = column), chunk totals
-// are combined through shared memory.  grid = (ceil(nx/32), nz).
+// are combined through shared memory.  grid = (ceil(nx/32), nz).  Rows go in
+// groups of kColCh held in registers with all their loads in flight; a chunk
+// of at most kColCh rows is read once, a longer one twice (sum, then scan).
+constexpr int kColCh = 16;
 template <typename TA, bool REV>
 __global__ void __launch_bounds__(1024) k_scan_cols(int nx, int ny, TA *a) {
   __shared__ TA tot[32][33];
@@ -218,18 +232,32 @@ __global__ void __launch_bounds__(1024) k_scan_cols(int nx, int ny, TA *a) {
   const size_t slab = (size_t)blockIdx.y * ny * nx;
   const int chunk = (ny + nw - 1) / nw;
   const int r0 = warp * chunk, r1 = min(ny, r0 + chunk);
+  auto at = [&](int r) { return slab + (size_t)(REV ? ny - 1 - r : r) * nx + x; };
+  TA v[kColCh];
   TA s = 0;
   if (x < nx)
-    for (int r = r0; r < r1; ++r) s += a[slab + (size_t)(REV ? ny - 1 - r : r) * nx + x];
+    for (int g = r0; g < r1; g += kColCh) {
+#pragma unroll
+      for (int c = 0; c < kColCh; ++c) v[c] = g + c < r1 ? a[at(g + c)] : TA(0);
+#pragma unroll
+      for (int c = 0; c < kColCh; ++c) s += v[c];
+    }
   tot[warp][lane] = s;
   __syncthreads();
   TA run = 0;
   for (int w = 0; w < warp; ++w) run += tot[w][lane];
   if (x < nx)
-    for (int r = r0; r < r1; ++r) {
-      const size_t id = slab + (size_t)(REV ? ny - 1 - r : r) * nx + x;
-      run += a[id];
-      a[id] = run;
+    for (int g = r0; g < r1; g += kColCh) {
+      if (chunk > kColCh) {  // the group is no longer in registers
+#pragma unroll
+        for (int c = 0; c < kColCh; ++c) v[c] = g + c < r1 ? a[at(g + c)] : TA(0);
+      }
+#pragma unroll
+      for (int c = 0; c < kColCh; ++c)
+        if (g + c < r1) {
+          run += v[c];
+          a[at(g + c)] = run;
+        }
     }
 }
 

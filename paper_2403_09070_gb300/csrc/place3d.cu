@@ -977,6 +977,8 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
       const double arg = pi * l * (z + 0.5) / h->nz;
       zc.cz[l * kMaxNz + z] = std::cos(arg);
       zc.sz[l * kMaxNz + z] = (l * pi / h->dz) * std::sin(arg);
+      zc.cz_f[l * kMaxNz + z] = (float)zc.cz[l * kMaxNz + z];
+      zc.sz_f[l * kMaxNz + z] = (float)zc.sz[l * kMaxNz + z];
     }
   if (cudaMemcpy(h->zc, &zc, sizeof(zc), cudaMemcpyHostToDevice) != cudaSuccess) {
     fail(h, PLACE3D_ERR_CUDA, "upload failed");

@@ -97,6 +97,10 @@ struct ZStageC {
   float pi_dx_f, pi_dy_f, pi_dz_f, inv_n_f;  // the same, rounded to FP32
   double cz[kMaxNz * kMaxNz];  // cos(pi l (z+1/2)/N_z), [l][z]
   double sz[kMaxNz * kMaxNz];  // w_l sin(pi l (z+1/2)/N_z), [l][z]
+  // The same tables rounded to FP32: an FP64 -> FP32 conversion per use runs
+  // on the FP64 pipe, a small fraction of the FP32 rate on this GPU.
+  float cz_f[kMaxNz * kMaxNz];
+  float sz_f[kMaxNz * kMaxNz];
 };
 
 // Input T2[z][k][j] (x and y already transformed, j fastest).  For each
@@ -111,12 +115,16 @@ template <> struct ZPar<double> {
   static __device__ __forceinline__ double pdy(const ZStageC *z) { return z->pi_dy; }
   static __device__ __forceinline__ double pdz(const ZStageC *z) { return z->pi_dz; }
   static __device__ __forceinline__ double invn(const ZStageC *z) { return z->inv_n; }
+  static __device__ __forceinline__ double cz(const ZStageC *z, int i) { return z->cz[i]; }
+  static __device__ __forceinline__ double sz(const ZStageC *z, int i) { return z->sz[i]; }
 };
 template <> struct ZPar<float> {
   static __device__ __forceinline__ float pdx(const ZStageC *z) { return z->pi_dx_f; }
   static __device__ __forceinline__ float pdy(const ZStageC *z) { return z->pi_dy_f; }
   static __device__ __forceinline__ float pdz(const ZStageC *z) { return z->pi_dz_f; }
   static __device__ __forceinline__ float invn(const ZStageC *z) { return z->inv_n_f; }
+  static __device__ __forceinline__ float cz(const ZStageC *z, int i) { return z->cz_f[i]; }
+  static __device__ __forceinline__ float sz(const ZStageC *z, int i) { return z->sz_f[i]; }
 };
 
 // All arithmetic in T (FP32 threads stay off the FP64 pipe); the energy sum
@@ -166,7 +174,7 @@ __global__ void __launch_bounds__(256) k_zstage(const ZStageC *__restrict__ zc, 
     for (int l = 0; l < NZM; ++l) {
       T a = 0;
 #pragma unroll
-      for (int z = 0; z < NZM; ++z) a += v[z] * (T)zc->cz[l * kMaxNz + z];
+      for (int z = 0; z < NZM; ++z) a += v[z] * ZPar<T>::cz(zc, l * kMaxNz + z);
       a *= invn;
       const T wl = (T)l * ZPar<T>::pdz(zc);
       const T w2 = wj * wj + wk * wk + wl * wl;
@@ -183,8 +191,8 @@ __global__ void __launch_bounds__(256) k_zstage(const ZStageC *__restrict__ zc, 
       T sc = 0, ss = 0;
 #pragma unroll
       for (int l = 0; l < NZM; ++l) {
-        sc += psi[l] * (T)zc->cz[l * kMaxNz + z];
-        ss += psi[l] * (T)zc->sz[l * kMaxNz + z];
+        sc += psi[l] * ZPar<T>::cz(zc, l * kMaxNz + z);
+        ss += psi[l] * ZPar<T>::sz(zc, l * kMaxNz + z);
       }
       czpsi.put(z * plane + t, sc);
       szpsi.put(z * plane + t, ss);
