@@ -131,14 +131,16 @@ __device__ __forceinline__ void block_sum_atomic(T (&v)[NV], double *dst) {
   }
 }
 
-// Warp-wide sum of NV values stored (plain store) into this warp's row
-// part[global warp][NV]; k_sum_parts adds the rows up later.  No block
-// barrier and no atomics: a block-wide reduction at the end of a kernel makes
-// every warp wait for the block's slowest one, and thousands of FP64 atomics
-// to the same words serialise in the L2.  One-dimensional grids with whole
-// warps; every lane must call it.
+// Warp-wide sum of NV values stored (plain store, in the lanes' precision T)
+// into this warp's row part[global warp][NV]; k_sum_parts adds the rows up
+// later.  No block barrier and no atomics: a block-wide reduction at the end
+// of a kernel makes every warp wait for the block's slowest one, and
+// thousands of FP64 atomics to the same words serialise in the L2.  FP32
+// rows stay FP32: widening each to FP64 here would put one conversion per
+// warp and value on the FP64 pipe, which is narrow on this GPU.
+// One-dimensional grids with whole warps; every lane must call it.
 template <int NV, typename T>
-__device__ __forceinline__ void warp_sum_part(T (&v)[NV], double *__restrict__ part) {
+__device__ __forceinline__ void warp_sum_part(T (&v)[NV], T *__restrict__ part) {
   const int lane = threadIdx.x & 31;
   const size_t row = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
 #pragma unroll
@@ -146,30 +148,48 @@ __device__ __forceinline__ void warp_sum_part(T (&v)[NV], double *__restrict__ p
     T s = v[k];
 #pragma unroll
     for (int m = 16; m; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
-    if (lane == 0) part[row * NV + k] = (double)s;
+    if (lane == 0) part[row * NV + k] = s;
   }
 }
 
-// dst[k] += sum over rows r < rows of part[r][NV] (FP64): a grid-stride
-// pass, one block reduction and one atomic per block and value.
+// (hi, lo) += v.  FP64: a plain sum (lo stays 0).  FP32: Knuth's two-sum,
+// each addition rounded on its own, so hi + lo carries the sum to about
+// 2^-44 relative with FP32 operations only (integer-valued sums below 2^48,
+// such as crossing counts, stay exact).
+__device__ __forceinline__ void ff_add(double &hi, double &, double v) { hi += v; }
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float v) {
+  const float s = __fadd_rn(hi, v);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
+// dst[k] += sum over rows r < rows of part[r][NV]: a grid-stride pass in
+// the rows' precision (FP32 rows as hi + lo pairs), one block reduction
+// widened to FP64 per warp and one FP64 atomic per block and value.
 constexpr int kSumBlocks = 256;
-template <int NV>
-__global__ void __launch_bounds__(256) k_sum_parts(const double *__restrict__ part, int rows,
+template <int NV, typename TP>
+__global__ void __launch_bounds__(256) k_sum_parts(const TP *__restrict__ part, int rows,
                                                    double *__restrict__ dst) {
-  double acc[NV];
+  TP hi[NV], lo[NV];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (int k = 0; k < NV; ++k) hi[k] = lo[k] = TP(0);
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x)
 #pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] += part[(size_t)r * NV + k];
+    for (int k = 0; k < NV; ++k) ff_add(hi[k], lo[k], part[(size_t)r * NV + k]);
   __shared__ double red[8][NV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    double s = acc[k];
+    TP h = hi[k], l = lo[k];
 #pragma unroll
-    for (int m = 16; m; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
-    if (lane == 0) red[warp][k] = s;
+    for (int m = 16; m; m >>= 1) {
+      const TP oh = __shfl_xor_sync(0xffffffffu, h, m), ol = __shfl_xor_sync(0xffffffffu, l, m);
+      ff_add(h, l, oh);
+      l += ol;
+    }
+    if (lane == 0) red[warp][k] = (double)h + (double)l;
   }
   __syncthreads();
   if (threadIdx.x == 0) {

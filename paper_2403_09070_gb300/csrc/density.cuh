@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(1024) k_scan_cols(int nx, int ny, TA *a) {
 template <typename T, typename Out>
 __global__ void __launch_bounds__(256) k_densify(int nxy, int nz, const long long *__restrict__ q,
                                                  const long long *__restrict__ A, Out rho,
-                                                 double *__restrict__ part = nullptr) {
+                                                 T *__restrict__ part = nullptr) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   T v[2] = {0, 0};
   if (t < nxy) {
@@ -380,6 +380,14 @@ __device__ __forceinline__ double g_scale_of(const double *scal) {
   const double sz = scal[S_SZ];
   return sz > 0.0 ? (scal[S_SX] + scal[S_SY]) / (2.0 * sz) : 0.0;
 }
+// g in the gather's precision: FP32 gathers narrow the three norms first
+// (three conversions instead of an FP64 division on the narrow FP64 pipe).
+template <typename T> __device__ __forceinline__ T g_scale_t(const double *scal);
+template <> __device__ __forceinline__ double g_scale_t<double>(const double *scal) { return g_scale_of(scal); }
+template <> __device__ __forceinline__ float g_scale_t<float>(const double *scal) {
+  const float sz = (float)scal[S_SZ];
+  return sz > 0.0f ? ((float)scal[S_SX] + (float)scal[S_SY]) / (2.0f * sz) : 0.0f;
+}
 
 // ---- a10 + a9 + a11 per instance: cell field gather fused with the WL add ----
 // g = acc_wl + lambda * (-omega sum_b vol(D cap b) E_b); gz uses the
@@ -395,7 +403,7 @@ __global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ 
                                                TO *__restrict__ gx, TO *__restrict__ gy,
                                                TO *__restrict__ gz) {
   __shared__ T g_sh;
-  if (threadIdx.x == 0) g_sh = (T)g_scale_of(fc.scal);  // one FP64 division per block
+  if (threadIdx.x == 0) g_sh = g_scale_t<T>(fc.scal);  // once per block
   __syncthreads();
   fc.g = g_sh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -664,7 +672,7 @@ __global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ it
     wy[k] = b2;
     wz[k] = d2;
   }
-  if (threadIdx.x == 0) g_sh = (T)g_scale_of(fc.scal);
+  if (threadIdx.x == 0) g_sh = g_scale_t<T>(fc.scal);
   __syncthreads();
   const T g = g_sh;
   const int c0 = start[it.x] + it.y * kChunk, c1 = min(start[it.x + 1], c0 + kChunk);
@@ -721,7 +729,7 @@ __global__ void k_final_macros(int nm, const int *__restrict__ macro_ids, const 
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= nm) return;
   const int i = macro_ids[m];
-  const T g = (T)g_scale_of(fc.scal);
+  const T g = g_scale_t<T>(fc.scal);
   const T dgx = (T)(-(double)fc.volb * mgrad[m * 3 + 0]);
   const T dgy = (T)(-(double)fc.volb * mgrad[m * 3 + 1]);
   const T dgz = (T)(-(double)fc.volb * mgrad[m * 3 + 2]);

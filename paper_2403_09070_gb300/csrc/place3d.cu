@@ -309,7 +309,7 @@ void launch_gemm(place3d_handle *h, cudaStream_t s, std::initializer_list<GemmPr
 // one row of 4 partial sums per warp at part (returns the row count), the
 // block form adds its per-net sums to the scalars directly (returns 0).
 template <typename T>
-int launch_wl(place3d_handle *h, const Bucket &b, int G, int PPL, cudaStream_t w, const WlC<T> &c, double *part) {
+int launch_wl(place3d_handle *h, const Bucket &b, int G, int PPL, cudaStream_t w, const WlC<T> &c, T *part) {
   V4<T> *acc = as<V4<T>>(h->acc);
   const V4<T> *pos = as<V4<T>>(h->pos), *off = as<V4<T>>(h->off);
   if (G == 0) {
@@ -355,12 +355,12 @@ int sum_grid(int rows) { return std::max(1, std::min(kSumBlocks, grid_for(rows, 
 
 // Add the z stage's per-warp energy rows (blocks of 256 threads) into the
 // scalars (one per layer in 2D mode).
-void sum_energy(place3d_handle *h, cudaStream_t s, int blocks) {
+template <typename T> void sum_energy(place3d_handle *h, cudaStream_t s, int blocks) {
   const int rows = blocks * 8;
   if (h->mode2d)
-    k_sum_parts<3><<<sum_grid(rows), 256, 0, s>>>(h->part_d, rows, h->scal + S_EL0);
+    k_sum_parts<3, T><<<sum_grid(rows), 256, 0, s>>>(as<T>(h->part_d), rows, h->scal + S_EL0);
   else
-    k_sum_parts<1><<<sum_grid(rows), 256, 0, s>>>(h->part_d, rows, h->scal + S_ESUM);
+    k_sum_parts<1, T><<<sum_grid(rows), 256, 0, s>>>(as<T>(h->part_d), rows, h->scal + S_ESUM);
   count_launch(h, ST_ZSTAGE);
 }
 
@@ -381,7 +381,7 @@ template <typename T> void run_transforms(place3d_handle *h, cudaStream_t s) {
     const int g = grid_for(pl, 256);
     const T *t2 = as<T>(h->t2);
     const OutPlain<T> cz{as<T>(h->czpsi)}, sz{as<T>(h->szpsi)};
-    double *es = h->part_d;
+    T *es = as<T>(h->part_d);
     if (nz <= 2)
       k_zstage<T, 2><<<g, 256, 0, s>>>(h->zc, t2, cz, sz, es);
     else if (nz <= 4)
@@ -391,7 +391,7 @@ template <typename T> void run_transforms(place3d_handle *h, cudaStream_t s) {
     else
       k_zstage<T, 16><<<g, 256, 0, s>>>(h->zc, t2, cz, sz, es);
     count_launch(h, ST_ZSTAGE);
-    sum_energy(h, s, g);
+    sum_energy<T>(h, s, g);
   }
   {
     StageScope sc(h, ST_INV, s);
@@ -416,9 +416,9 @@ void run_transforms_tc(place3d_handle *h, cudaStream_t s) {
   }
   {
     StageScope sc(h, ST_ZSTAGE, s);
-    const int k = p3d_tc::zstage(h->tc, s, h->part_d);
+    const int k = p3d_tc::zstage(h->tc, s, as<float>(h->part_d));
     for (int i = 0; i < k; ++i) count_launch(h, ST_ZSTAGE);
-    sum_energy(h, s, (int)(((long long)h->nx * h->ny + 255) / 256));
+    sum_energy<float>(h, s, (int)(((long long)h->nx * h->ny + 255) / 256));
   }
   {
     StageScope sc(h, ST_INV, s);
@@ -460,19 +460,19 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     const WlC<T> c = wl_consts<T>(h);
     int rows = 0;
     for (const Bucket &b : h->buckets) {
-      rows += launch_wl<T>(h, b, b.G, b.PPL, w, c, h->part_w + 4 * (size_t)rows);
+      rows += launch_wl<T>(h, b, b.G, b.PPL, w, c, as<T>(h->part_w) + 4 * (size_t)rows);
       count_launch(h, ST_WIRELENGTH);
     }
     if (rows > 0) {
-      k_sum_parts<4><<<sum_grid(rows), 256, 0, w>>>(h->part_w, rows, h->scal + S_WL_BI);
+      k_sum_parts<4, T><<<sum_grid(rows), 256, 0, w>>>(as<T>(h->part_w), rows, h->scal + S_WL_BI);
       count_launch(h, ST_WIRELENGTH);
     }
   }
   {
     StageScope sc(h, ST_NORMS, w);
     const int gn = std::min(grid_for(std::max(n, 1), 256), 1216);
-    k_norms<T><<<gn, 256, 0, w>>>(n, as<V4<T>>(h->acc), h->part_w);
-    k_sum_parts<3><<<sum_grid(gn * 8), 256, 0, w>>>(h->part_w, gn * 8, h->scal + S_SX);
+    k_norms<T><<<gn, 256, 0, w>>>(n, as<V4<T>>(h->acc), as<T>(h->part_w));
+    k_sum_parts<3, T><<<sum_grid(gn * 8), 256, 0, w>>>(as<T>(h->part_w), gn * 8, h->scal + S_SX);
     count_launch(h, ST_NORMS);
     count_launch(h, ST_NORMS);
   }
@@ -514,15 +514,18 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
       count_launch(h, ST_PREFIX);
     }
     if (h->tc) {
-      p3d_tc::densify(h->tc, s, h->nx * h->ny, h->nz, h->q, h->nm > 0 ? h->corner : nullptr, h->part_d);
+      p3d_tc::densify(h->tc, s, h->nx * h->ny, h->nz, h->q, h->nm > 0 ? h->corner : nullptr, as<float>(h->part_d));
     } else {
       k_densify<T><<<grid_for((long long)h->nx * h->ny, 256), 256, 0, s>>>(
-          h->nx * h->ny, h->nz, h->q, h->nm > 0 ? h->corner : nullptr, OutPlain<T>{as<T>(h->rho)}, h->part_d);
+          h->nx * h->ny, h->nz, h->q, h->nm > 0 ? h->corner : nullptr, OutPlain<T>{as<T>(h->rho)}, as<T>(h->part_d));
     }
     count_launch(h, ST_PREFIX);
     // density overflow (sum of max(rho - 1, 0) and of rho) from densify's per-warp rows
     const int orow = grid_for((long long)h->nx * h->ny, 256) * 8;
-    k_sum_parts<2><<<sum_grid(orow), 256, 0, s>>>(h->part_d, orow, h->scal + S_OVFL);
+    if (h->tc)
+      k_sum_parts<2, float><<<sum_grid(orow), 256, 0, s>>>(as<float>(h->part_d), orow, h->scal + S_OVFL);
+    else
+      k_sum_parts<2, T><<<sum_grid(orow), 256, 0, s>>>(as<T>(h->part_d), orow, h->scal + S_OVFL);
     count_launch(h, ST_PREFIX);
   }
   if (h->tc)
@@ -1361,9 +1364,9 @@ int place3d_autotune(place3d_handle *h, int repeats) {
       for (int r = 0; r <= repeats; ++r) {
         cudaEventRecord(e0, w);
         if (h->precision == PLACE3D_FP64)
-          launch_wl<double>(h, b, G, PPL, w, wl_consts<double>(h), h->part_w);
+          launch_wl<double>(h, b, G, PPL, w, wl_consts<double>(h), as<double>(h->part_w));
         else
-          launch_wl<float>(h, b, G, PPL, w, wl_consts<float>(h), h->part_w);
+          launch_wl<float>(h, b, G, PPL, w, wl_consts<float>(h), as<float>(h->part_w));
         cudaEventRecord(e1, w);
         P3D_CUDA(h, cudaEventSynchronize(e1));
         float t = 0;

@@ -33,11 +33,14 @@
 namespace p3d_tc {
 using namespace p3d;
 
-constexpr int BM = 128, BN = 64, BK = 64, STAGES = 4;
+// Pipeline depth: 4 stages (193 KiB of shared memory, one CTA per SM) when
+// a launch has at most one tile per SM; 2 stages (97 KiB, two CTAs per SM,
+// and room beside the wirelength kernels running concurrently) otherwise.
+constexpr int BM = 128, BN = 64, BK = 64;
 constexpr int A_BYTES = BM * BK * 2;                    // one BF16 plane of an A tile (16 KiB)
 constexpr int W_BYTES = BN * BK * 2;                    // one BF16 plane of a W tile (8 KiB)
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * W_BYTES;  // 48 KiB
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+template <int STAGES> constexpr int smem_bytes() { return STAGES * STAGE_BYTES + 1024; }
 constexpr int TMEM_COLS = BN;                           // FP32 accumulator columns
 constexpr long long kWaitCycles = 4000000000LL;         // about 2 s at 2 GHz
 
@@ -170,6 +173,7 @@ __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, vola
 }
 
 // ------------------------------------------------------------------ kernel
+template <int STAGES>
 __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Group g) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bars[2 * STAGES + 1];
@@ -395,8 +399,29 @@ static bool make_group(Group *g, std::initializer_list<ProbSpec> specs, int *err
 
 static int group_tiles(const Group &g) { return g.tile_start[g.count]; }
 
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      n = v;
+  }
+  return n > 0 ? n : 1;
+}
+
 static void launch(const Group &g, cudaStream_t s) {
-  k_tc_gemm<<<group_tiles(g), 192, SMEM_BYTES, s>>>(g);
+  const int tiles = group_tiles(g);
+  if (tiles <= sm_count())
+    k_tc_gemm<4><<<tiles, 192, smem_bytes<4>(), s>>>(g);
+  else
+    k_tc_gemm<2><<<tiles, 192, smem_bytes<2>(), s>>>(g);
+}
+
+static bool reserve_smem() {
+  return cudaFuncSetAttribute(k_tc_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<4>()) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<2>()) ==
+             cudaSuccess;
 }
 
 // Round-to-nearest-even FP32 -> BF16 on the host.
@@ -468,7 +493,7 @@ TcPlan *create(int device, int nx, int ny, int nz, double dx, double dy, double 
     if (why) *why = "N_x and N_y must be multiples of 128";
     return nullptr;
   }
-  if (cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess) {
+  if (!reserve_smem()) {
     if (why) *why = "cannot reserve shared memory for the tensor-core kernel";
     return nullptr;
   }
@@ -534,7 +559,7 @@ TcPlan *create(int device, int nx, int ny, int nz, double dx, double dy, double 
   return p;
 }
 
-void densify(TcPlan *p, cudaStream_t s, int nxy, int nz, const long long *q, const long long *corner, double *part) {
+void densify(TcPlan *p, cudaStream_t s, int nxy, int nz, const long long *q, const long long *corner, float *part) {
   k_densify<float><<<(nxy + 255) / 256, 256, 0, s>>>(nxy, nz, q, corner, OutSplit{p->rho, (long long)p->nb}, part);
 }
 
@@ -544,7 +569,7 @@ int forward(TcPlan *p, cudaStream_t s) {
   return 2;
 }
 
-int zstage(TcPlan *p, cudaStream_t s, double *part) {
+int zstage(TcPlan *p, cudaStream_t s, float *part) {
   const int pl = p->nx * p->ny;
   const int g = (pl + 255) / 256;
   const OutSplit cz{p->cz, (long long)p->nb}, sz{p->sz, (long long)p->nb};
@@ -589,8 +614,7 @@ extern "C" int place3d_tc_selftest(int M, int N, int K, int batches, const float
   if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess ||
       prop.major != 10 || prop.minor != 3)
     return PLACE3D_ERR_UNSUPPORTED;
-  if (cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess)
-    return PLACE3D_ERR_CUDA;
+  if (!reserve_smem()) return PLACE3D_ERR_CUDA;
   const size_t na = (size_t)batches * M * K, nw = (size_t)N * K, no = (size_t)batches * N * M;
   std::vector<double> av(A, A + na), wv(W, W + nw);
   std::string why;
@@ -634,8 +658,7 @@ extern "C" int place3d_tc_timeout_selftest(long long wait_cycles, int *wait_erro
   if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess ||
       prop.major != 10 || prop.minor != 3)
     return PLACE3D_ERR_UNSUPPORTED;
-  if (cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess)
-    return PLACE3D_ERR_CUDA;
+  if (!reserve_smem()) return PLACE3D_ERR_CUDA;
   const int M = BM, N = BN, K = BK;
   std::vector<double> av((size_t)M * K, 0.0), wv((size_t)N * K, 0.0);
   std::string why;

@@ -22,11 +22,11 @@ TcPlan *create(int device, int nx, int ny, int nz, double dx, double dy, double 
                const p3d::ZStageC *zc, std::string *why);
 // rho (cells + macro corners, z prefix) -> split-BF16 planes of the input.
 // (part: the per-warp overflow rows, see k_densify)
-void densify(TcPlan *p, cudaStream_t s, int nxy, int nz, const long long *q, const long long *corner, double *part);
+void densify(TcPlan *p, cudaStream_t s, int nxy, int nz, const long long *q, const long long *corner, float *part);
 // Forward x and y products; z stage (scaling, energy, z transforms);
 // inverse x and y products into the interleaved field map e4.  Each returns its launch count.
 int forward(TcPlan *p, cudaStream_t s);
-int zstage(TcPlan *p, cudaStream_t s, double *part);  // per-block energy rows (see k_zstage)
+int zstage(TcPlan *p, cudaStream_t s, float *part);  // per-block energy rows (see k_zstage)
 int inverse(TcPlan *p, cudaStream_t s);
 // Error code left by a bounded wait of the tensor-core kernel (0 = none);
 // synchronises with the device.

@@ -135,7 +135,7 @@ template <> struct ZPar<float> {
 // k_sum_parts into S_ESUM or S_EL0..S_EL2.
 template <typename T, int NZM, typename Out>
 __global__ void __launch_bounds__(256) k_zstage(const ZStageC *__restrict__ zc, const T *__restrict__ in,
-                                                Out czpsi, Out szpsi, double *__restrict__ part) {
+                                                Out czpsi, Out szpsi, T *__restrict__ part) {
   const int nx = zc->nx, ny = zc->ny, nz = zc->nz;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (zc->mode2d) {

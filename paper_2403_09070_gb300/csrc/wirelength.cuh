@@ -425,7 +425,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_wl_pair(int pin0, int nnets,
                                                  const int *__restrict__ pin_inst, const V4<T> *__restrict__ off,
                                                  const V4<T> *__restrict__ pos, WlC<T> c, V4<T> *__restrict__ acc,
-                                                 double *__restrict__ part) {
+                                                 T *__restrict__ part) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   T vals[4] = {0, 0, 0, 0};
   if (t < nnets) {
@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(wl_block<T>()) k_wl_group(int net0, int nnets,
                                                             const int *__restrict__ pin_inst,
                                                             const V4<T> *__restrict__ off,
                                                             const V4<T> *__restrict__ pos, WlC<T> c0,
-                                                            V4<T> *__restrict__ acc, double *__restrict__ part) {
+                                                            V4<T> *__restrict__ acc, T *__restrict__ part) {
   WlC<T> c = c0;
   c.mode2d = M2D ? 1 : 0;
   constexpr int GR = wl_block<T>() / G;  // groups (nets) per block
@@ -742,7 +742,7 @@ __global__ void __launch_bounds__(256) k_wl_block(int net0, const int *__restric
 
 // ---- a9: L1 norms S_x, S_y, S_z of the wirelength gradient (FP64) ----
 template <typename T>
-__global__ void __launch_bounds__(256) k_norms(int n, const V4<T> *__restrict__ acc, double *__restrict__ part) {
+__global__ void __launch_bounds__(256) k_norms(int n, const V4<T> *__restrict__ acc, T *__restrict__ part) {
   T v[3] = {0, 0, 0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const V4<T> a = acc[i];
