@@ -368,6 +368,14 @@ int place3d_tc_timeout_selftest(long long wait_cycles, int *wait_error);
  * the hook; it also clears itself once it has fired. */
 void place3d_debug_fail_alloc(int nth);
 
+/* Self-test of the int64 -> FP32 conversion the FP32 density pass uses (a
+ * test hook): converts the n host values vals[] on the current device with
+ * it, writes the results to the host array out[] (n floats) and sets
+ * *mismatches to the number of values whose result differs, bit for bit,
+ * from the hardware's round-to-nearest-even conversion.
+ * Errors: INVALID_ARG (NULL pointer, n < 0), CUDA. */
+int place3d_ll2f_selftest(const long long *vals, float *out, int n, int *mismatches);
+
 /* Last error message of the handle, or of the calling thread when h is NULL
  * (creation errors).  Never NULL. */
 const char *place3d_last_error(const place3d_handle *h);

@@ -45,6 +45,27 @@ __device__ __forceinline__ long long r_rint(float a) {
   return (long long)(__float_as_int(t) - 0x4B400000);
 }
 __device__ __forceinline__ long long r_rint(double a) { return __double2ll_rn(a); }
+// int64 -> FP32, round half to even, with 32-bit and integer operations only
+// (the 64-bit integer conversion instruction runs on the FP64 pipe).  |v| =
+// m 2^sh + rem with a 24-bit m: round m by rem against half of 2^sh (ties to
+// even), then scale by 2^sh, exact.  Equal to __ll2float_rn for every v.
+__device__ __forceinline__ float r_ll2f(long long v) {
+  const bool neg = v < 0;
+  const unsigned long long u = neg ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  float r;
+  if (u < (1ull << 24)) {
+    r = __uint2float_rn((unsigned)u);  // exact
+  } else {
+    const int sh = 63 - __clzll((long long)u) - 23;  // 1 <= sh <= 40
+    unsigned m = (unsigned)(u >> sh);
+    const unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    m += (rem > half || (rem == half && (m & 1u))) ? 1u : 0u;  // m <= 2^24
+    r = __uint2float_rn(m) * __int_as_float((127 + sh) << 23);
+  }
+  return neg ? -r : r;
+}
+__device__ __forceinline__ double r_ll2f(long long v, double) { return (double)v; }
+__device__ __forceinline__ float r_ll2f(long long v, float) { return r_ll2f(v); }
 // FP32 mode uses the fast exponential (a few ulp near 0, where the dominant
 // WA terms are); FP64 mode the full-precision one.
 __device__ __forceinline__ float r_exp(float a) { return __expf(a); }

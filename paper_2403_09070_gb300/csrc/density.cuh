@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256) k_densify(int nxy, int nz, const long lon
     for (int z = 0; z < nz; ++z) {
       const size_t id = (size_t)z * nxy + t;
       if (A) acc += A[id];
-      const T r = (T)(q[id] + acc) * (T)(1.0 / kFixedScale);
+      const T r = r_ll2f(q[id] + acc, T(0)) * (T)(1.0 / kFixedScale);
       rho.put(id, r);
       v[0] += r > T(1) ? r - T(1) : T(0);
       v[1] += r;

@@ -719,6 +719,39 @@ extern "C" {
 
 void place3d_debug_fail_alloc(int nth) { g_fail_alloc = nth > 0 ? nth : 0; }
 
+namespace {
+__global__ void k_ll2f_check(const long long *v, float *out, int n, int *bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float a = r_ll2f(v[i]), b = __ll2float_rn(v[i]);
+  out[i] = a;
+  if (__float_as_uint(a) != __float_as_uint(b)) atomicAdd(bad, 1);
+}
+}  // namespace
+
+int place3d_ll2f_selftest(const long long *vals, float *out, int n, int *mismatches) {
+  if (!vals || !out || !mismatches || n < 0) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "bad selftest arguments");
+  *mismatches = 0;
+  if (n == 0) return PLACE3D_OK;
+  long long *dv = nullptr;
+  float *dout = nullptr;
+  int *dbad = nullptr;
+  int rc = PLACE3D_ERR_CUDA;
+  if (cudaMalloc(&dv, sizeof(long long) * n) == cudaSuccess && cudaMalloc(&dout, sizeof(float) * n) == cudaSuccess &&
+      cudaMalloc(&dbad, sizeof(int)) == cudaSuccess && cudaMemset(dbad, 0, sizeof(int)) == cudaSuccess &&
+      cudaMemcpy(dv, vals, sizeof(long long) * n, cudaMemcpyHostToDevice) == cudaSuccess) {
+    k_ll2f_check<<<grid_for(n, 256), 256>>>(dv, dout, n, dbad);
+    if (cudaGetLastError() == cudaSuccess &&
+        cudaMemcpy(out, dout, sizeof(float) * n, cudaMemcpyDeviceToHost) == cudaSuccess &&
+        cudaMemcpy(mismatches, dbad, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess)
+      rc = PLACE3D_OK;
+  }
+  cudaFree(dv);
+  cudaFree(dout);
+  cudaFree(dbad);
+  return rc == PLACE3D_OK ? rc : fail(nullptr, rc, "conversion self-test failed");
+}
+
 double place3d_alpha(double dx, double dz, double beta, double w_hbt, double rh_top, double rh_bot) {
   const double eta = 2.0 * w_hbt / (rh_top + rh_bot);
   return 3.5e-3 * (dx * eta * eta / dz) * std::log(90.0 * beta * eta - 1.0);

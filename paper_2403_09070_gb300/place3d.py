@@ -69,7 +69,7 @@ EXPORTS = ("place3d_create", "place3d_geometry", "place3d_alpha", "place3d_set_p
            "place3d_density_map_noalloc", "place3d_tc_selftest", "place3d_autotune", "place3d_wl_forms",
            "place3d_set_wl_form", "place3d_result_to_device", "place3d_set_params", "place3d_eval_graph",
            "place3d_batch_create", "place3d_batch_eval", "place3d_batch_destroy", "place3d_set_layer_weights",
-           "place3d_tc_timeout_selftest", "place3d_debug_fail_alloc")
+           "place3d_tc_timeout_selftest", "place3d_debug_fail_alloc", "place3d_ll2f_selftest")
 NOALLOC_MAX_BINS = 262144
 
 _lib = None
@@ -125,6 +125,7 @@ def load_library(build_if_missing: bool = True):
     L.place3d_tc_timeout_selftest.argtypes = [C.c_longlong, vp]
     L.place3d_debug_fail_alloc.argtypes = [i32]
     L.place3d_debug_fail_alloc.restype = None
+    L.place3d_ll2f_selftest.argtypes = [vp, vp, i32, vp]
     L.place3d_density_map_noalloc.argtypes = [i32] + [vp] * 8 + [d] * 4 + [i32] * 3 + [vp, vp]
     _lib = L
     return L
@@ -358,6 +359,20 @@ def debug_fail_alloc(nth: int):
     """Make the nth device allocation of the next create on this thread fail
     as out of memory (nth <= 0 clears it)."""
     load_library().place3d_debug_fail_alloc(int(nth))
+
+
+def ll2f_selftest(vals):
+    """Convert int64 values with the density pass's int64 -> FP32 routine on
+    the GPU; returns (results as float32, count differing from the hardware
+    conversion)."""
+    L = load_library()
+    v = np.ascontiguousarray(vals, dtype=np.int64)
+    out = np.zeros(v.size, np.float32)
+    bad = C.c_int(0)
+    rc = L.place3d_ll2f_selftest(v.ctypes.data, out.ctypes.data, int(v.size), C.byref(bad))
+    if rc != 0:
+        raise Place3DError(rc, L.place3d_last_error(None).decode())
+    return out, bad.value
 
 
 def tc_timeout_selftest(wait_cycles: int = 200_000_000):
