@@ -178,6 +178,10 @@ double place3d_alpha(double dx, double dz, double beta, double w_hbt,
 /* Set instance centres x, y, z ([n_inst] each, dtype PLACE3D_F32/F64, mem
  * HOST or DEVICE).  Device buffers must stay valid until the next
  * evaluation has been enqueued; they are read on the handle's stream.
+ * HOST arrays in page-locked memory the device can address (cudaHostAlloc,
+ * torch pin_memory) are read by the packing kernel directly over the
+ * CPU-GPU link (no staging copy) and must stay valid until the stream has
+ * passed the packing kernel; other host arrays are copied first.
  * z is expected in [d_z/4, 3 d_z/4]; with PLACE3D_FLAG_CHECKS a value
  * outside, or a non-finite coordinate, returns OUT_OF_RANGE (after a sync). */
 int place3d_set_positions(place3d_handle *h, const void *x, const void *y,
@@ -188,7 +192,9 @@ int place3d_set_positions(place3d_handle *h, const void *x, const void *y,
  * the device only).  If out != NULL the call synchronises the stream and
  * fills *out; with out == NULL it returns right after enqueueing and
  * place3d_get_result() fetches the scalars later.  Host gradient buffers
- * imply a synchronisation. */
+ * imply a synchronisation; page-locked ones (all three, in the handle's
+ * precision) are written by the final kernel directly over the CPU-GPU
+ * link instead of through a device copy. */
 int place3d_eval_objective_and_grad(place3d_handle *h, place3d_result *out,
                                     void *gx, void *gy, void *gz, int dtype,
                                     int mem);

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -1081,6 +1082,28 @@ static int enqueue_pack(place3d_handle *h, const void *px, const void *py, const
   return PLACE3D_OK;
 }
 
+// Device address of a host array of `bytes` bytes when its first and last
+// bytes are both in page-locked host memory the device can address (the
+// host memory is then read or written by the kernels directly, over the
+// CPU-GPU link, with no staging copy); nullptr for pageable memory.
+static const void *host_direct(const void *p, size_t bytes) {
+  if (!p || bytes == 0) return nullptr;
+  const void *ends[2] = {p, static_cast<const char *>(p) + bytes - 1};
+  const void *dev[2] = {nullptr, nullptr};
+  for (int k = 0; k < 2; ++k) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ends[k]) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    dev[k] = a.devicePointer;
+  }
+  if (static_cast<const char *>(dev[1]) - static_cast<const char *>(dev[0]) != (std::ptrdiff_t)(bytes - 1))
+    return nullptr;
+  return dev[0];
+}
+
 int place3d_set_positions(place3d_handle *h, const void *x, const void *y, const void *z, int dtype, int mem) {
   if (!h) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL handle");
   if (h->n == 0) return PLACE3D_OK;
@@ -1093,7 +1116,14 @@ int place3d_set_positions(place3d_handle *h, const void *x, const void *y, const
   const size_t eb = dtype == PLACE3D_F64 ? 8 : 4;
   const void *px = x, *py = y, *pz = z;
   StageScope sc(h, ST_PREP, s);
-  if (mem == PLACE3D_MEM_HOST) {
+  const void *dx = mem == PLACE3D_MEM_HOST ? host_direct(x, eb * n) : nullptr;
+  const void *dy = dx ? host_direct(y, eb * n) : nullptr;
+  const void *dz = dy ? host_direct(z, eb * n) : nullptr;
+  if (dz) {  // page-locked host arrays: the pack kernel reads them directly
+    px = dx;
+    py = dy;
+    pz = dz;
+  } else if (mem == PLACE3D_MEM_HOST) {
     if (!h->stage_in) P3D_CUDA(h, cudaMalloc(&h->stage_in, 3 * 8 * (size_t)n));
     char *st = static_cast<char *>(h->stage_in);
     P3D_CUDA(h, cudaMemcpyAsync(st, x, eb * n, cudaMemcpyHostToDevice, s));
@@ -1201,9 +1231,18 @@ int place3d_eval_objective_and_grad(place3d_handle *h, place3d_result *out, void
     // target: no recapture when the caller's arrays move), then copies
     const size_t es = h->esz, n = (size_t)h->n;
     void *tgt[3] = {h->gout, (char *)h->gout + n * es, (char *)h->gout + 2 * n * es};
+    // page-locked host gradient arrays: the final kernel writes them directly
+    void *hd[3] = {nullptr, nullptr, nullptr};
+    bool direct = ng && mem == PLACE3D_MEM_HOST && n > 0;
+    for (int k = 0; k < 3 && direct; ++k) {
+      hd[k] = const_cast<void *>(host_direct(k == 0 ? gx : k == 1 ? gy : gz, n * es));
+      direct = hd[k] != nullptr;
+    }
+    if (direct)
+      for (int k = 0; k < 3; ++k) tgt[k] = hd[k];
     const int rc = eval_via_graph(h, tgt);
     if (rc != PLACE3D_OK) return rc;
-    if (ng && n > 0) {
+    if (ng && n > 0 && !direct) {
       const cudaMemcpyKind kind = mem == PLACE3D_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
       for (int k = 0; k < 3; ++k)
         P3D_CUDA(h, cudaMemcpyAsync(k == 0 ? gx : k == 1 ? gy : gz, tgt[k], n * es, kind, h->stream));
