@@ -589,7 +589,11 @@ def main():
                        "l2": "flushed between timed steps (256 MiB write, outside the step's event pair)",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": job_throughput(world, a.steps, e2e_ms), "unit": UNIT,
-                    "h2d_bytes_per_step": 3 * n * esz, "d2h_bytes_per_step": 3 * n * esz + 80},
+                    "h2d_bytes_per_step": 3 * n * esz, "d2h_bytes_per_step": 3 * n * esz + 80,
+                    "path": "place3d_set_positions + place3d_eval_objective_and_grad with page-locked host "
+                            "arrays, host wall clock per step: the packing kernel reads the positions and the "
+                            "final kernel writes the gradients over the CPU-GPU link; the scalars come back "
+                            "by copy"},
             "gpu_launches": launches * a.steps,
             "roofline": roof,
             "stages": stages,
