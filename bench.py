@@ -574,6 +574,9 @@ def main():
     fp64 = None
     if not a.no_fp64 and precision != "fp64" and rank == 0 and world == 1:
         fp64 = _fp64_plain(prob, torch, P)
+    nest = None
+    if rank == 0 and world == 1 and "_2d" not in a.workload:
+        nest = _nesterov_rate(prob, precision, torch)
 
     if rank == 0:
         esz = 8 if precision == "fp64" else 4
@@ -615,10 +618,35 @@ def main():
         if fp64 is not None:
             line["fp64_plain"] = fp64
             line["speedup_vs_fp64_plain"] = value / fp64["value"]
+        if nest is not None:
+            line["nesterov"] = nest
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def _nesterov_rate(prob, precision, torch, iters=30, warmup=5, ref_iters=10):
+    """Iterations per second of the Nesterov placement loop on the workload:
+    the device-helper loop (NesterovPlacer.run) and the torch statement of it
+    (run_reference), host wall clock with a synchronise on both sides, no
+    logging inside the timed iterations."""
+    from paper_2403_09070_gb300.nesterov import NesterovPlacer
+    out = {}
+    for name, k in (("run", iters), ("run_reference", ref_iters)):
+        pl = NesterovPlacer(prob, precision=precision)
+        f = getattr(pl, name)
+        f(prob["x"], prob["y"], prob["z"], iters=warmup, log_every=0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f(prob["x"], prob["y"], prob["z"], iters=k, log_every=0)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1000.0 / k
+        pl.obj.handle.close()
+        out[name] = {"iters_per_s": 1000.0 / ms, "ms_per_iter": ms, "iters": k}
+    return {"what": "preconditioned Nesterov iterations (eq. improved-precond, Lipschitz step, projection; "
+                    "one evaluation each); `run` = the device helpers, `run_reference` = torch operations",
+            **out}
 
 
 def _fp64_plain(prob, torch, P, steps=5, warmup=2):

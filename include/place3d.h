@@ -258,13 +258,20 @@ int place3d_result_to_device(place3d_handle *h, double *dst);
 
 /* Change gamma, gamma_z, alpha and lambda for the following evaluations (a
  * placement loop anneals gamma and raises lambda, eq. analytical-placement).
- * Errors: INVALID_ARG (gamma <= 0 or a non-finite value). */
+ * lambda lives in device memory and is rewritten on the handle's stream
+ * (ordered before every later evaluation on that stream; batch launches
+ * wait for it), so changing lambda alone leaves captured CUDA graphs as
+ * they are and does not synchronise.  gamma, gamma_z and alpha are kernel
+ * arguments: a change makes the next graph launch re-capture (and update
+ * the executable graph in place).
+ * Errors: INVALID_ARG (gamma <= 0 or a non-finite value), CUDA. */
 int place3d_set_params(place3d_handle *h, double gamma, double gamma_z,
                        double alpha, double lambda);
 
 /* 2D mode: set the three layers' density weights (lambda-, lambda+,
- * lambda') for the following evaluations.  Errors: INVALID_ARG (3D handle or
- * a non-finite weight). */
+ * lambda') for the following evaluations; device-resident and
+ * stream-ordered like lambda in place3d_set_params.  Errors: INVALID_ARG
+ * (3D handle or a non-finite weight), CUDA. */
 int place3d_set_layer_weights(place3d_handle *h, const double lam[3]);
 
 /* Read an intermediate map of the last evaluation into dst (host or device,
@@ -373,6 +380,50 @@ int place3d_tc_timeout_selftest(long long wait_cycles, int *wait_error);
  * PLACE3D_ERR_OOM and frees everything it had allocated.  nth <= 0 clears
  * the hook; it also clears itself once it has fired. */
 void place3d_debug_fail_alloc(int nth);
+
+/* Nesterov placement loop on the device (Sec. III-A: the gradient-based 3D
+ * global placement; eq. improved-precond; the movable range of the centres:
+ * x, y in the region, z in [d_z/4, 3 d_z/4]).  All arrays are device arrays
+ * of n_inst elements in the handle's precision (F64 for FP64 handles, F32
+ * otherwise), all work is enqueued on the handle's stream and nothing
+ * synchronises: the step length and the norms it is estimated from stay on
+ * the device.  3D-mode handles only (INVALID_ARG otherwise).  Start:
+ *   place3d_set_positions(v); place3d_eval_objective_and_grad(h, NULL,
+ *   NULL, NULL, NULL, ...); place3d_nesterov_init(g, init_step);
+ * then per iteration:
+ *   place3d_nesterov_update(u, v, g, (a_k - 1)/a_{k+1});
+ *   place3d_eval_objective_and_grad(h, NULL, NULL, NULL, NULL, ...);
+ *   place3d_nesterov_precondition(g);
+ *
+ * place3d_nesterov_precondition: takes the gradient G of the last
+ * evaluation, which must have been place3d_eval_objective_and_grad without
+ * device gradient arrays (INVALID_ARG otherwise), and forms g_new = G / H
+ * with H_i = max(1, |E_i| + lambda q_i) for macros (|E_i| = the instance's
+ * pin count) and max(1, lambda q_i) otherwise, q_i = w_i h_i d_z/2 with the
+ * die sizes at the evaluated z; the z component is 0 for z-fixed instances.
+ * Stores g_new into g and sets the step length to |v_new - v| / |g_new - g|
+ * (2-norms over all 3 n_inst components) when both are positive,
+ * |v_new - v| being the one of the last update.
+ * place3d_nesterov_init: the same with the previous g taken as 0 and the
+ * step length set to init_step / max |g_new| (init_step > 0, in the
+ * positions' units).
+ * place3d_nesterov_update: u_new = P(v - step g), v_new = P(u_new + coef
+ * (u_new - u)) with P the clamp to the movable range; u <- u_new,
+ * v <- v_new, and v_new becomes the handle's positions for the next
+ * evaluation (as place3d_set_positions would set them).
+ * place3d_nesterov_step reads the current step length (synchronises). */
+int place3d_nesterov_init(place3d_handle *h, void *gx, void *gy, void *gz, double init_step);
+int place3d_nesterov_precondition(place3d_handle *h, void *gx, void *gy, void *gz);
+int place3d_nesterov_update(place3d_handle *h, void *ux, void *uy, void *uz, void *vx,
+                            void *vy, void *vz, const void *gx, const void *gy,
+                            const void *gz, double coef);
+int place3d_nesterov_step(place3d_handle *h, double *step);
+
+/* Number of CUDA-graph captures the handle has made so far (place3d_eval_graph
+ * and the graph behind place3d_eval_objective_and_grad; a capture follows a
+ * change of the output buffers, of gamma / gamma_z / alpha, or of the
+ * reduction forms).  -1 for a NULL handle. */
+long long place3d_graph_captures(const place3d_handle *h);
 
 /* Self-test of the int64 -> FP32 conversion the FP32 density pass uses (a
  * test hook): converts the n host values vals[] on the current device with

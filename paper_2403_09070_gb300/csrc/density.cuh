@@ -368,12 +368,15 @@ __global__ void __launch_bounds__(256) k_macro_gather_direct(const int *__restri
 }
 
 // Final assembly constants.
+// The density weights live in device memory (lam_dev), read once per block:
+// a placement loop raises lambda every iteration, and a weight read at run
+// time keeps captured CUDA graphs valid across the change.
 template <typename T> struct FinalC {
-  T lam, alpha, volb;  // volb: bin volume (2D mode: bin area)
-  const double *scal;  // device scalars (S_x, S_y, S_z for g)
-  T g;                 // filled per block from scal
-  int mode2d;          // 2D mode: per-layer lambda, no z-gradient
-  T lam_l[3];          // 2D mode: (lambda-, lambda+, lambda')
+  T alpha, volb;         // volb: bin volume (2D mode: bin area)
+  const double *scal;    // device scalars (S_x, S_y, S_z for g)
+  const T *lam_dev;      // device: lambda, then the 2D layer weights (lambda-, lambda+, lambda')
+  T g;                   // filled per block from scal
+  int mode2d;            // 2D mode: per-layer lambda, no z-gradient
 };
 
 __device__ __forceinline__ double g_scale_of(const double *scal) {
@@ -402,8 +405,9 @@ __global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ 
                                                const V4<T> *__restrict__ acc, FinalC<T> fc,
                                                TO *__restrict__ gx, TO *__restrict__ gy,
                                                TO *__restrict__ gz) {
-  __shared__ T g_sh;
+  __shared__ T g_sh, lam_sh[4];
   if (threadIdx.x == 0) g_sh = g_scale_t<T>(fc.scal);  // once per block
+  if (threadIdx.x < 4) lam_sh[threadIdx.x] = fc.lam_dev[threadIdx.x];
   __syncthreads();
   fc.g = g_sh;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -446,8 +450,8 @@ __global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ 
   }
   const V4<T> a = acc[i];
   const T g = fc.g;
-  T lam = fc.lam;
-  if (fc.mode2d) lam = fc.lam_l[(f & 4) ? 2 : (p.z > c.zmid ? 1 : 0)];
+  T lam = lam_sh[0];
+  if (fc.mode2d) lam = lam_sh[1 + ((f & 4) ? 2 : (p.z > c.zmid ? 1 : 0))];
   T ozg = g * a.z + fc.alpha * a.w + lam * dgz;
   if ((f & 2) || fc.mode2d) ozg = T(0);
   gx[i] = (TO)(a.x + lam * dgx);
@@ -652,7 +656,7 @@ __global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ it
                                                      FinalC<T> fc, V4<T> *__restrict__ g4) {
   extern __shared__ __align__(16) unsigned char fwin_raw[];
   T *wx = reinterpret_cast<T *>(fwin_raw);
-  __shared__ T g_sh;
+  __shared__ T g_sh, lam_sh;
   if ((int)blockIdx.x >= *nitems) return;
   const int2 it = items[blockIdx.x];
   int x0, y0;
@@ -672,9 +676,12 @@ __global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ it
     wy[k] = b2;
     wz[k] = d2;
   }
-  if (threadIdx.x == 0) g_sh = g_scale_t<T>(fc.scal);
+  if (threadIdx.x == 0) {
+    g_sh = g_scale_t<T>(fc.scal);
+    lam_sh = fc.lam_dev[0];
+  }
   __syncthreads();
-  const T g = g_sh;
+  const T g = g_sh, lam = lam_sh;
   const int c0 = start[it.x] + it.y * kChunk, c1 = min(start[it.x + 1], c0 + kChunk);
   for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) {
     const CellRec<T> r = rec[s];
@@ -710,11 +717,11 @@ __global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ it
       }
     }
     const T kk = -b.om * fc.volb;
-    T ozg = g * a.z + fc.alpha * a.w + fc.lam * (kk * sz);
+    T ozg = g * a.z + fc.alpha * a.w + lam * (kk * sz);
     if (f & 2) ozg = T(0);
     V4<T> o;
-    o.x = a.x + fc.lam * (kk * sx);
-    o.y = a.y + fc.lam * (kk * sy);
+    o.x = a.x + lam * (kk * sx);
+    o.y = a.y + lam * (kk * sy);
     o.z = ozg;
     o.w = T(0);
     g4[i] = o;
@@ -729,16 +736,16 @@ __global__ void k_final_macros(int nm, const int *__restrict__ macro_ids, const 
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= nm) return;
   const int i = macro_ids[m];
-  const T g = g_scale_t<T>(fc.scal);
+  const T g = g_scale_t<T>(fc.scal), lam = fc.lam_dev[0];
   const T dgx = (T)(-(double)fc.volb * mgrad[m * 3 + 0]);
   const T dgy = (T)(-(double)fc.volb * mgrad[m * 3 + 1]);
   const T dgz = (T)(-(double)fc.volb * mgrad[m * 3 + 2]);
   const V4<T> a = acc[i];
-  T ozg = g * a.z + fc.alpha * a.w + fc.lam * dgz;
+  T ozg = g * a.z + fc.alpha * a.w + lam * dgz;
   if (flags[i] & 2) ozg = T(0);
   V4<T> o;
-  o.x = a.x + fc.lam * dgx;
-  o.y = a.y + fc.lam * dgy;
+  o.x = a.x + lam * dgx;
+  o.y = a.y + lam * dgy;
   o.z = ozg;
   o.w = T(0);
   g4[i] = o;

@@ -18,6 +18,7 @@
 #include "tc_gemm.h"
 #include "transform.cuh"
 #include "wirelength.cuh"
+#include "nesterov.cuh"
 
 using namespace p3d;
 
@@ -71,6 +72,16 @@ struct place3d_handle {
   double lam_layer[3] = {0, 0, 0};     // 2D mode: density weights of the three layers
   cudaStream_t stream = nullptr, side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_dens = nullptr;
+  // density weights on the device: double[4] then float[4] (lambda, then the
+  // 2D layer weights), written on the handle's stream by set_params /
+  // set_layer_weights; ev_param marks the last such write
+  void *d_lam = nullptr;
+  cudaEvent_t ev_param = nullptr;
+  // Nesterov loop helpers: pins per instance (eq. improved-precond), the
+  // loop state and its per-warp partial rows
+  float *npins = nullptr;
+  NestState *nest = nullptr;
+  void *part_n = nullptr;
   // the density path (the critical chain into the final gather) runs on a
   // greatest-priority stream so that its kernels take SMs first; the
   // wirelength path fills the rest
@@ -90,7 +101,7 @@ struct place3d_handle {
   int nx = 0, ny = 0, nz = 0;
   size_t nb = 0;
   double wb = 0, hb = 0, db = 0, dx = 0, dy = 0, dz = 0;
-  double xl = 0, yl = 0;  // region origin
+  double xl = 0, yl = 0, xh = 0, yh = 0;  // region
   double gamma = 0, gamma_z = 0, alpha = 0, lambda = 0;
   size_t esz = 8;  // bytes per real
   // device buffers
@@ -125,12 +136,14 @@ struct place3d_handle {
   // bumped by every change that a captured graph bakes in (gamma, lambda,
   // alpha, layer weights, reduction forms); graphs recapture when it moved
   unsigned version = 0, gversion = 0;
+  long long captures = 0;  // graph captures (eval_graph and the internal evaluation graph)
   cudaStream_t cap_stream = nullptr;
   const void *gptr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int gdtype = -1;
   // results
   double host_scal[S_COUNT];
   bool have_result = false;
+  bool gout_fresh = false;  // the last evaluation's gradient is in gout (what the Nesterov helpers read)
   std::string err;
   int launches = 0;
   // profiling
@@ -198,6 +211,31 @@ void count_launch(place3d_handle *h, int stage) {
 }
 
 int grid_for(long long n, int block) { return (int)((n + block - 1) / block); }
+
+// The device density weights in precision T (see place3d_handle::d_lam).
+template <typename T> const T *lam_dev(const place3d_handle *h) {
+  return reinterpret_cast<const T *>(static_cast<const char *>(h->d_lam) + (sizeof(T) == 8 ? 0 : 4 * sizeof(double)));
+}
+
+__global__ void k_set_lam(void *dst, double l0, double l1, double l2, double l3) {
+  double *d = static_cast<double *>(dst);
+  float *f = reinterpret_cast<float *>(d + 4);
+  const double v[4] = {l0, l1, l2, l3};
+  for (int k = 0; k < 4; ++k) {
+    d[k] = v[k];
+    f[k] = (float)v[k];
+  }
+}
+
+// Write lambda and the layer weights to the device on the handle's stream
+// (ordered before every later evaluation on it; batches on other streams
+// wait for ev_param).
+int upload_lam(place3d_handle *h) {
+  k_set_lam<<<1, 1, 0, h->stream>>>(h->d_lam, h->lambda, h->lam_layer[0], h->lam_layer[1], h->lam_layer[2]);
+  P3D_CUDA(h, cudaGetLastError());
+  P3D_CUDA(h, cudaEventRecord(h->ev_param, h->stream));
+  return PLACE3D_OK;
+}
 
 // Test hook (place3d_debug_fail_alloc): when positive, the n-th device
 // allocation of a later place3d_create on this thread reports
@@ -559,12 +597,12 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
   {
     StageScope sc(h, ST_FINAL, s);
     FinalC<T> fc;
-    fc.lam = (T)h->lambda;
     fc.alpha = (T)h->alpha;
     fc.volb = (T)(h->mode2d ? h->wb * h->hb : h->wb * h->hb * h->db);  // 2D: bin area
     fc.scal = h->scal;
+    fc.lam_dev = lam_dev<T>(h);
+    fc.g = T(0);
     fc.mode2d = h->mode2d ? 1 : 0;
-    for (int l = 0; l < 3; ++l) fc.lam_l[l] = (T)h->lam_layer[l];
     const bool direct = mem == PLACE3D_MEM_DEVICE && gx && gy && gz;
     const int odt = direct ? dtype : (sizeof(T) == 8 ? PLACE3D_F64 : PLACE3D_F32);
     void *ox = direct ? gx : h->gout;
@@ -642,7 +680,7 @@ void free_all(place3d_handle *h) {
                   h->net_start, h->pin_inst, h->q, h->corner, h->rho, h->t1, h->t2, h->czpsi,
                   h->szpsi, h->xinv, h->x2, h->e4, h->mats, h->suffix, h->mgrad,
                   h->scal, h->zc, h->gout, h->stage_in, h->check_flag, h->tkey, h->titems,
-                  h->part_w, h->part_d,
+                  h->part_w, h->part_d, h->d_lam, h->npins, h->nest, h->part_n,
                   h->tcount, h->tstart, h->tnitems, h->trec, h->g4};
   for (void *b : bufs)
     if (b) cudaFree(b);
@@ -652,6 +690,7 @@ void free_all(place3d_handle *h) {
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_dens) cudaEventDestroy(h->ev_dens);
+  if (h->ev_param) cudaEventDestroy(h->ev_param);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->dens) cudaStreamDestroy(h->dens);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
@@ -842,6 +881,8 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
   std::memset(h->stage_launch, 0, sizeof(h->stage_launch));
   h->xl = p->xl;
   h->yl = p->yl;
+  h->xh = p->xh;
+  h->yh = p->yh;
   h->mode2d = p->mode == PLACE3D_MODE_2D;
   for (int l = 0; l < 3; ++l) h->lam_layer[l] = h->mode2d ? p->lam_layer[l] : 0.0;
   auto bail = [&](int code) {
@@ -946,6 +987,9 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
       {&h->e4, 4 * es * nb},
       {(void **)&h->suffix, h->nm && !h->macro_direct ? 3 * 8 * nb : (size_t)8}, {(void **)&h->mgrad, (size_t)24 * std::max(h->nm, 1)},
       {(void **)&h->scal, sizeof(double) * S_COUNT}, {(void **)&h->zc, sizeof(ZStageC)},
+      {&h->d_lam, 8 * sizeof(double)},
+      {(void **)&h->npins, sizeof(float) * nn}, {(void **)&h->nest, sizeof(NestState)},
+      {&h->part_n, sizeof(double) * 8 * (size_t)grid_for((long long)nn, 256)},
       {&h->gout, 3 * es * nn}, {(void **)&h->check_flag, sizeof(int)},
       {(void **)&h->tkey, sizeof(int2) * nn},
       {&h->trec, (p->precision == PLACE3D_FP64 ? sizeof(CellRec<double>) : sizeof(CellRec<float>)) * nn},
@@ -980,13 +1024,23 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
       cudaStreamCreateWithPriority(&h->dens, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_dens, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_dens, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_param, cudaEventDisableTiming) != cudaSuccess) {
     fail(h, PLACE3D_ERR_CUDA, "stream/event creation failed");
     return bail(PLACE3D_ERR_CUDA);
   }
   int rc = h->precision == PLACE3D_FP64 ? upload_typed<double>(h, p, order, new_start)
                                         : upload_typed<float>(h, p, order, new_start);
   if (rc != PLACE3D_OK) return bail(rc);
+  {
+    std::vector<float> np(nn, 0.0f);
+    for (int k = 0; k < p->n_pin; ++k) np[p->pin_inst[k]] += 1.0f;
+    if (cudaMemcpy(h->npins, np.data(), sizeof(float) * nn, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(h->nest, 0, sizeof(NestState)) != cudaSuccess) {
+      fail(h, PLACE3D_ERR_CUDA, "upload failed");
+      return bail(PLACE3D_ERR_CUDA);
+    }
+  }
   if (cudaMemcpy(h->flags_d, fl.data(), nn, cudaMemcpyHostToDevice) != cudaSuccess ||
       (h->nm && cudaMemcpy(h->macro_ids, mids.data(), sizeof(int) * h->nm, cudaMemcpyHostToDevice) != cudaSuccess) ||
       cudaMemcpy(h->macro_slot, mslot.data(), sizeof(int) * nn, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -1040,6 +1094,10 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
       fail(h, PLACE3D_ERR_UNSUPPORTED, "FP32_TC: " + why);
       return bail(PLACE3D_ERR_UNSUPPORTED);
     }
+  }
+  {
+    const int rl = upload_lam(h);
+    if (rl != PLACE3D_OK) return bail(rl);
   }
   *out = h;
   return PLACE3D_OK;
@@ -1212,6 +1270,7 @@ static int eval_via_graph(place3d_handle *h, void *const tgt[3]) {
     if (ei != cudaSuccess) return cuda_fail(h, ei, "cudaGraphInstantiate");
     for (int k = 0; k < 3; ++k) h->egptr[k] = tgt[k];
     h->egversion = h->version;
+    ++h->captures;
   }
   P3D_CUDA(h, cudaGraphLaunch(h->egexec, h->stream));
   return PLACE3D_OK;
@@ -1247,10 +1306,12 @@ int place3d_eval_objective_and_grad(place3d_handle *h, place3d_result *out, void
       for (int k = 0; k < 3; ++k)
         P3D_CUDA(h, cudaMemcpyAsync(k == 0 ? gx : k == 1 ? gy : gz, tgt[k], n * es, kind, h->stream));
     }
+    h->gout_fresh = !direct;
   } else {
     const int rc = h->precision == PLACE3D_FP64 ? eval_impl<double>(h, gx, gy, gz, dtype, mem)
                                                 : eval_impl<float>(h, gx, gy, gz, dtype, mem);
     if (rc != PLACE3D_OK) return rc;
+    h->gout_fresh = !(mem == PLACE3D_MEM_DEVICE && ng);  // eval_impl writes device outputs directly
   }
   h->have_result = true;
   if (out || (ng && mem == PLACE3D_MEM_HOST)) {
@@ -1397,12 +1458,15 @@ int place3d_set_params(place3d_handle *h, double gamma, double gamma_z, double a
   if (!(gamma > 0) || !std::isfinite(gamma) || !std::isfinite(gamma_z) || !std::isfinite(alpha) ||
       !std::isfinite(lambda))
     return fail(h, PLACE3D_ERR_INVALID_ARG, "gamma must be > 0; gamma_z, alpha, lambda finite");
+  P3D_CUDA(h, cudaSetDevice(h->device));
+  // gamma, gamma_z and alpha are kernel arguments (a change re-captures the
+  // graphs at their next launch); lambda is read from the device
+  if (gamma != h->gamma || gamma_z != h->gamma_z || alpha != h->alpha) ++h->version;
   h->gamma = gamma;
   h->gamma_z = gamma_z;
   h->alpha = alpha;
   h->lambda = lambda;
-  ++h->version;
-  return PLACE3D_OK;
+  return upload_lam(h);
 }
 
 int place3d_set_layer_weights(place3d_handle *h, const double lam[3]) {
@@ -1410,9 +1474,9 @@ int place3d_set_layer_weights(place3d_handle *h, const double lam[3]) {
   if (!h->mode2d) return fail(h, PLACE3D_ERR_INVALID_ARG, "layer weights need a 2D-mode handle");
   for (int l = 0; l < 3; ++l)
     if (!std::isfinite(lam[l])) return fail(h, PLACE3D_ERR_INVALID_ARG, "layer weights must be finite");
+  P3D_CUDA(h, cudaSetDevice(h->device));
   for (int l = 0; l < 3; ++l) h->lam_layer[l] = lam[l];
-  ++h->version;
-  return PLACE3D_OK;
+  return upload_lam(h);  // read from the device: graphs stay valid
 }
 
 int place3d_autotune(place3d_handle *h, int repeats) {
@@ -1531,9 +1595,113 @@ int place3d_eval_graph(place3d_handle *h, const void *x, const void *y, const vo
     for (int k = 0; k < 6; ++k) h->gptr[k] = ptr[k];
     h->gdtype = dtype;
     h->gversion = h->version;
+    ++h->captures;
   }
   P3D_CUDA(h, cudaGraphLaunch(h->gexec, h->stream));
   h->have_result = true;
+  h->gout_fresh = false;
+  return PLACE3D_OK;
+}
+
+long long place3d_graph_captures(const place3d_handle *h) { return h ? h->captures : -1; }
+
+// ---------------- Nesterov loop helpers ----------------
+// The sums dv2, dg2 and gmax start at 0 (create, and k_nest_step clears them
+// after each use); the gradient preconditioned is the last evaluation's, in
+// the handle's own gradient buffer.
+extern "C++" {
+template <typename T>
+static int nest_precond(place3d_handle *h, void *gx, void *gy, void *gz, double init_step) {
+  cudaStream_t s = h->stream;
+  const int n = h->n, g = grid_for(n, 256);
+  if (n > 0) {
+    const T *G = as<T>(h->gout);
+    k_nest_precond<T><<<g, 256, 0, s>>>(n, G, G + n, G + 2 * (size_t)n, (T *)gx, (T *)gy, (T *)gz,
+                                        as<V4<T>>(h->pos), as<V4<T>>(h->size), h->flags_d, h->npins, lam_dev<T>(h),
+                                        (T)(0.5 * h->dz), (T)(0.5 * h->dz), as<T>(h->part_n),
+                                        init_step > 0 ? &h->nest->gmax_bits : nullptr);
+    k_sum_parts<1, T><<<sum_grid(g * 8), 256, 0, s>>>(as<T>(h->part_n), g * 8, &h->nest->dg2);
+  }
+  k_nest_step<<<1, 1, 0, s>>>(h->nest, init_step);
+  P3D_CUDA(h, cudaGetLastError());
+  return PLACE3D_OK;
+}
+}  // extern "C++"
+
+static int nest_check(place3d_handle *h, const void *const *ptrs, int count, bool need_grad) {
+  if (!h) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL handle");
+  if (h->mode2d) return fail(h, PLACE3D_ERR_INVALID_ARG, "the Nesterov helpers need a 3D-mode handle");
+  for (int k = 0; k < count; ++k)
+    if (!ptrs[k] && h->n > 0) return fail(h, PLACE3D_ERR_INVALID_ARG, "NULL device array");
+  if (need_grad && !h->gout_fresh)
+    return fail(h, PLACE3D_ERR_INVALID_ARG,
+                "the last evaluation must be place3d_eval_objective_and_grad without device gradient arrays");
+  P3D_CUDA(h, cudaSetDevice(h->device));
+  return PLACE3D_OK;
+}
+
+int place3d_nesterov_precondition(place3d_handle *h, void *gx, void *gy, void *gz) {
+  const void *ptrs[3] = {gx, gy, gz};
+  const int rc = nest_check(h, ptrs, 3, true);
+  if (rc != PLACE3D_OK) return rc;
+  return h->precision == PLACE3D_FP64 ? nest_precond<double>(h, gx, gy, gz, 0.0)
+                                      : nest_precond<float>(h, gx, gy, gz, 0.0);
+}
+
+int place3d_nesterov_init(place3d_handle *h, void *gx, void *gy, void *gz, double init_step) {
+  const void *ptrs[3] = {gx, gy, gz};
+  const int rc = nest_check(h, ptrs, 3, true);
+  if (rc != PLACE3D_OK) return rc;
+  if (!(init_step > 0) || !std::isfinite(init_step)) return fail(h, PLACE3D_ERR_INVALID_ARG, "init_step must be > 0");
+  const size_t es = h->esz * (size_t)h->n;
+  cudaStream_t s = h->stream;
+  for (void *p : {gx, gy, gz})  // the previous preconditioned gradient starts at 0
+    if (es) P3D_CUDA(h, cudaMemsetAsync(p, 0, es, s));
+  return h->precision == PLACE3D_FP64 ? nest_precond<double>(h, gx, gy, gz, init_step)
+                                      : nest_precond<float>(h, gx, gy, gz, init_step);
+}
+
+extern "C++" {
+template <typename T>
+static int nest_update(place3d_handle *h, void *const *u, void *const *v, const void *const *g, double coef) {
+  cudaStream_t s = h->stream;
+  const int n = h->n, gr = grid_for(n, 256);
+  NestBox<T> b;
+  b.lo[0] = (T)h->xl;
+  b.hi[0] = (T)h->xh;
+  b.lo[1] = (T)h->yl;
+  b.hi[1] = (T)h->yh;
+  b.lo[2] = (T)(0.25 * h->dz);
+  b.hi[2] = (T)(0.75 * h->dz);
+  if (n > 0) {
+    k_nest_update<T><<<gr, 256, 0, s>>>(n, (T *)u[0], (T *)u[1], (T *)u[2], (T *)v[0], (T *)v[1], (T *)v[2],
+                                        (const T *)g[0], (const T *)g[1], (const T *)g[2], h->nest, (T)coef, b,
+                                        as<V4<T>>(h->pos), as<T>(h->part_n));
+    k_sum_parts<1, T><<<sum_grid(gr * 8), 256, 0, s>>>(as<T>(h->part_n), gr * 8, &h->nest->dv2);
+  }
+  P3D_CUDA(h, cudaGetLastError());
+  return PLACE3D_OK;
+}
+}  // extern "C++"
+
+int place3d_nesterov_update(place3d_handle *h, void *ux, void *uy, void *uz, void *vx, void *vy, void *vz,
+                            const void *gx, const void *gy, const void *gz, double coef) {
+  const void *ptrs[9] = {ux, uy, uz, vx, vy, vz, gx, gy, gz};
+  const int rc = nest_check(h, ptrs, 9, false);
+  if (rc != PLACE3D_OK) return rc;
+  if (!std::isfinite(coef)) return fail(h, PLACE3D_ERR_INVALID_ARG, "coef must be finite");
+  void *u[3] = {ux, uy, uz}, *v[3] = {vx, vy, vz};
+  const void *g[3] = {gx, gy, gz};
+  return h->precision == PLACE3D_FP64 ? nest_update<double>(h, u, v, g, coef) : nest_update<float>(h, u, v, g, coef);
+}
+
+int place3d_nesterov_step(place3d_handle *h, double *step) {
+  if (!h || !step) return fail(h, PLACE3D_ERR_INVALID_ARG, "NULL argument");
+  P3D_CUDA(h, cudaSetDevice(h->device));
+  NestState st;
+  P3D_CUDA(h, cudaMemcpyAsync(&st, h->nest, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+  P3D_CUDA(h, cudaStreamSynchronize(h->stream));
+  *step = st.step;
   return PLACE3D_OK;
 }
 
@@ -1670,8 +1838,15 @@ int place3d_batch_eval(place3d_batch *b, const void *const *xs, const void *cons
     b->versions = vers;
     b->dtype = dtype;
   }
+  // density weights written by set_params on the handles' streams come first
+  for (auto *h : b->hs)
+    if (cudaStreamWaitEvent(static_cast<cudaStream_t>(cuda_stream), h->ev_param, 0) != cudaSuccess)
+      return PLACE3D_ERR_CUDA;
   if (cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(cuda_stream)) != cudaSuccess) return PLACE3D_ERR_CUDA;
-  for (auto *h : b->hs) h->have_result = true;
+  for (auto *h : b->hs) {
+    h->have_result = true;
+    h->gout_fresh = false;
+  }
   return PLACE3D_OK;
 }
 

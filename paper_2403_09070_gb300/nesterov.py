@@ -1,11 +1,17 @@
 """Nesterov placement loop over the place3d evaluation (Sec. III-A, the
 gradient-based 3D global placement of Fig. overall-flow).
 
-Per iteration: gradient at the reference solution through the autograd
-wrapper, 3D mixed-size preconditioning (eq. improved-precond), a Nesterov
-step with the step length predicted from a Lipschitz estimate, and
-projection of the centres into the region with z in [d_z/4, 3 d_z/4]
-(Sec. III-A movable range).  The density weight lambda grows geometrically.
+Per iteration: gradient at the reference solution, 3D mixed-size
+preconditioning (eq. improved-precond), a Nesterov step with the step length
+predicted from a Lipschitz estimate, and projection of the centres into the
+region with z in [d_z/4, 3 d_z/4] (Sec. III-A movable range).  The density
+weight lambda grows geometrically.
+
+`run` drives the loop through the library's device helpers
+(place3d_nesterov_update / _precondition: the step length never leaves the
+GPU, no host synchronisation per iteration); `run_reference` is the same
+loop written with torch operations over the autograd wrapper, kept as the
+readable statement of the method and as the fused loop's test reference.
 """
 from __future__ import annotations
 
@@ -67,7 +73,38 @@ class NesterovPlacer:
         return f.detach(), gv
 
     def run(self, x, y, z, iters: int = 100, log_every: int = 10, callback=None):
-        """Returns the final positions and a history of (iter, obj, wl_bi, hpwl_d2d, energy, lambda)."""
+        """The loop on the device helpers.  Returns the final positions (a
+        [3][n] tensor) and a history of (iter, obj, wl_bi, hpwl_d2d, energy,
+        lambda); logging synchronises, every log_every iterations."""
+        h = self.obj.handle
+        n = self.p["n_inst"]
+        u = self._project(torch.stack([torch.as_tensor(a, dtype=self.dt, device=self.dev) for a in (x, y, z)]))
+        u = u.contiguous()
+        v = u.clone()
+        g = torch.empty((3, n), dtype=self.dt, device=self.dev)
+        h.set_positions(v[0], v[1], v[2])
+        h.eval(sync=False)  # the gradient stays in the handle, where the helpers read it
+        h.nesterov_init(g, self.init_step)
+        a = 1.0
+        hist = []
+        for k in range(iters):
+            a_new = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * a * a))
+            h.nesterov_update(u, v, g, (a - 1.0) / a_new)  # also the next positions
+            h.eval(sync=False)
+            h.nesterov_precondition(g)
+            a = a_new
+            if log_every and (k % log_every == 0 or k == iters - 1):
+                h.result_to_device(self.obj.scalars)
+                s = self.obj.last_scalars()
+                hist.append((k, s["obj"], s["wl_bi"], s["hpwl_d2d"], s["energy"], self.obj.lam))
+                if callback:
+                    callback(k, s)
+            self.obj.set_params(lam=self.obj.lam * self.lam_mult)
+        return u, hist
+
+    def run_reference(self, x, y, z, iters: int = 100, log_every: int = 10, callback=None):
+        """The same loop with torch operations.  Returns the final positions
+        and a history of (iter, obj, wl_bi, hpwl_d2d, energy, lambda)."""
         u = self._project(torch.stack([torch.as_tensor(a, dtype=self.dt, device=self.dev) for a in (x, y, z)]))
         v = u.clone()
         a = 1.0

@@ -69,7 +69,9 @@ EXPORTS = ("place3d_create", "place3d_geometry", "place3d_alpha", "place3d_set_p
            "place3d_density_map_noalloc", "place3d_tc_selftest", "place3d_autotune", "place3d_wl_forms",
            "place3d_set_wl_form", "place3d_result_to_device", "place3d_set_params", "place3d_eval_graph",
            "place3d_batch_create", "place3d_batch_eval", "place3d_batch_destroy", "place3d_set_layer_weights",
-           "place3d_tc_timeout_selftest", "place3d_debug_fail_alloc", "place3d_ll2f_selftest")
+           "place3d_tc_timeout_selftest", "place3d_debug_fail_alloc", "place3d_ll2f_selftest",
+           "place3d_graph_captures", "place3d_nesterov_init", "place3d_nesterov_precondition",
+           "place3d_nesterov_update", "place3d_nesterov_step")
 NOALLOC_MAX_BINS = 262144
 
 _lib = None
@@ -126,6 +128,12 @@ def load_library(build_if_missing: bool = True):
     L.place3d_debug_fail_alloc.argtypes = [i32]
     L.place3d_debug_fail_alloc.restype = None
     L.place3d_ll2f_selftest.argtypes = [vp, vp, i32, vp]
+    L.place3d_graph_captures.argtypes = [vp]
+    L.place3d_graph_captures.restype = C.c_longlong
+    L.place3d_nesterov_init.argtypes = [vp] * 4 + [d]
+    L.place3d_nesterov_precondition.argtypes = [vp] * 4
+    L.place3d_nesterov_update.argtypes = [vp] * 10 + [d]
+    L.place3d_nesterov_step.argtypes = [vp, vp]
     L.place3d_density_map_noalloc.argtypes = [i32] + [vp] * 8 + [d] * 4 + [i32] * 3 + [vp, vp]
     _lib = L
     return L
@@ -329,6 +337,37 @@ class Place3D:
 
     def set_wl_form(self, bucket: int, lanes: int, pins: int):
         self._check(self._L.place3d_set_wl_form(self._h, int(bucket), int(lanes), int(pins)))
+
+    def _dev(self, arrs):
+        b = [_buf(a) for a in arrs]
+        want = F64 if self.precision == PRECISIONS["fp64"] else F32
+        if any(v[2] != MEM_DEVICE or v[1] != want for v in b):
+            raise ValueError("the Nesterov helpers take CUDA tensors in the handle's precision")
+        return [v[0] for v in b]
+
+    def nesterov_init(self, g, init_step: float):
+        """g <- the last evaluation's gradient / H; step <- init_step / max |g|
+        (device, no sync; the evaluation: eval() without gradient arrays)."""
+        self._check(self._L.place3d_nesterov_init(self._h, *self._dev(list(g)), float(init_step)))
+
+    def nesterov_precondition(self, g):
+        """g <- the last evaluation's gradient / H (eq. improved-precond);
+        step <- |dv| / |dg| (device, no sync)."""
+        self._check(self._L.place3d_nesterov_precondition(self._h, *self._dev(list(g))))
+
+    def nesterov_update(self, u, v, g, coef: float):
+        """u <- P(v - step g); v <- P(u_new + coef (u_new - u)), also the
+        positions of the next evaluation (device, no sync)."""
+        self._check(self._L.place3d_nesterov_update(self._h, *self._dev(list(u) + list(v) + list(g)), float(coef)))
+
+    def nesterov_step(self) -> float:
+        s = C.c_double(0)
+        self._check(self._L.place3d_nesterov_step(self._h, C.byref(s)))
+        return s.value
+
+    def graph_captures(self) -> int:
+        """CUDA-graph captures made by this handle so far."""
+        return int(self._L.place3d_graph_captures(self._h))
 
     def launches_per_eval(self) -> int:
         return int(self._L.place3d_launches_per_eval(self._h))

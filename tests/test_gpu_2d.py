@@ -87,7 +87,7 @@ def test_2d_cells_200k_tensor_cores():
 def test_2d_layer_weights_seen_by_captured_graph():
     """set_layer_weights changes the objective by the weighted layer
     energies, and a graph captured before the change picks the new weights
-    up (it is re-captured and updated in place at its next launch)."""
+    up (the weights are read from device memory at run time)."""
     from paper_2403_09070_gb300 import place3d as P
     q = _problem2d()
     n = q["n_inst"]
@@ -106,8 +106,9 @@ def test_2d_layer_weights_seen_by_captured_graph():
 
 def test_graph_sees_set_params():
     """3D mode: a graph captured before place3d_set_params evaluates with the
-    new gamma and lambda afterwards (the parameters are kernel arguments: the
-    graph is re-captured and updated in place at its next launch)."""
+    new gamma and lambda afterwards (gamma is a kernel argument: the graph is
+    re-captured and updated in place at its next launch; lambda is read from
+    device memory)."""
     from paper_2403_09070_gb300 import place3d as P
     p = synth.make_problem("cells_2k")
     n = p["n_inst"]
@@ -159,3 +160,38 @@ def test_2d_one_die_no_hbts(precision):
     assert r["n_cross"] == 0 and r["energy_layer"][1] == 0 and r["energy_layer"][2] == 0
     assert r["energy_layer"][0] > 0
     assert rel_l2(g[0], ref["gx"]) < (1e-9 if precision == "fp64" else 1e-4)
+
+
+def test_lambda_change_keeps_graph_gamma_change_recaptures():
+    """A new lambda is read from device memory by the captured graph (no new
+    capture, results equal a fresh plain evaluation); a new gamma re-captures
+    once."""
+    from paper_2403_09070_gb300 import place3d as P
+    p = synth.make_problem("cells_2k")
+    n = p["n_inst"]
+    xyz = [torch.tensor(p[k], device="cuda", dtype=torch.float64) for k in ("x", "y", "z")]
+    gs = [torch.empty(n, device="cuda", dtype=torch.float64) for _ in range(3)]
+
+    def plain(gamma, lam):
+        with P.Place3D(dict(p, gamma=gamma, lam=lam), precision="fp64") as hp:
+            hp.set_positions(*xyz)
+            g = [np.zeros(n) for _ in range(3)]
+            return hp.eval(*g), g
+
+    with P.Place3D(p, precision="fp64") as h:
+        h.eval_graph(*xyz, *gs)
+        c0 = h.graph_captures()
+        for lam in (3 * p["lam"], 10 * p["lam"]):
+            h.set_params(gamma=p["gamma"], gamma_z=0.0, alpha=h.alpha, lam=lam)
+            h.eval_graph(*xyz, *gs)
+            r, g = h.get_result(), [t.cpu().numpy() for t in gs]
+            assert h.graph_captures() == c0
+            rp, gp = plain(p["gamma"], lam)
+            assert r["obj"] == pytest.approx(rp["obj"], rel=1e-12)
+            for a, b in zip(g, gp):
+                assert rel_max(a, b) < 1e-12
+        h.set_params(gamma=2 * p["gamma"], gamma_z=0.0, alpha=h.alpha, lam=lam)
+        h.eval_graph(*xyz, *gs)
+        assert h.graph_captures() == c0 + 1
+        rp, _ = plain(2 * p["gamma"], lam)
+        assert h.get_result()["obj"] == pytest.approx(rp["obj"], rel=1e-12)
