@@ -392,9 +392,36 @@ template <> __device__ __forceinline__ float g_scale_t<float>(const double *scal
   return sz > 0.0f ? ((float)scal[S_SX] + (float)scal[S_SY]) / (2.0f * sz) : 0.0f;
 }
 
+// Final gradient of instance i from its WL accumulators a and its density
+// force (dgx, dgy, dgz): x, y = WL + lambda force; z = g FD + alpha dp(z)/dz
+// + lambda force (0 for z-fixed instances and in 2D mode).
+template <typename T, typename TO>
+__device__ __forceinline__ void final_out(int i, uint8_t f, T z, const V4<T> &a, T dgx, T dgy, T dgz, T g,
+                                          const T *lam4, const FinalC<T> &fc, T zmid, TO *__restrict__ gx,
+                                          TO *__restrict__ gy, TO *__restrict__ gz) {
+  T lam = lam4[0];
+  if (fc.mode2d) lam = lam4[1 + ((f & 4) ? 2 : (z > zmid ? 1 : 0))];
+  T ozg = g * a.z + fc.alpha * a.w + lam * dgz;
+  if ((f & 2) || fc.mode2d) ozg = T(0);
+  gx[i] = (TO)(a.x + lam * dgx);
+  gy[i] = (TO)(a.y + lam * dgy);
+  gz[i] = (TO)ozg;
+}
+
+// Density force of macro slot m from the macro gather's FP64 sums.
+template <typename T>
+__device__ __forceinline__ void macro_force(const double *__restrict__ mgrad, int m, T volb, T &dgx, T &dgy,
+                                            T &dgz) {
+  dgx = (T)(-(double)volb * mgrad[m * 3 + 0]);
+  dgy = (T)(-(double)volb * mgrad[m * 3 + 1]);
+  dgz = (T)(-(double)volb * mgrad[m * 3 + 2]);
+}
+
 // ---- a10 + a9 + a11 per instance: cell field gather fused with the WL add ----
 // g = acc_wl + lambda * (-omega sum_b vol(D cap b) E_b); gz uses the
-// normalised FD gradient.  Macros take their density part from mgrad.
+// normalised FD gradient.  Macros take their density part from mgrad, or,
+// with skip_macros, are left to k_final_macro_out (so that the cells need
+// not wait for the macro gather).
 template <typename T, typename TO>
 __global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ pos,
                                                const V4<T> *__restrict__ size,
@@ -404,7 +431,7 @@ __global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ 
                                                const double *__restrict__ mgrad,
                                                const V4<T> *__restrict__ acc, FinalC<T> fc,
                                                TO *__restrict__ gx, TO *__restrict__ gy,
-                                               TO *__restrict__ gz) {
+                                               TO *__restrict__ gz, int skip_macros) {
   __shared__ T g_sh, lam_sh[4];
   if (threadIdx.x == 0) g_sh = g_scale_t<T>(fc.scal);  // once per block
   if (threadIdx.x < 4) lam_sh[threadIdx.x] = fc.lam_dev[threadIdx.x];
@@ -416,10 +443,8 @@ __global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ 
   const V4<T> p = pos[i];
   T dgx = 0, dgy = 0, dgz = 0;
   if (f & 1) {
-    const int m = macro_slot[i];
-    dgx = (T)(-(double)fc.volb * mgrad[m * 3 + 0]);
-    dgy = (T)(-(double)fc.volb * mgrad[m * 3 + 1]);
-    dgz = (T)(-(double)fc.volb * mgrad[m * 3 + 2]);
+    if (skip_macros) return;
+    macro_force(mgrad, macro_slot[i], fc.volb, dgx, dgy, dgz);
   } else {
     const Box<T> b = inst_box(c, p.x, p.y, p.z, size[i], false, (f & 4) != 0);
     T cl[3], chh[3];
@@ -448,15 +473,24 @@ __global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ 
       dgz = k * sz;
     }
   }
-  const V4<T> a = acc[i];
-  const T g = fc.g;
-  T lam = lam_sh[0];
-  if (fc.mode2d) lam = lam_sh[1 + ((f & 4) ? 2 : (p.z > c.zmid ? 1 : 0))];
-  T ozg = g * a.z + fc.alpha * a.w + lam * dgz;
-  if ((f & 2) || fc.mode2d) ozg = T(0);
-  gx[i] = (TO)(a.x + lam * dgx);
-  gy[i] = (TO)(a.y + lam * dgy);
-  gz[i] = (TO)ozg;
+  final_out(i, f, p.z, acc[i], dgx, dgy, dgz, fc.g, lam_sh, fc, c.zmid, gx, gy, gz);
+}
+
+// The macros' final gradients (the part k_final skips with skip_macros).
+template <typename T, typename TO>
+__global__ void k_final_macro_out(int nm, const int *__restrict__ macro_ids, const V4<T> *__restrict__ pos,
+                                  const uint8_t *__restrict__ flags, const double *__restrict__ mgrad,
+                                  const V4<T> *__restrict__ acc, FinalC<T> fc, T zmid, TO *__restrict__ gx,
+                                  TO *__restrict__ gy, TO *__restrict__ gz) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nm) return;
+  const int i = macro_ids[m];
+  T lam4[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) lam4[k] = fc.lam_dev[k];
+  T dgx, dgy, dgz;
+  macro_force(mgrad, m, fc.volb, dgx, dgy, dgz);
+  final_out(i, flags[i], pos[i].z, acc[i], dgx, dgy, dgz, g_scale_t<T>(fc.scal), lam4, fc, zmid, gx, gy, gz);
 }
 
 // ======================= tile-bucketed scatter and gather =======================

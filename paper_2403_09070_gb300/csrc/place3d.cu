@@ -77,6 +77,11 @@ struct place3d_handle {
   // set_layer_weights; ev_param marks the last such write
   void *d_lam = nullptr;
   cudaEvent_t ev_param = nullptr;
+  // the macros' path (corner map + scans before densify, field gather after
+  // the transforms) on its own stream, overlapped with the cells' scatter and
+  // gather
+  cudaStream_t mac = nullptr;
+  cudaEvent_t ev_mac = nullptr, ev_field = nullptr, ev_mgrad = nullptr;
   // Nesterov loop helpers: pins per instance (eq. improved-precond), the
   // loop state and its per-warp partial rows
   float *npins = nullptr;
@@ -491,6 +496,10 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
   P3D_CUDA(h, cudaMemsetAsync(h->scal, 0, sizeof(double) * S_COUNT, caller));  // before the fork: both paths add
   P3D_CUDA(h, cudaEventRecord(h->ev_fork, caller));
   if (s != caller) P3D_CUDA(h, cudaStreamWaitEvent(s, h->ev_fork, 0));
+  // macros on their own stream (direct field gather, untiled scatter)
+  const bool split = !serial && h->nm > 0 && h->macro_direct && !h->tiles;
+  cudaStream_t ms = split ? h->mac : s;
+  if (split) P3D_CUDA(h, cudaStreamWaitEvent(ms, h->ev_fork, 0));
   // ---------------- wirelength path (side stream) ----------------
   P3D_CUDA(h, cudaStreamWaitEvent(w, h->ev_fork, 0));
   {
@@ -536,9 +545,9 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
       count_launch(h, ST_SCATTER);
     }
     if (h->nm > 0) {
-      P3D_CUDA(h, cudaMemsetAsync(h->corner, 0, sizeof(long long) * h->nb, s));
-      k_macro_corners<T><<<grid_for(h->nm * 8, 128), 128, 0, s>>>(h->nm, h->macro_ids, as<V4<T>>(h->pos),
-                                                                  as<V4<T>>(h->size), dc, h->corner);
+      P3D_CUDA(h, cudaMemsetAsync(h->corner, 0, sizeof(long long) * h->nb, ms));
+      k_macro_corners<T><<<grid_for(h->nm * 8, 128), 128, 0, ms>>>(h->nm, h->macro_ids, as<V4<T>>(h->pos),
+                                                                   as<V4<T>>(h->size), dc, h->corner);
       count_launch(h, ST_SCATTER);
     }
   }
@@ -546,11 +555,15 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     StageScope sc(h, ST_PREFIX, s);
     const int rows = h->ny * h->nz;
     if (h->nm > 0) {
-      k_scan_rows<long long, long long, false><<<grid_for(rows, 8), 256, 0, s>>>(rows, h->nx, h->corner, 1,
-                                                                                h->corner);
+      k_scan_rows<long long, long long, false><<<grid_for(rows, 8), 256, 0, ms>>>(rows, h->nx, h->corner, 1,
+                                                                                 h->corner);
       count_launch(h, ST_PREFIX);
-      k_scan_cols<long long, false><<<dim3(grid_for(h->nx, 32), h->nz), 1024, 0, s>>>(h->nx, h->ny, h->corner);
+      k_scan_cols<long long, false><<<dim3(grid_for(h->nx, 32), h->nz), 1024, 0, ms>>>(h->nx, h->ny, h->corner);
       count_launch(h, ST_PREFIX);
+      if (split) {
+        P3D_CUDA(h, cudaEventRecord(h->ev_mac, ms));
+        P3D_CUDA(h, cudaStreamWaitEvent(s, h->ev_mac, 0));
+      }
     }
     if (h->tc) {
       p3d_tc::densify(h->tc, s, h->nx * h->ny, h->nz, h->q, h->nm > 0 ? h->corner : nullptr, as<float>(h->part_d));
@@ -572,11 +585,16 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
   else
     run_transforms<T>(h, s);
   if (h->nm > 0 && h->macro_direct) {
-    StageScope sc(h, ST_MACRO_GATHER, s);
-    P3D_CUDA(h, cudaMemsetAsync(h->mgrad, 0, sizeof(double) * 3 * h->nm, s));
-    k_macro_gather_direct<T><<<dim3(h->nm, 16), 256, 0, s>>>(h->macro_ids, as<V4<T>>(h->pos), as<V4<T>>(h->size),
-                                                            dc, as<V4<T>>(h->e4), h->mgrad);
+    if (split) {
+      P3D_CUDA(h, cudaEventRecord(h->ev_field, s));
+      P3D_CUDA(h, cudaStreamWaitEvent(ms, h->ev_field, 0));
+    }
+    StageScope sc(h, ST_MACRO_GATHER, ms);
+    P3D_CUDA(h, cudaMemsetAsync(h->mgrad, 0, sizeof(double) * 3 * h->nm, ms));
+    k_macro_gather_direct<T><<<dim3(h->nm, 16), 256, 0, ms>>>(h->macro_ids, as<V4<T>>(h->pos), as<V4<T>>(h->size),
+                                                             dc, as<V4<T>>(h->e4), h->mgrad);
     count_launch(h, ST_MACRO_GATHER);
+    if (split) P3D_CUDA(h, cudaEventRecord(h->ev_mgrad, ms));
   } else if (h->nm > 0) {
     StageScope sc(h, ST_MACRO_GATHER, s);
     const int rows = h->ny * h->nz;
@@ -618,13 +636,25 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
         k_final<T, double><<<grid_for(n, 256), 256, 0, s>>>(n, as<V4<T>>(h->pos), as<V4<T>>(h->size), h->flags_d,
                                                             h->macro_slot, dc, as<V4<T>>(h->e4),
                                                             h->mgrad, as<V4<T>>(h->acc), fc, (double *)ox, (double *)oy,
-                                                            (double *)oz);
+                                                            (double *)oz, split ? 1 : 0);
       else
         k_final<T, float><<<grid_for(n, 256), 256, 0, s>>>(n, as<V4<T>>(h->pos), as<V4<T>>(h->size), h->flags_d,
                                                            h->macro_slot, dc, as<V4<T>>(h->e4),
                                                            h->mgrad, as<V4<T>>(h->acc), fc, (float *)ox, (float *)oy,
-                                                           (float *)oz);
+                                                           (float *)oz, split ? 1 : 0);
       count_launch(h, ST_FINAL);
+      if (split) {  // the macros, once their field gather is done
+        P3D_CUDA(h, cudaStreamWaitEvent(s, h->ev_mgrad, 0));
+        if (odt == PLACE3D_F64)
+          k_final_macro_out<T, double><<<grid_for(h->nm, 128), 128, 0, s>>>(
+              h->nm, h->macro_ids, as<V4<T>>(h->pos), h->flags_d, h->mgrad, as<V4<T>>(h->acc), fc, dc.zmid,
+              (double *)ox, (double *)oy, (double *)oz);
+        else
+          k_final_macro_out<T, float><<<grid_for(h->nm, 128), 128, 0, s>>>(
+              h->nm, h->macro_ids, as<V4<T>>(h->pos), h->flags_d, h->mgrad, as<V4<T>>(h->acc), fc, dc.zmid,
+              (float *)ox, (float *)oy, (float *)oz);
+        count_launch(h, ST_FINAL);
+      }
     }
     if (!direct && gx && gy && gz && n > 0) {
       // host outputs (or device outputs of another dtype): copy / convert
@@ -691,6 +721,10 @@ void free_all(place3d_handle *h) {
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_dens) cudaEventDestroy(h->ev_dens);
   if (h->ev_param) cudaEventDestroy(h->ev_param);
+  if (h->ev_mac) cudaEventDestroy(h->ev_mac);
+  if (h->ev_field) cudaEventDestroy(h->ev_field);
+  if (h->ev_mgrad) cudaEventDestroy(h->ev_mgrad);
+  if (h->mac) cudaStreamDestroy(h->mac);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->dens) cudaStreamDestroy(h->dens);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
@@ -1025,7 +1059,11 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_dens, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_param, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_param, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&h->mac, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_mac, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_field, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_mgrad, cudaEventDisableTiming) != cudaSuccess) {
     fail(h, PLACE3D_ERR_CUDA, "stream/event creation failed");
     return bail(PLACE3D_ERR_CUDA);
   }
