@@ -81,7 +81,7 @@ struct place3d_handle {
   // the transforms) on its own stream, overlapped with the cells' scatter and
   // gather
   cudaStream_t mac = nullptr;
-  cudaEvent_t ev_mac = nullptr, ev_field = nullptr, ev_mgrad = nullptr;
+  cudaEvent_t ev_mac = nullptr, ev_field = nullptr, ev_mgrad = nullptr, ev_z = nullptr;
   // Nesterov loop helpers: pins per instance (eq. improved-precond), the
   // loop state and its per-warp partial rows
   float *npins = nullptr;
@@ -399,8 +399,15 @@ int sum_grid(int rows) { return std::max(1, std::min(kSumBlocks, grid_for(rows, 
 
 // Add the z stage's per-warp energy rows (blocks of 256 threads) into the
 // scalars (one per layer in 2D mode).
-template <typename T> void sum_energy(place3d_handle *h, cudaStream_t s, int blocks) {
+// rs: the stream for the reduction (it only feeds the scalars, so it can run
+// beside the inverse products); rs == s keeps it in line.
+template <typename T> void sum_energy(place3d_handle *h, cudaStream_t s, cudaStream_t rs, int blocks) {
   const int rows = blocks * 8;
+  if (rs != s) {
+    cudaEventRecord(h->ev_z, s);
+    cudaStreamWaitEvent(rs, h->ev_z, 0);
+    s = rs;
+  }
   if (h->mode2d)
     k_sum_parts<3, T><<<sum_grid(rows), 256, 0, s>>>(as<T>(h->part_d), rows, h->scal + S_EL0);
   else
@@ -409,7 +416,7 @@ template <typename T> void sum_energy(place3d_handle *h, cudaStream_t s, int blo
 }
 
 // The spectral solve: rho -> E_x, E_y, E_z (and the energy sum).
-template <typename T> void run_transforms(place3d_handle *h, cudaStream_t s) {
+template <typename T> void run_transforms(place3d_handle *h, cudaStream_t s, cudaStream_t rs) {
   const int nx = h->nx, ny = h->ny, nz = h->nz;
   const long long pl = (long long)nx * ny;
   const T *M = as<T>(h->mats);
@@ -435,7 +442,7 @@ template <typename T> void run_transforms(place3d_handle *h, cudaStream_t s) {
     else
       k_zstage<T, 16><<<g, 256, 0, s>>>(h->zc, t2, cz, sz, es);
     count_launch(h, ST_ZSTAGE);
-    sum_energy<T>(h, s, g);
+    sum_energy<T>(h, s, rs, g);
   }
   {
     StageScope sc(h, ST_INV, s);
@@ -452,7 +459,7 @@ template <typename T> void run_transforms(place3d_handle *h, cudaStream_t s) {
 }
 
 // The same solve on the tensor cores (split-BF16 tcgen05 products).
-void run_transforms_tc(place3d_handle *h, cudaStream_t s) {
+void run_transforms_tc(place3d_handle *h, cudaStream_t s, cudaStream_t rs) {
   {
     StageScope sc(h, ST_FWD, s);
     const int k = p3d_tc::forward(h->tc, s);
@@ -462,7 +469,7 @@ void run_transforms_tc(place3d_handle *h, cudaStream_t s) {
     StageScope sc(h, ST_ZSTAGE, s);
     const int k = p3d_tc::zstage(h->tc, s, as<float>(h->part_d));
     for (int i = 0; i < k; ++i) count_launch(h, ST_ZSTAGE);
-    sum_energy<float>(h, s, (int)(((long long)h->nx * h->ny + 255) / 256));
+    sum_energy<float>(h, s, rs, (int)(((long long)h->nx * h->ny + 255) / 256));
   }
   {
     StageScope sc(h, ST_INV, s);
@@ -497,9 +504,13 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
   P3D_CUDA(h, cudaEventRecord(h->ev_fork, caller));
   if (s != caller) P3D_CUDA(h, cudaStreamWaitEvent(s, h->ev_fork, 0));
   // macros on their own stream (direct field gather, untiled scatter)
+  // third stream (not in serial mode): the macros' path when their field
+  // gather is direct and the scatter untiled, and the scalar reductions that
+  // nothing on the density chain waits for
   const bool split = !serial && h->nm > 0 && h->macro_direct && !h->tiles;
-  cudaStream_t ms = split ? h->mac : s;
-  if (split) P3D_CUDA(h, cudaStreamWaitEvent(ms, h->ev_fork, 0));
+  cudaStream_t ms = serial ? s : h->mac;
+  if (ms != s) P3D_CUDA(h, cudaStreamWaitEvent(ms, h->ev_fork, 0));
+  cudaStream_t mcs = split ? ms : s;  // stream of the macros' kernels
   // ---------------- wirelength path (side stream) ----------------
   P3D_CUDA(h, cudaStreamWaitEvent(w, h->ev_fork, 0));
   {
@@ -545,9 +556,9 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
       count_launch(h, ST_SCATTER);
     }
     if (h->nm > 0) {
-      P3D_CUDA(h, cudaMemsetAsync(h->corner, 0, sizeof(long long) * h->nb, ms));
-      k_macro_corners<T><<<grid_for(h->nm * 8, 128), 128, 0, ms>>>(h->nm, h->macro_ids, as<V4<T>>(h->pos),
-                                                                   as<V4<T>>(h->size), dc, h->corner);
+      P3D_CUDA(h, cudaMemsetAsync(h->corner, 0, sizeof(long long) * h->nb, mcs));
+      k_macro_corners<T><<<grid_for(h->nm * 8, 128), 128, 0, mcs>>>(h->nm, h->macro_ids, as<V4<T>>(h->pos),
+                                                                    as<V4<T>>(h->size), dc, h->corner);
       count_launch(h, ST_SCATTER);
     }
   }
@@ -555,13 +566,13 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     StageScope sc(h, ST_PREFIX, s);
     const int rows = h->ny * h->nz;
     if (h->nm > 0) {
-      k_scan_rows<long long, long long, false><<<grid_for(rows, 8), 256, 0, ms>>>(rows, h->nx, h->corner, 1,
-                                                                                 h->corner);
+      k_scan_rows<long long, long long, false><<<grid_for(rows, 8), 256, 0, mcs>>>(rows, h->nx, h->corner, 1,
+                                                                                  h->corner);
       count_launch(h, ST_PREFIX);
-      k_scan_cols<long long, false><<<dim3(grid_for(h->nx, 32), h->nz), 1024, 0, ms>>>(h->nx, h->ny, h->corner);
+      k_scan_cols<long long, false><<<dim3(grid_for(h->nx, 32), h->nz), 1024, 0, mcs>>>(h->nx, h->ny, h->corner);
       count_launch(h, ST_PREFIX);
       if (split) {
-        P3D_CUDA(h, cudaEventRecord(h->ev_mac, ms));
+        P3D_CUDA(h, cudaEventRecord(h->ev_mac, mcs));
         P3D_CUDA(h, cudaStreamWaitEvent(s, h->ev_mac, 0));
       }
     }
@@ -574,27 +585,30 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     count_launch(h, ST_PREFIX);
     // density overflow (sum of max(rho - 1, 0) and of rho) from densify's per-warp rows
     const int orow = grid_for((long long)h->nx * h->ny, 256) * 8;
+    if (ms != s) {  // nothing on the density chain waits for it
+      P3D_CUDA(h, cudaEventRecord(h->ev_z, s));
+      P3D_CUDA(h, cudaStreamWaitEvent(ms, h->ev_z, 0));
+    }
     if (h->tc)
-      k_sum_parts<2, float><<<sum_grid(orow), 256, 0, s>>>(as<float>(h->part_d), orow, h->scal + S_OVFL);
+      k_sum_parts<2, float><<<sum_grid(orow), 256, 0, ms>>>(as<float>(h->part_d), orow, h->scal + S_OVFL);
     else
-      k_sum_parts<2, T><<<sum_grid(orow), 256, 0, s>>>(as<T>(h->part_d), orow, h->scal + S_OVFL);
+      k_sum_parts<2, T><<<sum_grid(orow), 256, 0, ms>>>(as<T>(h->part_d), orow, h->scal + S_OVFL);
     count_launch(h, ST_PREFIX);
   }
   if (h->tc)
-    run_transforms_tc(h, s);
+    run_transforms_tc(h, s, ms);
   else
-    run_transforms<T>(h, s);
+    run_transforms<T>(h, s, ms);
   if (h->nm > 0 && h->macro_direct) {
     if (split) {
       P3D_CUDA(h, cudaEventRecord(h->ev_field, s));
-      P3D_CUDA(h, cudaStreamWaitEvent(ms, h->ev_field, 0));
+      P3D_CUDA(h, cudaStreamWaitEvent(mcs, h->ev_field, 0));
     }
-    StageScope sc(h, ST_MACRO_GATHER, ms);
-    P3D_CUDA(h, cudaMemsetAsync(h->mgrad, 0, sizeof(double) * 3 * h->nm, ms));
-    k_macro_gather_direct<T><<<dim3(h->nm, 16), 256, 0, ms>>>(h->macro_ids, as<V4<T>>(h->pos), as<V4<T>>(h->size),
-                                                             dc, as<V4<T>>(h->e4), h->mgrad);
+    StageScope sc(h, ST_MACRO_GATHER, mcs);
+    P3D_CUDA(h, cudaMemsetAsync(h->mgrad, 0, sizeof(double) * 3 * h->nm, mcs));
+    k_macro_gather_direct<T><<<dim3(h->nm, 16), 256, 0, mcs>>>(h->macro_ids, as<V4<T>>(h->pos), as<V4<T>>(h->size),
+                                                              dc, as<V4<T>>(h->e4), h->mgrad);
     count_launch(h, ST_MACRO_GATHER);
-    if (split) P3D_CUDA(h, cudaEventRecord(h->ev_mgrad, ms));
   } else if (h->nm > 0) {
     StageScope sc(h, ST_MACRO_GATHER, s);
     const int rows = h->ny * h->nz;
@@ -644,6 +658,7 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
                                                            (float *)oz, split ? 1 : 0);
       count_launch(h, ST_FINAL);
       if (split) {  // the macros, once their field gather is done
+        P3D_CUDA(h, cudaEventRecord(h->ev_mgrad, ms));
         P3D_CUDA(h, cudaStreamWaitEvent(s, h->ev_mgrad, 0));
         if (odt == PLACE3D_F64)
           k_final_macro_out<T, double><<<grid_for(h->nm, 128), 128, 0, s>>>(
@@ -666,6 +681,10 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
       P3D_CUDA(h, cudaMemcpyAsync(gy, oy, (size_t)n * tb, k, s));
       P3D_CUDA(h, cudaMemcpyAsync(gz, oz, (size_t)n * tb, k, s));
     }
+  }
+  if (ms != s) {  // the third stream's reductions
+    P3D_CUDA(h, cudaEventRecord(h->ev_mgrad, ms));
+    P3D_CUDA(h, cudaStreamWaitEvent(caller, h->ev_mgrad, 0));
   }
   if (s != caller) {
     P3D_CUDA(h, cudaEventRecord(h->ev_dens, s));
@@ -724,6 +743,7 @@ void free_all(place3d_handle *h) {
   if (h->ev_mac) cudaEventDestroy(h->ev_mac);
   if (h->ev_field) cudaEventDestroy(h->ev_field);
   if (h->ev_mgrad) cudaEventDestroy(h->ev_mgrad);
+  if (h->ev_z) cudaEventDestroy(h->ev_z);
   if (h->mac) cudaStreamDestroy(h->mac);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->dens) cudaStreamDestroy(h->dens);
@@ -1063,7 +1083,8 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
       cudaStreamCreateWithPriority(&h->mac, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_mac, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_field, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_mgrad, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_mgrad, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_z, cudaEventDisableTiming) != cudaSuccess) {
     fail(h, PLACE3D_ERR_CUDA, "stream/event creation failed");
     return bail(PLACE3D_ERR_CUDA);
   }
