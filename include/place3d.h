@@ -396,8 +396,10 @@ void place3d_debug_fail_alloc(int nth);
  *   place3d_nesterov_precondition(g);
  *
  * place3d_nesterov_precondition: takes the gradient G of the last
- * evaluation, which must have been place3d_eval_objective_and_grad without
- * device gradient arrays (INVALID_ARG otherwise), and forms g_new = G / H
+ * evaluation, which must have been place3d_eval_objective_and_grad (that
+ * keeps the gradient in the handle unless profiling is on or the gradient
+ * arrays are device arrays of the other precision; INVALID_ARG after those,
+ * after place3d_eval_graph or a batch), and forms g_new = G / H
  * with H_i = max(1, |E_i| + lambda q_i) for macros (|E_i| = the instance's
  * pin count) and max(1, lambda q_i) otherwise, q_i = w_i h_i d_z/2 with the
  * die sizes at the evaluated z; the z component is 0 for z-fixed instances.

@@ -1694,7 +1694,7 @@ static int nest_check(place3d_handle *h, const void *const *ptrs, int count, boo
     if (!ptrs[k] && h->n > 0) return fail(h, PLACE3D_ERR_INVALID_ARG, "NULL device array");
   if (need_grad && !h->gout_fresh)
     return fail(h, PLACE3D_ERR_INVALID_ARG,
-                "the last evaluation must be place3d_eval_objective_and_grad without device gradient arrays");
+                "the last evaluation did not keep its gradient in the handle (see place3d_nesterov_precondition)");
   P3D_CUDA(h, cudaSetDevice(h->device));
   return PLACE3D_OK;
 }

@@ -125,3 +125,41 @@ def test_fused_nesterov_follows_the_torch_loop():
             out.append(u.cpu().numpy())
             pl.obj.handle.close()
         assert np.abs(out[0] - out[1]).max() < 1e-9 * span, iters
+
+
+def test_nesterov_helpers_reject_misuse():
+    """The device Nesterov helpers need a 3D handle, the handle's precision
+    on CUDA tensors, and a last evaluation whose gradient the handle kept
+    (not eval_graph, not device gradient arrays of the other precision)."""
+    from paper_2403_09070_gb300 import place3d as P
+    p = synth.make_problem("cells_2k")
+    n = p["n_inst"]
+    xyz = [torch.tensor(p[k], device="cuda", dtype=torch.float32) for k in ("x", "y", "z")]
+    g = torch.zeros((3, n), device="cuda", dtype=torch.float32)
+    with P.Place3D(p, precision="fp32") as h:
+        h.set_positions(*xyz)
+        with pytest.raises(P.Place3DError):  # no evaluation yet
+            h.nesterov_init(g, 1.0)
+        # device gradient arrays of the other precision: written directly, not kept
+        h.eval(*[torch.empty(n, device="cuda", dtype=torch.float64) for _ in range(3)])
+        with pytest.raises(P.Place3DError):
+            h.nesterov_precondition(g)
+        h.eval(*[torch.empty(n, device="cuda") for _ in range(3)])  # kept in the handle, then copied
+        h.nesterov_precondition(g)
+        h.eval(sync=False)  # gradient kept in the handle
+        with pytest.raises(ValueError):
+            h.nesterov_init(g.double(), 1.0)  # wrong precision
+        with pytest.raises(P.Place3DError):
+            h.nesterov_init(g, 0.0)  # init_step must be > 0
+        h.nesterov_init(g, 1.0)
+        assert h.nesterov_step() > 0
+        gs = [torch.empty(n, device="cuda") for _ in range(3)]
+        h.eval_graph(*xyz, *gs)
+        with pytest.raises(P.Place3DError):
+            h.nesterov_precondition(g)
+    q = synth.to_problem2d(p, seed=3)
+    with P.Place3D(q, precision="fp32") as h2:
+        h2.set_positions(*(torch.tensor(q[k], device="cuda", dtype=torch.float32) for k in ("x", "y", "z")))
+        h2.eval(sync=False)
+        with pytest.raises(P.Place3DError):
+            h2.nesterov_init(torch.zeros((3, q["n_inst"]), device="cuda"), 1.0)
