@@ -85,6 +85,15 @@ __device__ __forceinline__ bool clip_axis(T lo, T hi, T fN, int n, T &cl, T &chh
   return true;
 }
 
+// The same with the bin's lower edge e given as T (an integer, so e + 1 is
+// exact): the loops step e in T instead of converting every bin index (an
+// int -> float conversion runs on the narrow conversion pipe).
+template <typename T>
+__device__ __forceinline__ T ov_edge(T cl, T chh, T e) {
+  const T hi = e + T(1);
+  return rn_sub(chh < hi ? chh : hi, cl > e ? cl : e);
+}
+
 template <typename T>
 __device__ __forceinline__ T ov_axis(T cl, T chh, int b) {
   const T lo = (T)b, hi = (T)(b + 1);
@@ -117,13 +126,17 @@ __global__ void __launch_bounds__(256) k_scatter_cells(int n, const V4<T> *__res
   if (!clip_axis(b.lo[1], b.hi[1], c.fny, c.ny, cl[1], chh[1], b0[1], b1[1])) return;
   if (!clip_axis(b.lo[2], b.hi[2], c.fnz, c.nz, cl[2], chh[2], b0[2], b1[2])) return;
   const T scale = (T)kFixedScale;
-  for (int k = b0[2]; k <= b1[2]; ++k) {
-    const T oz = ov_axis(cl[2], chh[2], k);
-    for (int j = b0[1]; j <= b1[1]; ++j) {
-      const T oy = ov_axis(cl[1], chh[1], j);
+  const T ey0 = (T)b0[1], ex0 = (T)(b0[0] + h);
+  T ez = (T)b0[2];
+  for (int k = b0[2]; k <= b1[2]; ++k, ez += T(1)) {
+    const T oz = ov_edge(cl[2], chh[2], ez);
+    T ey = ey0;
+    for (int j = b0[1]; j <= b1[1]; ++j, ey += T(1)) {
+      const T oy = ov_edge(cl[1], chh[1], ey);
       long long *row = q + ((size_t)k * c.ny + j) * c.nx;
-      for (int ii = b0[0] + h; ii <= b1[0]; ii += 2) {
-        const T ox = ov_axis(cl[0], chh[0], ii);
+      T ex = ex0;
+      for (int ii = b0[0] + h; ii <= b1[0]; ii += 2, ex += T(2)) {
+        const T ox = ov_edge(cl[0], chh[0], ex);
         const T v = rn_mul(rn_mul(rn_mul(b.om, ox), oy), oz);
         atomic_add_i64(row + ii, r_rint(rn_mul(v, scale)));
       }
