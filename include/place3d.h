@@ -261,7 +261,8 @@ int place3d_result_to_device(place3d_handle *h, double *dst);
  * lambda lives in device memory and is rewritten on the handle's stream
  * (ordered before every later evaluation on that stream; batch launches
  * wait for it), so changing lambda alone leaves captured CUDA graphs as
- * they are and does not synchronise.  gamma, gamma_z and alpha are kernel
+ * they are and does not synchronise.  A batch launched earlier on another
+ * stream must have finished first (the write is not ordered after it).  gamma, gamma_z and alpha are kernel
  * arguments: a change makes the next graph launch re-capture (and update
  * the executable graph in place).
  * Errors: INVALID_ARG (gamma <= 0 or a non-finite value), CUDA. */
