@@ -4,7 +4,7 @@ an FP64 product, and the PLACE3D_FP32_TC evaluation against the oracle
 import numpy as np
 import pytest
 
-from gpu_harness import rel_l2, run_gpu, run_oracle
+from gpu_harness import rel_l2, rel_max, run_gpu, run_oracle
 from helpers import dz_of, problem
 from paper_2403_09070_gb300 import place3d as P
 from paper_2403_09070_gb300 import synth
@@ -75,13 +75,48 @@ def test_fp32_tc_rejects_unaligned_grid():
     assert ei.value.code == -7
 
 
+def _precision_study(name, p, x, y, z, alpha, ref):
+    """Errors of the FP64 and FP32 paths (and of the FP32_TC result passed in
+    by the caller) against the FP64 oracle's evaluation `ref` at the same
+    positions: relative errors of the scalars, relative L2 and max-norm
+    errors of the gradient.  Printed as one JSON line (pytest -s)."""
+    import json
+    out = {}
+    for m in ("fp64", "fp32"):
+        g = run_gpu(p, x, y, z, m, alpha=alpha, maps=False)
+        e = {k: abs(g["res"][k] - ref[k]) / max(abs(ref[k]), 1e-300)
+             for k in ("obj", "wl_bi", "wl_z", "energy", "hpwl_d2d")}
+        e["n_cross_equal"] = g["res"]["n_cross"] == ref["n_cross"]
+        for k in ("gx", "gy", "gz"):
+            e[k + "_rel_l2"] = rel_l2(g[k], ref[k])
+            e[k + "_rel_max"] = rel_max(g[k], ref[k])
+        out[m] = e
+    print("PRECISION", json.dumps({"workload": name, "reference": "FP64 oracle, direct density definition",
+                                   "modes": out}))
+    return out
+
+
+def _tc_errors(g, ref):
+    e = {k: abs(g["res"][k] - ref[k]) / max(abs(ref[k]), 1e-300) for k in ("obj", "wl_bi", "wl_z", "energy", "hpwl_d2d")}
+    for k in ("gx", "gy", "gz"):
+        e[k + "_rel_l2"] = rel_l2(g[k], ref[k])
+        e[k + "_rel_max"] = rel_max(g[k], ref[k])
+    return e
+
+
 def test_fp32_tc_full_size_bench_configuration():
     """The bench's workload and launch configuration (1M cells, 512x512x4,
-    FP32_TC, autotuned reduction forms) against the full FP64 oracle."""
+    FP32_TC, autotuned reduction forms) against the full FP64 oracle; with the
+    FP64 and FP32 paths at the same positions for the precision study."""
+    import json
     p = synth.make_problem("cells_1m")
     x32, y32, z32 = (np.asarray(p[k], np.float32).astype(np.float64) for k in ("x", "y", "z"))
     g = run_gpu(p, x32, y32, z32, "fp32_tc", autotune=True)
     o, r = run_oracle(p, x32, y32, z32, g["alpha"], density_mode=0)
+    print("PRECISION", json.dumps({"workload": "cells_1m", "modes": {"fp32_tc": _tc_errors(g, r)}}))
+    study = _precision_study("cells_1m", p, x32, y32, z32, g["alpha"], r)
+    assert study["fp64"]["obj"] < 1e-8 and study["fp64"]["gx_rel_l2"] < 1e-8
+    assert study["fp32"]["obj"] < 2e-5 and study["fp32"]["gx_rel_l2"] < 1e-4
     assert np.array_equal(g["q"], o.density_fixed(x32, y32, z32, use_float=True))
     assert g["res"]["obj"] == pytest.approx(r["obj"], rel=2e-5)
     assert g["res"]["n_cross"] == r["n_cross"]
@@ -111,6 +146,11 @@ def test_fp32_tc_large_skewed_configuration():
     g = run_gpu(p, x32, y32, z32, "fp32_tc", autotune=True)
     assert any(f[1] == 0 for f in g["forms"])  # the block form ran
     o, r = run_oracle(p, x32, y32, z32, g["alpha"], density_mode=0)
+    import json
+    print("PRECISION", json.dumps({"workload": "cells_4m_skewed", "modes": {"fp32_tc": _tc_errors(g, r)}}))
+    study = _precision_study("cells_4m_skewed", p, x32, y32, z32, g["alpha"], r)
+    assert study["fp64"]["obj"] < 1e-8 and study["fp64"]["gx_rel_l2"] < 1e-8
+    assert study["fp32"]["obj"] < 2e-5 and study["fp32"]["gx_rel_l2"] < 1e-4
     assert np.array_equal(g["q"], o.density_fixed(x32, y32, z32, use_float=True))
     assert g["res"]["obj"] == pytest.approx(r["obj"], rel=2e-5)
     assert g["res"]["n_cross"] == r["n_cross"]
