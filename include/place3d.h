@@ -225,8 +225,10 @@ int place3d_get_result(place3d_handle *h, place3d_result *out);
 /* One evaluation as a CUDA graph: position packing (as set_positions with
  * DEVICE arrays) plus the whole evaluation, writing the gradient to DEVICE
  * arrays gx, gy, gz.  The first call (and any call with other pointers or
- * dtype) captures the graph on a private stream and instantiates it; every
- * call launches it on the handle's stream.  The pointers are baked into the
+ * dtype, or after gamma, gamma_z, alpha or a reduction form changed)
+ * captures the graph on a private stream and instantiates it (or updates
+ * the executable graph in place when its shape is unchanged); every call
+ * launches it on the handle's stream.  The pointers are baked into the
  * graph: the arrays must stay allocated while the handle replays it.
  * Results: place3d_get_result / place3d_result_to_device. */
 int place3d_eval_graph(place3d_handle *h, const void *x, const void *y,
@@ -238,8 +240,10 @@ int place3d_eval_graph(place3d_handle *h, const void *x, const void *y,
  * root, so the instances run concurrently.  handles stay owned by the
  * caller and must outlive the batch; all on one device.  place3d_batch_eval
  * takes per-instance DEVICE pointers (arrays of count pointers, dtype as in
- * place3d_eval_graph), captures on first use or when any pointer changes,
- * and launches on cuda_stream.  Per-instance results via
+ * place3d_eval_graph), captures on first use or when any pointer or any
+ * handle's gamma, gamma_z, alpha or reduction form changes (updating the
+ * executable graph in place when it can), and launches on cuda_stream after
+ * the handles' last parameter writes.  Per-instance results via
  * place3d_get_result.  Errors: INVALID_ARG, CUDA. */
 typedef struct place3d_batch place3d_batch;
 int place3d_batch_create(place3d_handle *const *handles, int count,

@@ -138,8 +138,9 @@ struct place3d_handle {
   cudaGraphExec_t egexec = nullptr;
   const void *egptr[3] = {nullptr, nullptr, nullptr};
   unsigned egversion = 0;
-  // bumped by every change that a captured graph bakes in (gamma, lambda,
-  // alpha, layer weights, reduction forms); graphs recapture when it moved
+  // bumped by every change that a captured graph bakes in (gamma, gamma_z,
+  // alpha, reduction forms; lambda and the layer weights are read from the
+  // device); graphs re-capture when it moved
   unsigned version = 0, gversion = 0;
   long long captures = 0;  // graph captures (eval_graph and the internal evaluation graph)
   cudaStream_t cap_stream = nullptr;

@@ -127,8 +127,8 @@ template <> struct ZPar<float> {
   static __device__ __forceinline__ float sz(const ZStageC *z, int i) { return z->sz_f[i]; }
 };
 
-// All arithmetic in T (FP32 threads stay off the FP64 pipe); the energy sum
-// is widened to FP64 per warp.  2D mode (zc->mode2d, N_z = 3 layers): no z
+// All arithmetic in T (FP32 threads stay off the FP64 pipe); the energy sums
+// leave one row per warp in T for k_sum_parts.  2D mode (zc->mode2d, N_z = 3 layers): no z
 // transform, psi = c_j c_k a / (w_j^2 + w_k^2) per layer with a = (1/(N_x
 // N_y)) T2, E_z = 0 (Szpsi = 0), one energy sum per layer.  The block
 // sums go to part[block][1] (3D) or part[block][3] (2D), added up by

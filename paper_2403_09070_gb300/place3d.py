@@ -286,7 +286,8 @@ class Place3D:
 
     def eval_graph(self, x, y, z, gx, gy, gz):
         """Pack + evaluate as one CUDA-graph launch (CUDA tensors; the graph is
-        re-captured only when a tensor's address or the dtype changes)."""
+        re-captured only when a tensor's address, the dtype, gamma, gamma_z, alpha or a
+        reduction form changes; a new lambda is read from device memory)."""
         b = [_buf(a) for a in (x, y, z, gx, gy, gz)]
         if any(v[2] != MEM_DEVICE for v in b) or len({v[1] for v in b}) != 1:
             raise ValueError("eval_graph takes CUDA tensors of one dtype")
