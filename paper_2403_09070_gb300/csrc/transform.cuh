@@ -130,8 +130,8 @@ template <> struct ZPar<float> {
 // All arithmetic in T (FP32 threads stay off the FP64 pipe); the energy sums
 // leave one row per warp in T for k_sum_parts.  2D mode (zc->mode2d, N_z = 3 layers): no z
 // transform, psi = c_j c_k a / (w_j^2 + w_k^2) per layer with a = (1/(N_x
-// N_y)) T2, E_z = 0 (Szpsi = 0), one energy sum per layer.  The block
-// sums go to part[block][1] (3D) or part[block][3] (2D), added up by
+// N_y)) T2, E_z = 0 (Szpsi = 0), one energy sum per layer.  The warp
+// sums go to part[warp][1] (3D) or part[warp][3] (2D), added up by
 // k_sum_parts into S_ESUM or S_EL0..S_EL2.
 template <typename T, int NZM, typename Out>
 __global__ void __launch_bounds__(256) k_zstage(const ZStageC *__restrict__ zc, const T *__restrict__ in,
