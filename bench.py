@@ -95,13 +95,19 @@ class Clocks:
 
     The sampler polls every 10 ms and is running (first sample seen) before
     start() returns; only samples that arrive between start() and stop()
-    count.  A timed region shorter than the polling period can still see no
-    sample: then the first sample after it is reported, marked "after"."""
+    count.  start() comes right before the timed steps; mark() right after
+    them, and extend_clock_window() then repeats the same step, untimed, until
+    the window is MIN_WINDOW_S long, so the clock record holds several samples
+    of this workload even when the timed steps take a few milliseconds
+    ("samples_in_timed_steps" counts the ones inside the timed steps).  With no
+    sample at all, the first one after the window is reported, marked "after"."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     PERIOD_MS = 10
+    MIN_WINDOW_S = 0.15  # timed steps shorter than this are followed by the same steps, untimed
+
 
     def __init__(self, dev: int):
         self.dev = dev
@@ -127,6 +133,10 @@ class Clocks:
         for line in self.p.stdout:
             self.lines.append((time.time(), line.strip()))
 
+    def mark(self):
+        """End of the timed steps (samples up to here count as "during")."""
+        self.t_mark = time.time()
+
     def stop(self) -> dict:
         self.t1 = time.time()
         if self.p is None:
@@ -140,6 +150,8 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.p.kill()
         self.t.join(timeout=5)
+        t_mark = getattr(self, "t_mark", self.t1)
+        strict = sum(1 for t, _ in self.lines if self.t0 <= t <= t_mark)
         inside = [ln for t, ln in self.lines if self.t0 <= t <= self.t1]
         where = "during"
         if not inside:
@@ -161,7 +173,26 @@ class Clocks:
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm), "sampled": where,
+                "samples_in_timed_steps": strict, "window_ms": round((self.t1 - self.t0) * 1000.0, 1),
                 "period_ms": self.PERIOD_MS}
+
+
+def extend_clock_window(clk: Clocks, fn, torch):
+    """After the timed steps: mark their end, then keep running the same step
+    (untimed) until the sampler's window reaches Clocks.MIN_WINDOW_S, so that a
+    short timed region still yields several clock samples of this workload."""
+    clk.mark()
+    while time.time() - clk.t0 < Clocks.MIN_WINDOW_S:
+        for _ in range(8):
+            fn()
+        torch.cuda.synchronize()
+
+
+def step_stats(per_step_ms) -> dict:
+    """Mean and median of the per-step device times (ms)."""
+    a = np.asarray(per_step_ms, np.float64)
+    return {"mean_ms": float(a.mean()), "median_ms": float(np.median(a)), "min_ms": float(a.min()),
+            "max_ms": float(a.max()), "steps": int(a.size)}
 
 
 # ---------------------------------------------------------------- oracle legs (CPU)
@@ -328,7 +359,9 @@ def run_batch(a):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-        return max_over_ranks(float(sum(e0.elapsed_time(e1) for e0, e1 in ev)), dist if world > 1 else None, "cuda")
+        per = [e0.elapsed_time(e1) for e0, e1 in ev]
+        timed.last = per
+        return max_over_ranks(float(sum(per)), dist if world > 1 else None, "cuda")
 
     for _ in range(a.warmup):
         one_graph()
@@ -337,6 +370,8 @@ def run_batch(a):
     clk = Clocks(local)
     clk.start()
     ms = timed(one_graph, a.steps)
+    per_step = timed.last
+    extend_clock_window(clk, one_graph, torch)
     clocks = clk.stop()
     ms_seq = timed(sequential, a.steps)
     n_total = sum(p["n_inst"] for p in probs)
@@ -367,6 +402,8 @@ def run_batch(a):
         print(json.dumps({
             "metric": METRIC, "value": job_throughput(world, a.steps * len(probs), ms), "unit": UNIT,
             "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+            "step_ms": step_stats(per_step),
+            "median_evals_per_s": len(probs) * 1000.0 / step_stats(per_step)["median_ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 (transforms bf16x3 split on tensor cores where N_x, N_y are multiples of 128)",
             "data": "synthetic",
@@ -465,7 +502,9 @@ def main():
         if profile:
             h.set_profiling(False)
             st = h.stage_times(reset=True)
-        tot = max_over_ranks(float(sum(e0.elapsed_time(e1) for e0, e1 in ev)), dist if world > 1 else None, "cuda")
+        per = [e0.elapsed_time(e1) for e0, e1 in ev]
+        timed.last = per
+        tot = max_over_ranks(float(sum(per)), dist if world > 1 else None, "cuda")
         return tot, st
 
     for _ in range(a.warmup):
@@ -478,6 +517,8 @@ def main():
     clk = Clocks(local)
     clk.start()
     total_ms, st_a = timed(step, a.steps, profile=step is step_launches, tag="timed_main")
+    per_step = timed.last
+    extend_clock_window(clk, step, torch)
     clocks = clk.stop()
     # timed region B: separate launches with per-stage CUDA events (stages and roofline)
     total_b_ms, st = timed(step_launches, a.steps, profile=True, tag="timed_launches")
@@ -586,7 +627,10 @@ def main():
         esz = 8 if precision == "fp64" else 4
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
+            "step_ms": step_stats(per_step),
+            "median_evals_per_s": job_throughput(world, 1, step_stats(per_step)["median_ms"]),
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32_tc": "f32 (transforms bf16x3 split on tensor cores, f64 scalars)",
                       "fp32": "f32 (f64 scalars)", "fp64": "f64"}[precision],
@@ -653,7 +697,7 @@ def _nesterov_rate(prob, precision, torch, iters=30, warmup=5, ref_iters=10):
             **out}
 
 
-def _fp64_plain(prob, torch, P, steps=5, warmup=2):
+def _fp64_plain(prob, torch, P, steps=20, warmup=3):
     """The plain FP64 GPU path on the same workload (context for the fast path)."""
     n = prob["n_inst"]
     h = P.Place3D(prob, precision="fp64", stream=torch.cuda.current_stream())

@@ -319,29 +319,38 @@ int place3d_launches_per_eval(const place3d_handle *h);
  * already handed out by that framework's allocator, so a cudaMalloc here
  * would fail or steal from it), or code in a phase where an allocation would
  * implicitly synchronise the device and stall streams it does not own.  This
- * entry point serves them: it computes the fixed-point density map of the
- * evaluation (cells by eq. density-map-accum, macros by Theorem 1, the FP64
- * contribution arithmetic and 2^-36 quantisation of place3d_create's FP64
- * mode) and writes rho[z][y][x] = counts * 2^-36 to a buffer the caller
- * provides, without allocating anything.  The paper has no counterpart of
- * this entry point.
+ * entry point serves them: it computes the same fixed-point density map as a
+ * place3d_create handle in PLACE3D_FP64 mode (FP64 contribution arithmetic,
+ * counts of 2^-36, macros through corner maps and integer prefix sums) and
+ * writes rho[z][y][x] = counts * 2^-36 to a buffer the caller provides,
+ * without allocating anything.  The paper has no counterpart of this entry
+ * point.
  *
  * Its two int64 accumulator maps live in one array of
  * 2 * PLACE3D_NOALLOC_MAX_BINS int64 (4 MiB) compiled into the library; every
- * GPU that loads the library holds that array until the process exits.
+ * GPU that loads the library's device code holds that array until the process
+ * exits.
  *
  * All pointers are DEVICE pointers of the current device: x, y, z, w_bot,
  * h_bot, w_top, h_top ([n_inst] doubles, as in place3d_problem), is_macro
  * ([n_inst] bytes) and rho ([nz*ny*nx] doubles, written).  The region and the
  * grid follow place3d_problem.  Work is enqueued on cuda_stream (NULL = the
  * default stream) and the call returns without synchronising.
- * - The first call on a device looks up the array's device address; make
- *   that first call before any stream capture on that device.
+ * - Warm-up: the first call on a device (and the first after that device's
+ *   context was reset or re-created) looks up the array's device address.
+ *   With CUDA's lazy module loading (the default) that first call is also
+ *   where the library's device code, and with it the array, is loaded onto
+ *   the device, which allocates device memory and may synchronise.  Make one
+ *   call on each device before entering the phase or arena in which nothing
+ *   may allocate, and before any stream capture on that device.
  * - Every call on a device uses the same array and clears it first.  Calls
  *   whose work overlaps on the GPU (other streams or host threads without
  *   ordering between them) race on it and produce wrong maps: order them.
+ * - Positions are not checked: for a non-finite coordinate, or z outside
+ *   [d_z/4, 3 d_z/4], the map is undefined (every access stays inside the
+ *   grid; the counts are simply wrong).
  * Errors: OUT_OF_RANGE if nx*ny*nz > PLACE3D_NOALLOC_MAX_BINS, INVALID_ARG for
- * a bad grid, region or NULL pointer, CUDA for a failed launch.
+ * a bad grid, region or NULL pointer, CUDA for a failed launch or lookup.
  */
 #define PLACE3D_NOALLOC_MAX_BINS 262144
 int place3d_density_map_noalloc(int n_inst, const double *x, const double *y,

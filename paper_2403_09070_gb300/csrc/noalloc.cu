@@ -3,6 +3,7 @@
 // sums, FP64 contribution arithmetic) writing rho to a caller buffer, with
 // its two int64 accumulator maps in a file-scope device array instead of
 // memory the library allocates.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -21,19 +22,70 @@ static __device__ __align__(256) long long g_noalloc_scratch[2 * PLACE3D_NOALLOC
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-long long *g_scratch_ptr[kMaxDevices] = {};
 
-// The device address of the scratch array for `dev` (current device),
-// looked up once per device.
+// Cached device address of the scratch array per device, tagged with the
+// unique id of the context it was looked up in.  The array's address belongs
+// to the module loaded into one context: after a device reset, or after the
+// primary context was released and created again, the module is loaded anew
+// and the array can sit elsewhere, so a cached address whose context id no
+// longer matches the current one is looked up again.
+struct ScratchAddr {
+  unsigned long long ctx_id;
+  long long *ptr;
+};
+ScratchAddr g_scratch[kMaxDevices] = {};
+
+// cuCtxGetCurrent / cuCtxGetId through the runtime's driver entry points (the
+// library does not link the driver library itself).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+std::once_flag g_entry_once;
+
+void resolve_entry_points() {
+  void *f = nullptr;
+  cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+  f = nullptr;
+  q = cudaDriverEntryPointSymbolNotFound;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f);
+}
+
+// Unique id of the calling thread's current context; false if there is none
+// yet (the runtime makes the device's primary context current on its first
+// call that needs one) or the entry points are unavailable.
+bool current_ctx_id(unsigned long long *id) {
+  std::call_once(g_entry_once, resolve_entry_points);
+  if (!g_ctx_get_current || !g_ctx_get_id) return false;
+  CUcontext c = nullptr;
+  if (g_ctx_get_current(&c) != CUDA_SUCCESS || !c) return false;
+  return g_ctx_get_id(c, id) == CUDA_SUCCESS;
+}
+
+// The device address of the scratch array for `dev` (the current device):
+// looked up with cudaGetSymbolAddress on the first call in a context (this
+// first lookup loads the library's module on the device if it is not loaded
+// yet), then reused while the current context stays the same.  Without a
+// context id the address is looked up on every call.
 cudaError_t scratch_for(int dev, long long **out) {
+  unsigned long long id = 0;
+  const bool have_id = current_ctx_id(&id);
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<long long *>(p);
+  if (have_id && g_scratch[dev].ptr && g_scratch[dev].ctx_id == id) {
+    *out = g_scratch[dev].ptr;
+    return cudaSuccess;
   }
-  *out = g_scratch_ptr[dev];
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  unsigned long long id2 = 0;
+  g_scratch[dev] = current_ctx_id(&id2) ? ScratchAddr{id2, static_cast<long long *>(p)} : ScratchAddr{0, nullptr};
+  *out = static_cast<long long *>(p);
   return cudaSuccess;
 }
 
