@@ -63,12 +63,21 @@ extern "C" {
  * instead of concurrently on a second stream (for profiling one kernel at a
  * time). */
 #define PLACE3D_FLAG_SERIAL 8
-/* Bucket the std cells per evaluation into 16x16-bin tiles and scatter /
- * gather them through shared-memory windows (a counting sort by tile, then
- * one block per chunk of a tile), instead of one thread per cell with global
- * int64 atomics and global field gathers.  Same results; which is faster
- * depends on the cell order and density.  Ignored in 2D mode. */
+/* Cell scatter and field gather.  By default the std cells are sorted per
+ * evaluation by the 16x16-bin tile holding their centre (a counting sort)
+ * and scattered / gathered through shared-memory windows of a tile plus a
+ * halo, one block per chunk of a tile (Sec. IV-A's instance parallelism for
+ * std cells, with the charge staged in shared memory: global atomics once
+ * per window bin instead of once per cell and bin).  PLACE3D_FLAG_NO_TILES
+ * uses one thread per cell
+ * with global int64 atomics and global field loads instead.  Both give the
+ * same fixed-point map bit for bit and the same gradient up to rounding.
+ * The tiled form needs fewer than 2^24 instances, at most 8192 tiles and a
+ * halo of at most 8 bins (cells at most ~16 bins wide); otherwise the
+ * per-cell form is used.  PLACE3D_FLAG_TILES (the former opt-in) is
+ * accepted and changes nothing. */
 #define PLACE3D_FLAG_TILES 16
+#define PLACE3D_FLAG_NO_TILES 32
 
 /* ---- placement mode (place3d_problem.mode) ---- */
 #define PLACE3D_MODE_3D 0 /* 3D mixed-size placement, eq. analytical-placement */
@@ -244,7 +253,9 @@ int place3d_eval_graph(place3d_handle *h, const void *x, const void *y,
  * handle's gamma, gamma_z, alpha or reduction form changes (updating the
  * executable graph in place when it can), and launches on cuda_stream after
  * the handles' last parameter writes.  Per-instance results via
- * place3d_get_result.  Errors: INVALID_ARG, CUDA. */
+ * place3d_get_result.  Errors: INVALID_ARG, CUDA (the message, naming the
+ * failing call or instance, from place3d_last_error(NULL) on the calling
+ * thread). */
 typedef struct place3d_batch place3d_batch;
 int place3d_batch_create(place3d_handle *const *handles, int count,
                          place3d_batch **out);

@@ -26,23 +26,20 @@ __device__ __forceinline__ float r_ceil(float a) { return ceilf(a); }
 __device__ __forceinline__ double r_ceil(double a) { return ceil(a); }
 // Round-half-to-even of a non-negative float to int64 without the
 // float -> 64-bit conversion instruction (it runs on the FP64 pipe, which is
-// narrow on this GPU).  a = m * 2^s with a 24-bit mantissa m:
+// narrow on this GPU), and without branches (the lanes of a warp quantise
+// contributions of very different sizes).  a = m * 2^s with a 24-bit
+// mantissa m:
 //   a >= 2^23 (s >= 0): a is an integer, m << s;
-//   2^22 <= a < 2^23 (s = -1): a is a multiple of 1/2; halve m, ties to even;
-//   a < 2^22: a + 1.5 * 2^23 lies in [2^23, 2^24), where the FP32 add itself
-//   rounds to the nearest integer (ties to even), read off the mantissa.
-// Exactly llrintf for 0 <= a < 2^63.
+//   a < 2^23: a + 2^23 lies in [2^23, 2^24), where one ulp is 1, so the FP32
+//   add itself rounds a to the nearest integer (ties to even), read off the
+//   sum's mantissa.
+// Exactly llrintf for 0 <= a < 2^63; 0 for a <= 0.
 __device__ __forceinline__ long long r_rint(float a) {
-  if (!(a > 0.0f)) return 0;  // zero, negative or NaN (contributions are >= 0)
   const unsigned u = __float_as_uint(a);
   const int s = (int)((u >> 23) & 0xffu) - 150;
-  if (s >= 0) return (long long)((unsigned long long)((u & 0x7fffffu) | 0x800000u) << s);
-  if (s == -1) {
-    const unsigned m = (u & 0x7fffffu) | 0x800000u, q = m >> 1;
-    return (long long)(q + (m & q & 1u));
-  }
-  const float t = __fadd_rn(a, 12582912.0f);  // 1.5 * 2^23
-  return (long long)(__float_as_int(t) - 0x4B400000);
+  const long long big = (long long)((unsigned long long)((u & 0x7fffffu) | 0x800000u) << (s > 0 ? s : 0));
+  const long long small = (long long)(__float_as_int(__fadd_rn(a, 8388608.0f)) - 0x4B000000);
+  return a >= 8388608.0f ? big : (a > 0.0f ? small : 0ll);
 }
 __device__ __forceinline__ long long r_rint(double a) { return __double2ll_rn(a); }
 // int64 -> FP32, round half to even, with 32-bit and integer operations only

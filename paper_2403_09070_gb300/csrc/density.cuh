@@ -506,18 +506,24 @@ __global__ void k_final_macro_out(int nm, const int *__restrict__ macro_ids, con
   final_out(i, flags[i], pos[i].z, acc[i], dgx, dgy, dgz, g_scale_t<T>(fc.scal), lam4, fc, zmid, gx, gy, gz);
 }
 
-// ======================= tile-bucketed scatter and gather =======================
-// Cells are bucketed per evaluation by the 16x16-bin tile (all layers) that
-// holds their centre (counting sort: block histograms give ranks, a scan
-// gives tile starts, a placement pass writes each cell's record in tile
-// order).  A work item is a chunk of one tile's cells; its block accumulates
-// contributions in a shared-memory window (tile + halo of R bins, all
-// layers) and adds the window to the map once, and later gathers the field
-// from a shared-memory copy of the same window.  Cells whose footprint
-// leaves the window use the global map directly.
+// ======================= tile-sorted scatter and gather =======================
+// Cells are sorted per evaluation by the 16x16-bin tile (all layers) that
+// holds their centre: a counting sort (block histograms give each cell its
+// rank in its tile, a scan gives the tile starts), then one 32-byte record
+// per cell in tile order holding its stretched cuboid and omega (inst_box,
+// computed once for both the scatter and the gather).  A work item is a
+// chunk of at most kChunk cells of one tile; its block accumulates the
+// chunk's charge in a shared-memory window (the tile plus a halo of R bins,
+// all layers) and adds the window to the map with one global atomic per
+// nonzero bin, and later gathers the field of the same window from a
+// shared-memory copy.  A cell whose footprint leaves the window (only when
+// it is wider than the halo allows) uses the global map directly.
 constexpr int kTile = 16;
-constexpr int kChunk = 1024;  // cells per work item
+constexpr int kChunk = 1024;  // cells per work item: bounds the window's split sums (k_scatter_tiles)
 constexpr int kCountPerThread = 8;
+// The tile counters lie one per 128-byte line: the count blocks' atomics on
+// different tiles then never queue on the same line in the L2.
+constexpr int kCountPad = 32;
 
 struct TileC {
   int ntx, nty, R, WX, WY;  // tiles per axis, halo, window size (bins)
@@ -533,11 +539,13 @@ __device__ __forceinline__ int tile_of(const DensC<T> &c, const TileC &tc, T X, 
 }
 
 // Tile of every cell and its rank inside the tile (macros get -1).  Each
-// block of 1024 threads takes 8 cells per thread, ranks them in a
-// shared-memory histogram, then reserves its range of every tile with one
-// global atomic per (block, tile).
+// block of kCountBlock threads takes kCountPerThread cells per thread (few,
+// large blocks: the per-(block, tile) global atomics contend less), ranks them in a
+// shared-memory histogram, then reserves its range of every tile it holds
+// cells of with one global atomic per (block, tile).
+constexpr int kCountBlock = 512;
 template <typename T>
-__global__ void __launch_bounds__(1024) k_tile_count(int n, const V4<T> *__restrict__ pos,
+__global__ void __launch_bounds__(kCountBlock) k_tile_count(int n, const V4<T> *__restrict__ pos,
                                                      const uint8_t *__restrict__ flags, DensC<T> c, TileC tc,
                                                      int ntiles, int *__restrict__ count, int2 *__restrict__ key) {
   extern __shared__ int hist[];
@@ -559,7 +567,7 @@ __global__ void __launch_bounds__(1024) k_tile_count(int n, const V4<T> *__restr
   __syncthreads();
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
     const int v = hist[t];
-    hist[t] = v ? atomicAdd(count + t, v) : 0;  // this block's first rank in tile t
+    hist[t] = v ? atomicAdd(count + t * kCountPad, v) : 0;  // this block's first rank in tile t
   }
   __syncthreads();
 #pragma unroll
@@ -578,8 +586,8 @@ static __global__ void __launch_bounds__(1024) k_tile_scan(int ntiles, const int
   const int t0 = t * per, t1 = min(ntiles, t0 + per);
   int cells = 0, its = 0;
   for (int k = t0; k < t1; ++k) {
-    cells += count[k];
-    its += (count[k] + kChunk - 1) / kChunk;
+    cells += count[k * kCountPad];
+    its += (count[k * kCountPad] + kChunk - 1) / kChunk;
   }
   s_cells[t] = cells;
   s_items[t] = its;
@@ -593,10 +601,11 @@ static __global__ void __launch_bounds__(1024) k_tile_scan(int ntiles, const int
   }
   int cs = s_cells[t] - cells, is = s_items[t] - its;
   for (int k = t0; k < t1; ++k) {
+    const int ck = count[k * kCountPad];
     start[k] = cs;
-    const int nc = (count[k] + kChunk - 1) / kChunk;
+    const int nc = (ck + kChunk - 1) / kChunk;
     for (int j = 0; j < nc; ++j) items[is + j] = make_int2(k, j);
-    cs += count[k];
+    cs += ck;
     is += nc;
   }
   if (t == 1023) {
@@ -605,26 +614,39 @@ static __global__ void __launch_bounds__(1024) k_tile_scan(int ntiles, const int
   }
 }
 
-// Cell record in tile order: position, sizes, and the instance index with
-// its flags in the top byte.
-template <typename T> struct CellRec {
-  V4<T> pos, size;
-  int idx_flags, pad[3];
+// One cell in tile order: its stretched cuboid in bin units (unclipped, as
+// inst_box gives it), omega, and the instance index with its flags in the
+// top byte.  32 bytes in FP32 (one sector), 64 in FP64.
+template <typename T> struct TileRec;
+template <> struct alignas(32) TileRec<float> {
+  float lo[3], hi[3], om;
+  int idx_flags;
+};
+template <> struct alignas(64) TileRec<double> {
+  double lo[3], hi[3], om;
+  int idx_flags, pad;
 };
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_tile_place(int n, const int2 *__restrict__ key, const int *__restrict__ start,
                                                     const V4<T> *__restrict__ pos, const V4<T> *__restrict__ size,
-                                                    const uint8_t *__restrict__ flags, CellRec<T> *__restrict__ rec) {
+                                                    const uint8_t *__restrict__ flags, DensC<T> c,
+                                                    TileRec<T> *__restrict__ rec) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int2 k = key[i];
   if (k.x < 0) return;
-  CellRec<T> r;
-  r.pos = pos[i];
-  r.size = size[i];
-  r.idx_flags = i | ((int)flags[i] << 24);
-  r.pad[0] = r.pad[1] = r.pad[2] = 0;
+  const uint8_t f = flags[i];
+  const V4<T> p = pos[i];
+  const Box<T> b = inst_box(c, p.x, p.y, p.z, size[i], false, (f & 4) != 0);
+  TileRec<T> r;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    r.lo[a] = b.lo[a];
+    r.hi[a] = b.hi[a];
+  }
+  r.om = b.om;
+  r.idx_flags = i | ((int)f << 24);
   rec[start[k.x] + k.y] = r;
 }
 
@@ -634,14 +656,60 @@ __device__ __forceinline__ void tile_window(const TileC &tc, int tile, int &x0, 
   y0 = (tile / tc.ntx) * kTile - tc.R;
 }
 
-// ---- a2 with shared-memory bin tiles ----
-// The window keeps each int64 count as two 32-bit words (low word, and high
-// word plus the low word's carries), so every update is a native 32-bit
-// shared-memory atomic; the window is added to the map once per item.
+// Per-axis overlaps of a clipped cuboid with its (at most 3) bins, for the
+// separable fast paths: o[a] = overlap with bin b0 + a (0 past the last bin).
+template <typename T>
+__device__ __forceinline__ void axis_ov3(T cl, T chh, int b0, int nb, T (&o)[3]) {
+  const T e0 = (T)b0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) o[a] = a < nb ? ov_edge(cl, chh, e0 + T(a)) : T(0);
+}
+
+// ---- a2 through shared-memory windows ----
+// Each quantised contribution v (0 <= v <= 2^36: a contribution is at most
+// one bin of density) is split as v = hi * 2^22 + lo and the two parts are
+// added to two 32-bit words of the bin with native shared-memory adds.  A
+// chunk holds at most kChunk = 1024 cells and a cell adds to a bin at most
+// once, so the low sums stay below 1024 * 2^22 = 2^32 and the high sums
+// below 2^24: no 32-bit sum wraps, and hi_sum * 2^22 + lo_sum is the exact
+// int64 total, added to the map once per bin.
+// A cell covering at most 3 bins per axis (every std cell whose stretched
+// footprint is under 2 bins wide: all of them on the usual grids) takes the
+// separable path: 3 overlaps per axis, the products ((omega*ox)*oy) once per
+// (x, y) pair, then *oz and the scale per bin -- the same IEEE operations in
+// the same order as the per-bin form, so the same quantised values.
+template <typename T>
+__device__ __forceinline__ void win_add(unsigned *wlo, unsigned *whi, int w, long long v) {
+  const unsigned long long u = (unsigned long long)v;
+  atomicAdd(wlo + w, (unsigned)(u & 0x3fffffull));
+  atomicAdd(whi + w, (unsigned)(u >> 22));
+}
+
+// rint(a) split as hi * 2^22 + lo (0 <= lo < 2^22) for 0 <= a <= 2^36, in
+// 32-bit integer operations: for a >= 2^23, a = m 2^s with a 24-bit mantissa
+// m and 0 <= s <= 13, so hi = m >> (22 - s) and lo = (m << s) mod 2^22; below
+// 2^23 the FP32 add of 2^23 rounds a to an integer (ties to even) as in
+// r_rint.  Equal to splitting r_rint(a).
+__device__ __forceinline__ void rint_split(float a, unsigned &hi, unsigned &lo) {
+  const unsigned u = __float_as_uint(a);
+  const int s = (int)((u >> 23) & 0xffu) - 150;
+  const unsigned m = (u & 0x7fffffu) | 0x800000u;
+  const unsigned sm = (unsigned)(__float_as_int(__fadd_rn(a, 8388608.0f)) - 0x4B000000);
+  const bool big = a >= 8388608.0f;
+  const int sc = s < 0 ? 0 : (s > 22 ? 22 : s);
+  hi = big ? (m >> (22 - sc)) : (a > 0.0f ? sm >> 22 : 0u);
+  lo = big ? ((m << sc) & 0x3fffffu) : (a > 0.0f ? sm & 0x3fffffu : 0u);
+}
+__device__ __forceinline__ void rint_split(double a, unsigned &hi, unsigned &lo) {
+  const unsigned long long u = (unsigned long long)r_rint(a);
+  hi = (unsigned)(u >> 22);
+  lo = (unsigned)(u & 0x3fffffull);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_scatter_tiles(const int2 *__restrict__ items, const int *__restrict__ nitems,
                                                        const int *__restrict__ start,
-                                                       const CellRec<T> *__restrict__ rec, DensC<T> c, TileC tc,
+                                                       const TileRec<T> *__restrict__ rec, DensC<T> c, TileC tc,
                                                        long long *__restrict__ q) {
   extern __shared__ unsigned win32[];
   if ((int)blockIdx.x >= *nitems) return;
@@ -655,37 +723,69 @@ __global__ void __launch_bounds__(256) k_scatter_tiles(const int2 *__restrict__ 
   const int c0 = start[it.x] + it.y * kChunk, c1 = min(start[it.x + 1], c0 + kChunk);
   const T scale = (T)kFixedScale;
   for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) {
-    const CellRec<T> r = rec[s];
-    const Box<T> b = inst_box(c, r.pos.x, r.pos.y, r.pos.z, r.size, false);
+    const TileRec<T> r = rec[s];
     T cl[3], chh[3];
     int b0[3], b1[3];
-    if (!clip_axis(b.lo[0], b.hi[0], c.fnx, c.nx, cl[0], chh[0], b0[0], b1[0])) continue;
-    if (!clip_axis(b.lo[1], b.hi[1], c.fny, c.ny, cl[1], chh[1], b0[1], b1[1])) continue;
-    if (!clip_axis(b.lo[2], b.hi[2], c.fnz, c.nz, cl[2], chh[2], b0[2], b1[2])) continue;
+    if (!clip_axis(r.lo[0], r.hi[0], c.fnx, c.nx, cl[0], chh[0], b0[0], b1[0])) continue;
+    if (!clip_axis(r.lo[1], r.hi[1], c.fny, c.ny, cl[1], chh[1], b0[1], b1[1])) continue;
+    if (!clip_axis(r.lo[2], r.hi[2], c.fnz, c.nz, cl[2], chh[2], b0[2], b1[2])) continue;
     const bool inwin = b0[0] >= x0 && b1[0] < x0 + tc.WX && b0[1] >= y0 && b1[1] < y0 + tc.WY;
-    for (int k = b0[2]; k <= b1[2]; ++k) {
-      const T oz = ov_axis(cl[2], chh[2], k);
-      for (int j = b0[1]; j <= b1[1]; ++j) {
-        const T oy = ov_axis(cl[1], chh[1], j);
-        for (int ii = b0[0]; ii <= b1[0]; ++ii) {
-          const T ox = ov_axis(cl[0], chh[0], ii);
-          const long long v = r_rint(rn_mul(rn_mul(rn_mul(rn_mul(b.om, ox), oy), oz), scale));
-          if (inwin) {
-            const int w = (k * tc.WY + (j - y0)) * tc.WX + (ii - x0);
-            const unsigned lo = (unsigned)v, hi = (unsigned)((unsigned long long)v >> 32);
-            const unsigned old = atomicAdd(wlo + w, lo);
-            const unsigned up = hi + (old + lo < old ? 1u : 0u);  // low-word carry
-            if (up) atomicAdd(whi + w, up);
-          } else {
-            atomic_add_i64(q + ((size_t)k * c.ny + j) * c.nx + ii, v);
+    const int nxb = b1[0] - b0[0] + 1, nyb = b1[1] - b0[1] + 1, nzb = b1[2] - b0[2] + 1;
+    if (inwin && nxb <= 3 && nyb <= 3 && nzb <= 3) {
+      T ox[3], oy[3], oz[3];
+      axis_ov3(cl[0], chh[0], b0[0], nxb, ox);
+      axis_ov3(cl[1], chh[1], b0[1], nyb, oy);
+      axis_ov3(cl[2], chh[2], b0[2], nzb, oz);
+      T t[3][3];  // ((omega * ox) * oy) per (y, x) pair
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T wo = rn_mul(r.om, ox[a]);
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) t[bb][a] = rn_mul(wo, oy[bb]);
+      }
+      // all 27 slots without branches: a slot past the cuboid's last bin has a
+      // zero overlap, so its value is 0 and its (possibly out-of-window) add is
+      // skipped by predicate
+      const int wbase = (b0[2] * tc.WY + (b0[1] - y0)) * tc.WX + (b0[0] - x0);
+#pragma unroll
+      for (int cz = 0; cz < 3; ++cz)
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+          const int wrow = wbase + (cz * tc.WY + bb) * tc.WX;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            unsigned hi, lo;
+            rint_split(rn_mul(rn_mul(t[bb][a], oz[cz]), scale), hi, lo);
+            if (hi | lo) {
+              atomicAdd(wlo + wrow + a, lo);
+              atomicAdd(whi + wrow + a, hi);
+            }
           }
+        }
+      continue;
+    }
+    T ez = (T)b0[2];
+    for (int k = b0[2]; k <= b1[2]; ++k, ez += T(1)) {
+      const T oz = ov_edge(cl[2], chh[2], ez);
+      T ey = (T)b0[1];
+      for (int j = b0[1]; j <= b1[1]; ++j, ey += T(1)) {
+        const T oy = ov_edge(cl[1], chh[1], ey);
+        const int wrow = (k * tc.WY + (j - y0)) * tc.WX - x0;
+        T ex = (T)b0[0];
+        for (int ii = b0[0]; ii <= b1[0]; ++ii, ex += T(1)) {
+          const T ox = ov_edge(cl[0], chh[0], ex);
+          const long long v = r_rint(rn_mul(rn_mul(rn_mul(rn_mul(r.om, ox), oy), oz), scale));
+          if (inwin)
+            win_add<T>(wlo, whi, wrow + ii, v);
+          else
+            atomic_add_i64(q + ((size_t)k * c.ny + j) * c.nx + ii, v);
         }
       }
     }
   }
   __syncthreads();
   for (int k = threadIdx.x; k < nwin; k += blockDim.x) {
-    const long long v = (long long)(((unsigned long long)whi[k] << 32) | (unsigned long long)wlo[k]);
+    const long long v = (long long)(((unsigned long long)whi[k] << 22) + (unsigned long long)wlo[k]);
     if (!v) continue;
     const int xx = x0 + k % tc.WX, yy = y0 + (k / tc.WX) % tc.WY, zz = k / (tc.WX * tc.WY);
     if (xx >= 0 && xx < c.nx && yy >= 0 && yy < c.ny) atomic_add_i64(q + ((size_t)zz * c.ny + yy) * c.nx + xx, v);
@@ -693,68 +793,79 @@ __global__ void __launch_bounds__(256) k_scatter_tiles(const int2 *__restrict__ 
 }
 
 // ---- a10 + a9 + a11 for the cells of one work item, field from shared memory ----
-// Writes (gx, gy, gz, 0) per instance into an interleaved buffer (one write
-// per cell); k_split_grad copies it to the caller's arrays.
+// Writes (gx, gy, gz, 0) per instance into the interleaved buffer g4 (one
+// 16- or 32-byte write per cell); k_split_grad copies it to the caller's
+// arrays with coalesced stores.  Cells covering at most 3 bins per axis sum
+// the window with 3 overlaps per axis computed once.
 template <typename T>
 __global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ items, const int *__restrict__ nitems,
                                                      const int *__restrict__ start,
-                                                     const CellRec<T> *__restrict__ rec, DensC<T> c, TileC tc,
+                                                     const TileRec<T> *__restrict__ rec, DensC<T> c, TileC tc,
                                                      const V4<T> *__restrict__ e4, const V4<T> *__restrict__ acc,
                                                      FinalC<T> fc, V4<T> *__restrict__ g4) {
   extern __shared__ __align__(16) unsigned char fwin_raw[];
-  T *wx = reinterpret_cast<T *>(fwin_raw);
-  __shared__ T g_sh, lam_sh;
+  V4<T> *fw = reinterpret_cast<V4<T> *>(fwin_raw);
+  __shared__ T g_sh, lam_sh[4];
   if ((int)blockIdx.x >= *nitems) return;
   const int2 it = items[blockIdx.x];
   int x0, y0;
   tile_window(tc, it.x, x0, y0);
   const int nwin = tc.WX * tc.WY * c.nz;
-  T *wy = wx + nwin, *wz = wy + nwin;
   for (int k = threadIdx.x; k < nwin; k += blockDim.x) {
     const int xx = x0 + k % tc.WX, yy = y0 + (k / tc.WX) % tc.WY, zz = k / (tc.WX * tc.WY);
-    T a = 0, b2 = 0, d2 = 0;
-    if (xx >= 0 && xx < c.nx && yy >= 0 && yy < c.ny) {
-      const V4<T> e = e4[((size_t)zz * c.ny + yy) * c.nx + xx];
-      a = e.x;
-      b2 = e.y;
-      d2 = e.z;
-    }
-    wx[k] = a;
-    wy[k] = b2;
-    wz[k] = d2;
+    V4<T> e{T(0), T(0), T(0), T(0)};
+    if (xx >= 0 && xx < c.nx && yy >= 0 && yy < c.ny) e = e4[((size_t)zz * c.ny + yy) * c.nx + xx];
+    fw[k] = e;
   }
-  if (threadIdx.x == 0) {
-    g_sh = g_scale_t<T>(fc.scal);
-    lam_sh = fc.lam_dev[0];
-  }
+  if (threadIdx.x == 0) g_sh = g_scale_t<T>(fc.scal);
+  if (threadIdx.x < 4) lam_sh[threadIdx.x] = fc.lam_dev[threadIdx.x];
   __syncthreads();
-  const T g = g_sh, lam = lam_sh;
+  const T g = g_sh;
   const int c0 = start[it.x] + it.y * kChunk, c1 = min(start[it.x + 1], c0 + kChunk);
   for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) {
-    const CellRec<T> r = rec[s];
+    const TileRec<T> r = rec[s];
     const int i = r.idx_flags & 0xffffff, f = (r.idx_flags >> 24) & 0xff;
     const V4<T> a = acc[i];
-    const Box<T> b = inst_box(c, r.pos.x, r.pos.y, r.pos.z, r.size, false);
     T cl[3], chh[3];
     int b0[3], b1[3];
     T sx = 0, sy = 0, sz = 0;
-    if (clip_axis(b.lo[0], b.hi[0], c.fnx, c.nx, cl[0], chh[0], b0[0], b1[0]) &&
-        clip_axis(b.lo[1], b.hi[1], c.fny, c.ny, cl[1], chh[1], b0[1], b1[1]) &&
-        clip_axis(b.lo[2], b.hi[2], c.fnz, c.nz, cl[2], chh[2], b0[2], b1[2])) {
+    if (clip_axis(r.lo[0], r.hi[0], c.fnx, c.nx, cl[0], chh[0], b0[0], b1[0]) &&
+        clip_axis(r.lo[1], r.hi[1], c.fny, c.ny, cl[1], chh[1], b0[1], b1[1]) &&
+        clip_axis(r.lo[2], r.hi[2], c.fnz, c.nz, cl[2], chh[2], b0[2], b1[2])) {
       const bool inwin = b0[0] >= x0 && b1[0] < x0 + tc.WX && b0[1] >= y0 && b1[1] < y0 + tc.WY;
-      for (int k = b0[2]; k <= b1[2]; ++k) {
-        const T oz = ov_axis(cl[2], chh[2], k);
-        for (int j = b0[1]; j <= b1[1]; ++j) {
-          const T oyz = ov_axis(cl[1], chh[1], j) * oz;
-          for (int ii = b0[0]; ii <= b1[0]; ++ii) {
-            const T v = ov_axis(cl[0], chh[0], ii) * oyz;
-            if (inwin) {
-              const int w = (k * tc.WY + (j - y0)) * tc.WX + (ii - x0);
-              sx += v * wx[w];
-              sy += v * wy[w];
-              sz += v * wz[w];
-            } else {
-              const V4<T> e = e4[((size_t)k * c.ny + j) * c.nx + ii];
+      const int nxb = b1[0] - b0[0] + 1, nyb = b1[1] - b0[1] + 1, nzb = b1[2] - b0[2] + 1;
+      if (inwin && nxb <= 3 && nyb <= 3 && nzb <= 3) {
+        T ox[3], oy[3], oz[3];
+        axis_ov3(cl[0], chh[0], b0[0], nxb, ox);
+        axis_ov3(cl[1], chh[1], b0[1], nyb, oy);
+        axis_ov3(cl[2], chh[2], b0[2], nzb, oz);
+        // all 27 slots without branches: a slot past the cuboid's last bin has
+        // weight 0 and reads the cuboid's first bin (always in the window)
+        const int wbase = (b0[2] * tc.WY + (b0[1] - y0)) * tc.WX + (b0[0] - x0);
+#pragma unroll
+        for (int cz = 0; cz < 3; ++cz)
+#pragma unroll
+          for (int bb = 0; bb < 3; ++bb) {
+            const T oyz = oy[bb] * oz[cz];
+            const int wrow = wbase + (cz < nzb ? cz : 0) * tc.WY * tc.WX + (bb < nyb ? bb : 0) * tc.WX;
+#pragma unroll
+            for (int aa = 0; aa < 3; ++aa) {
+              const V4<T> e = fw[wrow + (aa < nxb ? aa : 0)];
+              const T v = ox[aa] * oyz;  // 0 past the last bin
+              sx += v * e.x;
+              sy += v * e.y;
+              sz += v * e.z;
+            }
+          }
+      } else {
+        for (int k = b0[2]; k <= b1[2]; ++k) {
+          const T oz = ov_axis(cl[2], chh[2], k);
+          for (int j = b0[1]; j <= b1[1]; ++j) {
+            const T oyz = ov_axis(cl[1], chh[1], j) * oz;
+            const int wrow = (k * tc.WY + (j - y0)) * tc.WX - x0;
+            for (int ii = b0[0]; ii <= b1[0]; ++ii) {
+              const T v = ov_axis(cl[0], chh[0], ii) * oyz;
+              const V4<T> e = inwin ? fw[wrow + ii] : e4[((size_t)k * c.ny + j) * c.nx + ii];
               sx += v * e.x;
               sy += v * e.y;
               sz += v * e.z;
@@ -763,9 +874,11 @@ __global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ it
         }
       }
     }
-    const T kk = -b.om * fc.volb;
+    const T kk = -r.om * fc.volb;
+    // 2D mode: the layer is the cuboid's z bin (0 bottom, 1 top, 2 HBT)
+    const T lam = fc.mode2d ? lam_sh[1 + (int)r.lo[2]] : lam_sh[0];
     T ozg = g * a.z + fc.alpha * a.w + lam * (kk * sz);
-    if (f & 2) ozg = T(0);
+    if ((f & 2) || fc.mode2d) ozg = T(0);
     V4<T> o;
     o.x = a.x + lam * (kk * sx);
     o.y = a.y + lam * (kk * sy);
@@ -775,21 +888,22 @@ __global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ it
   }
 }
 
-// Final gradient of the macros (their density part comes from mgrad).
+// Final gradient of the macros into g4 (their density part comes from mgrad).
 template <typename T>
-__global__ void k_final_macros(int nm, const int *__restrict__ macro_ids, const uint8_t *__restrict__ flags,
-                               const double *__restrict__ mgrad, const V4<T> *__restrict__ acc, FinalC<T> fc,
-                               V4<T> *__restrict__ g4) {
+__global__ void k_final_macros(int nm, const int *__restrict__ macro_ids, const V4<T> *__restrict__ pos,
+                               const uint8_t *__restrict__ flags, const double *__restrict__ mgrad,
+                               const V4<T> *__restrict__ acc, FinalC<T> fc, T zmid, V4<T> *__restrict__ g4) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= nm) return;
   const int i = macro_ids[m];
-  const T g = g_scale_t<T>(fc.scal), lam = fc.lam_dev[0];
-  const T dgx = (T)(-(double)fc.volb * mgrad[m * 3 + 0]);
-  const T dgy = (T)(-(double)fc.volb * mgrad[m * 3 + 1]);
-  const T dgz = (T)(-(double)fc.volb * mgrad[m * 3 + 2]);
+  const T g = g_scale_t<T>(fc.scal);
+  // 2D mode: the weight of the macro's die layer
+  const T lam = fc.mode2d ? fc.lam_dev[pos[i].z > zmid ? 2 : 1] : fc.lam_dev[0];
+  T dgx, dgy, dgz;
+  macro_force(mgrad, m, fc.volb, dgx, dgy, dgz);
   const V4<T> a = acc[i];
   T ozg = g * a.z + fc.alpha * a.w + lam * dgz;
-  if (flags[i] & 2) ozg = T(0);
+  if ((flags[i] & 2) || fc.mode2d) ozg = T(0);
   V4<T> o;
   o.x = a.x + lam * dgx;
   o.y = a.y + lam * dgy;

@@ -99,7 +99,7 @@ struct place3d_handle {
   int ntiles = 0, max_items = 0;
   size_t smem_scatter = 0, smem_final = 0;
   int2 *tkey = nullptr, *titems = nullptr;
-  void *trec = nullptr;  // CellRec<T>[n] in tile order
+  void *trec = nullptr;  // TileRec<T>[n] in tile order
   void *g4 = nullptr;    // interleaved gradient V4<T>[n]
   int *tcount = nullptr, *tstart = nullptr, *tnitems = nullptr;
   int n = 0, nm = 0, nnet = 0, npin = 0;
@@ -479,20 +479,29 @@ void run_transforms_tc(place3d_handle *h, cudaStream_t s, cudaStream_t rs) {
   }
 }
 
+// Tiled final assembly: the cells' gather into g4, then (once the macros'
+// field gather on the macro stream is done, when split) the macros' rows of
+// g4, then one coalesced copy of g4 into the three output arrays.
 template <typename T, typename TO>
-void launch_final_tiles(place3d_handle *h, cudaStream_t s, const DensC<T> &dc, const FinalC<T> &fc, TO *ox, TO *oy,
-                        TO *oz) {
-  k_final_tiles<T><<<h->max_items, 256, h->smem_final, s>>>(h->titems, h->tnitems, h->tstart, as<CellRec<T>>(h->trec),
+int launch_final_tiles(place3d_handle *h, cudaStream_t s, cudaStream_t ms, bool split, const DensC<T> &dc,
+                       const FinalC<T> &fc, TO *ox, TO *oy, TO *oz) {
+  k_final_tiles<T><<<h->max_items, 256, h->smem_final, s>>>(h->titems, h->tnitems, h->tstart, as<TileRec<T>>(h->trec),
                                                             dc, h->tcfg, as<V4<T>>(h->e4), as<V4<T>>(h->acc), fc,
                                                             as<V4<T>>(h->g4));
   count_launch(h, ST_FINAL);
   if (h->nm > 0) {
-    k_final_macros<T><<<grid_for(h->nm, 128), 128, 0, s>>>(h->nm, h->macro_ids, h->flags_d, h->mgrad,
-                                                           as<V4<T>>(h->acc), fc, as<V4<T>>(h->g4));
+    if (split) {
+      P3D_CUDA(h, cudaEventRecord(h->ev_mgrad, ms));
+      P3D_CUDA(h, cudaStreamWaitEvent(s, h->ev_mgrad, 0));
+    }
+    k_final_macros<T><<<grid_for(h->nm, 128), 128, 0, s>>>(h->nm, h->macro_ids, as<V4<T>>(h->pos), h->flags_d,
+                                                           h->mgrad, as<V4<T>>(h->acc), fc, dc.zmid,
+                                                           as<V4<T>>(h->g4));
     count_launch(h, ST_FINAL);
   }
   k_split_grad<T, TO><<<grid_for(h->n, 256), 256, 0, s>>>(h->n, as<V4<T>>(h->g4), ox, oy, oz);
   count_launch(h, ST_FINAL);
+  return PLACE3D_OK;
 }
 
 template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void *gz, int dtype, int mem) {
@@ -508,7 +517,7 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
   // third stream (not in serial mode): the macros' path when their field
   // gather is direct and the scatter untiled, and the scalar reductions that
   // nothing on the density chain waits for
-  const bool split = !serial && h->nm > 0 && h->macro_direct && !h->tiles;
+  const bool split = !serial && h->nm > 0 && h->macro_direct;
   cudaStream_t ms = serial ? s : h->mac;
   if (ms != s) P3D_CUDA(h, cudaStreamWaitEvent(ms, h->ev_fork, 0));
   cudaStream_t mcs = split ? ms : s;  // stream of the macros' kernels
@@ -542,14 +551,14 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     StageScope sc(h, ST_SCATTER, s);
     P3D_CUDA(h, cudaMemsetAsync(h->q, 0, sizeof(long long) * h->nb, s));
     if (n > 0 && h->tiles) {
-      P3D_CUDA(h, cudaMemsetAsync(h->tcount, 0, sizeof(int) * h->ntiles, s));
-      k_tile_count<T><<<grid_for(n, 1024 * kCountPerThread), 1024, sizeof(int) * h->ntiles, s>>>(
+      P3D_CUDA(h, cudaMemsetAsync(h->tcount, 0, sizeof(int) * kCountPad * h->ntiles, s));
+      k_tile_count<T><<<grid_for(n, kCountBlock * kCountPerThread), kCountBlock, sizeof(int) * h->ntiles, s>>>(
           n, as<V4<T>>(h->pos), h->flags_d, dc, h->tcfg, h->ntiles, h->tcount, h->tkey);
       k_tile_scan<<<1, 1024, 0, s>>>(h->ntiles, h->tcount, h->tstart, h->titems, h->tnitems);
       k_tile_place<T><<<grid_for(n, 256), 256, 0, s>>>(n, h->tkey, h->tstart, as<V4<T>>(h->pos), as<V4<T>>(h->size),
-                                                       h->flags_d, as<CellRec<T>>(h->trec));
+                                                       h->flags_d, dc, as<TileRec<T>>(h->trec));
       k_scatter_tiles<T><<<h->max_items, 256, h->smem_scatter, s>>>(h->titems, h->tnitems, h->tstart,
-                                                                    as<CellRec<T>>(h->trec), dc, h->tcfg, h->q);
+                                                                    as<TileRec<T>>(h->trec), dc, h->tcfg, h->q);
       for (int k = 0; k < 4; ++k) count_launch(h, ST_SCATTER);
     } else if (n > 0) {
       k_scatter_cells<T><<<grid_for(2 * (long long)n, 256), 256, 0, s>>>(n, as<V4<T>>(h->pos), as<V4<T>>(h->size), h->flags_d,
@@ -642,10 +651,10 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     void *oy = direct ? gy : (char *)h->gout + (size_t)n * sizeof(T);
     void *oz = direct ? gz : (char *)h->gout + (size_t)2 * n * sizeof(T);
     if (n > 0 && h->tiles) {
-      if (odt == PLACE3D_F64)
-        launch_final_tiles<T, double>(h, s, dc, fc, (double *)ox, (double *)oy, (double *)oz);
-      else
-        launch_final_tiles<T, float>(h, s, dc, fc, (float *)ox, (float *)oy, (float *)oz);
+      const int rt = odt == PLACE3D_F64
+                         ? launch_final_tiles<T, double>(h, s, ms, split, dc, fc, (double *)ox, (double *)oy, (double *)oz)
+                         : launch_final_tiles<T, float>(h, s, ms, split, dc, fc, (float *)ox, (float *)oy, (float *)oz);
+      if (rt != PLACE3D_OK) return rt;
     } else if (n > 0) {
       if (odt == PLACE3D_F64)
         k_final<T, double><<<grid_for(n, 256), 256, 0, s>>>(n, as<V4<T>>(h->pos), as<V4<T>>(h->size), h->flags_d,
@@ -1011,7 +1020,9 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
         hw = std::max(hw, std::max(p->w_bot[i], p->w_top[i]));
         hh = std::max(hh, std::max(p->h_bot[i], p->h_top[i]));
       }
-    const int R = (int)std::max(std::ceil(0.5 * hw / wbv), std::ceil(0.5 * hh / hbv)) + 1;
+    // a cell's centre lies in its tile, so a halo of ceil(half the stretched
+    // footprint) bins holds the whole footprint
+    const int R = std::max(1, (int)std::max(std::ceil(0.5 * hw / wbv), std::ceil(0.5 * hh / hbv)));
     h->tcfg.ntx = (p->nx + kTile - 1) / kTile;
     h->tcfg.nty = (p->ny + kTile - 1) / kTile;
     h->tcfg.R = R;
@@ -1020,8 +1031,8 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
     h->ntiles = h->tcfg.ntx * h->tcfg.nty;
     const size_t wbins = (size_t)h->tcfg.WX * h->tcfg.WY * p->nz;
     h->smem_scatter = wbins * 8;  // two 32-bit words per bin
-    h->smem_final = wbins * 3 * (p->precision == PLACE3D_FP64 ? 8 : 4);
-    h->tiles = (p->flags & PLACE3D_FLAG_TILES) && !h->mode2d && R <= 8 && h->ntiles <= 8192 && n < (1 << 24) &&
+    h->smem_final = wbins * 4 * (p->precision == PLACE3D_FP64 ? 8 : 4);  // one (E_x, E_y, E_z, -) vector per bin
+    h->tiles = !(p->flags & PLACE3D_FLAG_NO_TILES) && R <= 8 && h->ntiles <= 8192 && n < (1 << 24) &&
                h->smem_final <= 200 * 1024 && h->smem_scatter <= 200 * 1024;
     h->max_items = (n + kChunk - 1) / kChunk + h->ntiles;
   }
@@ -1047,9 +1058,9 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
       {&h->part_n, sizeof(double) * 8 * (size_t)grid_for((long long)nn, 256)},
       {&h->gout, 3 * es * nn}, {(void **)&h->check_flag, sizeof(int)},
       {(void **)&h->tkey, sizeof(int2) * nn},
-      {&h->trec, (p->precision == PLACE3D_FP64 ? sizeof(CellRec<double>) : sizeof(CellRec<float>)) * nn},
+      {&h->trec, (p->precision == PLACE3D_FP64 ? sizeof(TileRec<double>) : sizeof(TileRec<float>)) * nn},
       {&h->g4, v4 * nn},
-      {(void **)&h->tcount, sizeof(int) * (size_t)std::max(h->ntiles, 1)},
+      {(void **)&h->tcount, sizeof(int) * kCountPad * (size_t)std::max(h->ntiles, 1)},
       {(void **)&h->tstart, sizeof(int) * (size_t)(h->ntiles + 1)},
       {(void **)&h->titems, sizeof(int2) * (size_t)std::max(h->max_items, 1)}, {(void **)&h->tnitems, sizeof(int)}};
   for (auto &a : allocs) {
@@ -1135,17 +1146,25 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
     fail(h, PLACE3D_ERR_CUDA, "upload failed");
     return bail(PLACE3D_ERR_CUDA);
   }
-  if (h->tiles) {
+  if (h->tiles && std::max(h->smem_scatter, h->smem_final) > 48 * 1024) {
+    // The limit is a property of the kernel, shared by every handle: raise it
+    // to the device's opt-in maximum (never lower it, which would break the
+    // launches of a handle with larger windows captured earlier)
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     const bool f64 = h->precision == PLACE3D_FP64;
     cudaError_t e1 = f64 ? cudaFuncSetAttribute(k_scatter_tiles<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)h->smem_scatter)
+                                                optin)
                          : cudaFuncSetAttribute(k_scatter_tiles<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)h->smem_scatter);
+                                                optin);
     cudaError_t e2 = f64 ? cudaFuncSetAttribute(k_final_tiles<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)h->smem_final)
+                                                optin)
                          : cudaFuncSetAttribute(k_final_tiles<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)h->smem_final);
-    if (e1 != cudaSuccess || e2 != cudaSuccess) h->tiles = false;
+                                                optin);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || (size_t)optin < std::max(h->smem_scatter, h->smem_final)) {
+      (void)cudaGetLastError();
+      h->tiles = false;
+    }
   }
   if (h->precision == PLACE3D_FP32_TC) {
     std::string why;
@@ -1858,51 +1877,62 @@ int place3d_batch_create(place3d_handle *const *handles, int count, place3d_batc
 
 int place3d_batch_eval(place3d_batch *b, const void *const *xs, const void *const *ys, const void *const *zs,
                        void *const *gxs, void *const *gys, void *const *gzs, int dtype, void *cuda_stream) {
-  if (!b || !xs || !ys || !zs || !gxs || !gys || !gzs) return PLACE3D_ERR_INVALID_ARG;
-  if (dtype != PLACE3D_F64 && dtype != PLACE3D_F32) return PLACE3D_ERR_INVALID_ARG;
-  if (cudaSetDevice(b->device) != cudaSuccess) return PLACE3D_ERR_CUDA;
+  if (!b || !xs || !ys || !zs || !gxs || !gys || !gzs) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL argument");
+  if (dtype != PLACE3D_F64 && dtype != PLACE3D_F32) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "bad dtype");
+  P3D_CUDA(nullptr, cudaSetDevice(b->device));
   const int n = (int)b->hs.size();
   std::vector<const void *> ptr;
   for (int i = 0; i < n; ++i) {
     const void *pi[6] = {xs[i], ys[i], zs[i], gxs[i], gys[i], gzs[i]};
     for (int k = 0; k < 6; ++k) {
-      if (!pi[k]) return PLACE3D_ERR_INVALID_ARG;
+      if (!pi[k]) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL instance array");
       ptr.push_back(pi[k]);
     }
   }
   std::vector<unsigned> vers;
   for (auto *h : b->hs) vers.push_back(h->version);
   if (!b->exec || b->dtype != dtype || b->ptrs != ptr || b->versions != vers) {
-    for (auto *h : b->hs)
-      if (cudaStreamSynchronize(h->stream) != cudaSuccess) return PLACE3D_ERR_CUDA;
-    if (cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PLACE3D_ERR_CUDA;
-    int rc = cudaEventRecord(b->fork, b->root) == cudaSuccess ? PLACE3D_OK : PLACE3D_ERR_CUDA;
+    for (auto *h : b->hs) P3D_CUDA(nullptr, cudaStreamSynchronize(h->stream));
+    P3D_CUDA(nullptr, cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal));
+    int rc = PLACE3D_OK;
+    std::string why;
+    cudaError_t ce = cudaEventRecord(b->fork, b->root);
+    if (ce != cudaSuccess) {
+      rc = PLACE3D_ERR_CUDA;
+      why = std::string("cudaEventRecord(fork): ") + cudaGetErrorString(ce);
+    }
     for (int i = 0; i < n && rc == PLACE3D_OK; ++i) {
-      if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) {
+      if ((ce = cudaStreamWaitEvent(b->streams[i], b->fork, 0)) != cudaSuccess) {
         rc = PLACE3D_ERR_CUDA;
+        why = std::string("cudaStreamWaitEvent(fork): ") + cudaGetErrorString(ce);
         break;
       }
       rc = capture_eval(b->hs[i], b->streams[i], &ptr[6 * i], dtype);
-      if (rc == PLACE3D_OK && (cudaEventRecord(b->done[i], b->streams[i]) != cudaSuccess ||
-                               cudaStreamWaitEvent(b->root, b->done[i], 0) != cudaSuccess))
+      if (rc != PLACE3D_OK) {
+        why = "instance " + std::to_string(i) + ": " + b->hs[i]->err;
+        break;
+      }
+      if ((ce = cudaEventRecord(b->done[i], b->streams[i])) != cudaSuccess ||
+          (ce = cudaStreamWaitEvent(b->root, b->done[i], 0)) != cudaSuccess) {
         rc = PLACE3D_ERR_CUDA;
+        why = std::string("joining instance ") + std::to_string(i) + ": " + cudaGetErrorString(ce);
+      }
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(b->root, &graph);
     if (rc != PLACE3D_OK || e != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
-      return rc != PLACE3D_OK ? rc : PLACE3D_ERR_CUDA;
+      if (rc != PLACE3D_OK) return fail(nullptr, rc, "batch capture: " + why);
+      return cuda_fail(nullptr, e, "cudaStreamEndCapture (batch)");
     }
-    if (install_graph(&b->exec, graph) != cudaSuccess) return PLACE3D_ERR_CUDA;
+    P3D_CUDA(nullptr, install_graph(&b->exec, graph));
     b->ptrs = ptr;
     b->versions = vers;
     b->dtype = dtype;
   }
   // density weights written by set_params on the handles' streams come first
-  for (auto *h : b->hs)
-    if (cudaStreamWaitEvent(static_cast<cudaStream_t>(cuda_stream), h->ev_param, 0) != cudaSuccess)
-      return PLACE3D_ERR_CUDA;
-  if (cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(cuda_stream)) != cudaSuccess) return PLACE3D_ERR_CUDA;
+  for (auto *h : b->hs) P3D_CUDA(nullptr, cudaStreamWaitEvent(static_cast<cudaStream_t>(cuda_stream), h->ev_param, 0));
+  P3D_CUDA(nullptr, cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(cuda_stream)));
   for (auto *h : b->hs) {
     h->have_result = true;
     h->gout_fresh = false;

@@ -21,7 +21,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_tc": FP32_TC}
 F64, F32 = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
 FLAG_CHECKS = 1
-FLAG_MACRO_GATHER_SCAN, FLAG_MACRO_GATHER_DIRECT, FLAG_SERIAL, FLAG_TILES = 2, 4, 8, 16
+FLAG_MACRO_GATHER_SCAN, FLAG_MACRO_GATHER_DIRECT, FLAG_SERIAL, FLAG_TILES, FLAG_NO_TILES = 2, 4, 8, 16, 32
 WL_FORMS = ((1, 1), (1, 2), (1, 4), (2, 2), (4, 1), (2, 4), (8, 1), (4, 4), (16, 1), (8, 4), (32, 1), (16, 4), (32, 2),
             (32, 4))
 MAP_RHO_FIXED, MAP_EX, MAP_EY, MAP_EZ = 0, 1, 2, 3
@@ -467,7 +467,7 @@ class Batch:
             stream = stream.cuda_stream
         rc = self._L.place3d_batch_eval(self._b, *arrs, dts.pop(), C.c_void_p(stream or 0))
         if rc != 0:
-            raise Place3DError(rc, "place3d_batch_eval failed")
+            raise Place3DError(rc, "place3d_batch_eval: " + self._L.place3d_last_error(None).decode())
 
     def close(self):
         if getattr(self, "_b", None):

@@ -33,14 +33,18 @@ def test_profiled_traffic_is_keyed_to_the_sources(tmp_path, monkeypatch):
     t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     e = t["cells_1m"]["fp32_tc"]["wirelength"]
     assert set(e["sources"]) and e["bytes_per_eval"] > 0
-    # a copy of the repository layout with one listed source changed: the lookup returns None
+    # a copy of the repository layout whose entry is keyed to the copied
+    # sources: the lookup returns the bytes; one listed source changed: None
+    import hashlib
     prof = tmp_path / "profiles"
     prof.mkdir()
-    (prof / "traffic.json").write_text(json.dumps(t))
     for path in e["sources"]:
         dst = tmp_path / path
         dst.parent.mkdir(parents=True, exist_ok=True)
-        dst.write_bytes(open(os.path.join(ROOT, path), "rb").read())
+        data = open(os.path.join(ROOT, path), "rb").read()
+        dst.write_bytes(data)
+        e["sources"][path] = hashlib.sha256(data).hexdigest()
+    (prof / "traffic.json").write_text(json.dumps(t))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench._profiled_traffic("wirelength", "cells_1m", "fp32_tc") == e["bytes_per_eval"]
     first = next(iter(e["sources"]))

@@ -220,21 +220,44 @@ def test_every_reduction_form(precision):
             h.set_wl_form(bi, G, ppl)
 
 
-@pytest.mark.parametrize("kind", ["default", "outside", "hifanout", "zfixed"])
-def test_tile_bucketed_scatter_gather_path(kind):
-    """The shared-memory tile scatter/gather (PLACE3D_FLAG_TILES) matches the
-    oracle like the default per-cell path (bit-exact map included)."""
+@pytest.mark.parametrize("kind", ["default", "outside", "hifanout", "zfixed", "nz1"])
+def test_per_cell_scatter_gather_path(kind):
+    """The per-cell scatter/gather (PLACE3D_FLAG_NO_TILES: one thread per
+    cell, global int64 atomics and field loads) matches the oracle like the
+    default tile-sorted path (bit-exact map included)."""
     p, x, y, z = _edge(kind)
-    _check_fp64(p, x, y, z, flags=16)
-    _check_fp32(p, x, y, z, flags=16)
+    _check_fp64(p, x, y, z, flags=32)
+    _check_fp32(p, x, y, z, flags=32)
 
 
 @pytest.mark.parametrize("positions", ["uniform", "center"])
-def test_tiles_cells_200k_fp64(positions):
-    """Tile-bucketed path at 256x256x4 with clustered and uniform cells."""
+def test_per_cell_path_cells_200k(positions):
+    """The per-cell path at 256x256x4 with clustered and uniform cells."""
     p = synth.make_problem("cells_200k", positions=positions)
-    _check_fp64(p, p["x"], p["y"], p["z"], maps=True, flags=16)
-    _check_fp32(p, p["x"], p["y"], p["z"], flags=16)
+    _check_fp64(p, p["x"], p["y"], p["z"], maps=True, flags=32)
+    _check_fp32(p, p["x"], p["y"], p["z"], flags=32)
+
+
+def test_tiles_with_wide_cells():
+    """A few cells 7 bins wide among 1-2-bin ones: the tile windows' halo
+    grows to 4 bins and the map stays bit-exact."""
+    rng = np.random.default_rng(3)
+    die = (0.0, 0.0, 400.0, 300.0)
+    grid = (80, 60, 2)
+    n = 600
+    sizes = [(float(rng.integers(1, 9)), 1.0, 0.0, 0.0) for _ in range(n)]
+    sizes = [(w, h, 0.8 * w, 0.8 * h) for (w, h, _, _) in sizes]
+    for k in range(0, n, 97):
+        sizes[k] = (35.0, 2.0, 28.0, 1.6)  # 7 bins wide: halo 4
+    nets = [list(rng.choice(n, size=int(rng.integers(2, 6)), replace=False)) for _ in range(700)]
+    P_ = sum(len(e) for e in nets)
+    p = problem(sizes, nets=nets, offsets=np.zeros((P_, 4)), die=die, grid=grid, gamma=20.0)
+    dz = dz_of(p)
+    x = rng.uniform(die[0], die[2], n)
+    y = rng.uniform(die[1], die[3], n)
+    z = rng.uniform(dz / 4, 3 * dz / 4, n)
+    _check_fp64(p, x, y, z)
+    _check_fp32(p, x, y, z)
 
 
 # ---- dummy fillers (Sec. III-A): pinless instances, z-fixed ones with a zero z-gradient ----
