@@ -129,6 +129,14 @@ struct place3d_handle {
   void *stage_in = nullptr;  // staging for host positions [3][n] doubles
   int *check_flag = nullptr;
   std::vector<Bucket> buckets;
+  // nets above 128 pins split into chunks (k_wl_big_*): chunk and net
+  // tables, per-net pass counters, per-chunk partial and per-net merged
+  // extremes (NetExt) and WA sums (Sums) in the handle's precision
+  int4 *big_chunk = nullptr;
+  int2 *big_net = nullptr;
+  int *big_done = nullptr;
+  void *big_ext_part = nullptr, *big_sum_part = nullptr, *big_ext = nullptr, *big_sums = nullptr;
+  int big_nchunks = 0, big_nnets = 0;
   // tensor-core transform state (FP32_TC)
   p3d_tc::TcPlan *tc = nullptr;
   // CUDA graph of one evaluation (place3d_eval_graph)
@@ -357,8 +365,17 @@ template <typename T>
 int launch_wl(place3d_handle *h, const Bucket &b, int G, int PPL, cudaStream_t w, const WlC<T> &c, T *part) {
   V4<T> *acc = as<V4<T>>(h->acc);
   const V4<T> *pos = as<V4<T>>(h->pos), *off = as<V4<T>>(h->off);
-  if (G == 0) {
-    k_wl_block<T><<<b.count, 256, 0, w>>>(b.first, h->net_start, h->pin_inst, off, pos, c, acc, h->scal);
+  if (G == 0) {  // nets above 128 pins: three passes over their chunks
+    const WlBig bg{h->big_chunk, h->big_net, h->big_done};
+    const int nc = h->big_nchunks;
+    k_wl_big_ext<T><<<nc, 256, 0, w>>>(bg, h->net_start, h->pin_inst, off, pos, c, as<NetExt<T>>(h->big_ext_part),
+                                       as<NetExt<T>>(h->big_ext));
+    k_wl_big_sums<T><<<nc, 256, 0, w>>>(bg, h->pin_inst, off, pos, c, as<NetExt<T>>(h->big_ext),
+                                        as<Sums<T>>(h->big_sum_part), as<Sums<T>>(h->big_sums), h->scal);
+    k_wl_big_out<T><<<nc, 256, 0, w>>>(bg, h->net_start, h->pin_inst, off, pos, c, as<NetExt<T>>(h->big_ext),
+                                       as<Sums<T>>(h->big_sums), acc);
+    count_launch(h, ST_WIRELENGTH);
+    count_launch(h, ST_WIRELENGTH);
     return 0;
   }
   if (G == 1 && PPL == 1) {  // 2-pin nets, closed form
@@ -740,7 +757,8 @@ void free_all(place3d_handle *h) {
                   h->szpsi, h->xinv, h->x2, h->e4, h->mats, h->suffix, h->mgrad,
                   h->scal, h->zc, h->gout, h->stage_in, h->check_flag, h->tkey, h->titems,
                   h->part_w, h->part_d, h->d_lam, h->npins, h->nest, h->part_n,
-                  h->tcount, h->tstart, h->tnitems, h->trec, h->g4};
+                  h->tcount, h->tstart, h->tnitems, h->trec, h->g4, h->big_chunk, h->big_net,
+                  h->big_done, h->big_ext_part, h->big_sum_part, h->big_ext, h->big_sums};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (h->tc) p3d_tc::destroy(h->tc);
@@ -1082,6 +1100,38 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
         p3d_malloc((void **)&h->part_d, sizeof(double) * 3 * rd) != cudaSuccess) {
       fail(h, PLACE3D_ERR_OOM, "cudaMalloc (partial-sum rows)");
       return bail(PLACE3D_ERR_OOM);
+    }
+  }
+  // chunks of the nets above 128 pins (the block-form bucket, G = 0)
+  for (const Bucket &b : h->buckets) {
+    if (b.G != 0) continue;
+    std::vector<int4> chunks;
+    std::vector<int2> nets;
+    for (int t = 0; t < b.count; ++t) {
+      const int e = b.first + t, s0 = new_start[e], d = new_start[e + 1] - s0;
+      const int nch = (d + kWlChunk - 1) / kWlChunk;
+      nets.push_back(make_int2((int)chunks.size(), nch));
+      for (int k = 0; k < nch; ++k) chunks.push_back(make_int4(e, s0 + k * kWlChunk, std::min(kWlChunk, d - k * kWlChunk), t));
+    }
+    h->big_nchunks = (int)chunks.size();
+    h->big_nnets = (int)nets.size();
+    const size_t ne = h->precision == PLACE3D_FP64 ? sizeof(NetExt<double>) : sizeof(NetExt<float>);
+    const size_t ns = h->precision == PLACE3D_FP64 ? sizeof(Sums<double>) : sizeof(Sums<float>);
+    if (p3d_malloc((void **)&h->big_chunk, sizeof(int4) * chunks.size()) != cudaSuccess ||
+        p3d_malloc((void **)&h->big_net, sizeof(int2) * nets.size()) != cudaSuccess ||
+        p3d_malloc((void **)&h->big_done, sizeof(int) * nets.size()) != cudaSuccess ||
+        p3d_malloc(&h->big_ext_part, ne * chunks.size()) != cudaSuccess ||
+        p3d_malloc(&h->big_sum_part, ns * chunks.size()) != cudaSuccess ||
+        p3d_malloc(&h->big_ext, ne * nets.size()) != cudaSuccess ||
+        p3d_malloc(&h->big_sums, ns * nets.size()) != cudaSuccess) {
+      fail(h, PLACE3D_ERR_OOM, "cudaMalloc (high-fanout net chunks)");
+      return bail(PLACE3D_ERR_OOM);
+    }
+    if (cudaMemcpy(h->big_chunk, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->big_net, nets.data(), sizeof(int2) * nets.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(h->big_done, 0, sizeof(int) * nets.size()) != cudaSuccess) {
+      fail(h, PLACE3D_ERR_CUDA, "upload failed");
+      return bail(PLACE3D_ERR_CUDA);
     }
   }
   int prio_lo = 0, prio_hi = 0;

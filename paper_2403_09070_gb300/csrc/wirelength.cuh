@@ -687,56 +687,130 @@ __global__ void __launch_bounds__(wl_block<T>()) k_wl_group(int net0, int nnets,
   warp_sum_part<4>(vals, part);  // (W^_Bi, p^(z), W_Bi, crossing) rows
 }
 
-// ---- high-fanout nets: one block (256 threads) per net, three passes ----
+// ---- high-fanout nets, split across blocks ----
+// A net above 128 pins is cut into chunks of at most kWlChunk pins, one
+// 256-thread block per chunk, in three passes (three launches): the 1st/2nd
+// extremes, the WA sums, the per-pin outputs.  Each block of a pass writes
+// its chunk's partial result; the net's last block to finish the pass (an
+// atomic counter per net after a memory fence: no block ever waits for
+// another) merges the net's partials in chunk order, so the merged values do
+// not depend on the blocks' timing, and resets the counter for the next pass.
+constexpr int kWlChunk = 1024;
+
+struct WlBig {
+  const int4 *chunk;  // [chunks]: (net in the reordered CSR, first pin, pin count, big-net slot)
+  const int2 *net;    // [big nets]: (first chunk, chunk count)
+  int *done;          // [big nets]: chunks finished in the current pass (0 between passes)
+};
+
+// A POD struct read through the L2 (another block's partial result).
+template <typename S> __device__ __forceinline__ S ld_l2(const S *p) {
+  static_assert(sizeof(S) % 4 == 0, "word-sized struct");
+  S r;
+  const unsigned *src = reinterpret_cast<const unsigned *>(p);
+  unsigned *dst = reinterpret_cast<unsigned *>(&r);
+#pragma unroll
+  for (int k = 0; k < (int)(sizeof(S) / 4); ++k) dst[k] = __ldcg(src + k);
+  return r;
+}
+
+// Counts this block's chunk as done; true in the net's last block (which
+// then sees every other chunk's partial result).
+__device__ __forceinline__ bool big_last_block(const WlBig &bg, int slot, int nch) {
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(bg.done + slot, 1) == nch - 1;
+    if (last) {
+      __threadfence();
+      bg.done[slot] = 0;
+    }
+  }
+  __syncthreads();
+  return last != 0;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_wl_block(int net0, const int *__restrict__ net_start,
-                                                  const int *__restrict__ pin_inst,
-                                                  const V4<T> *__restrict__ off,
-                                                  const V4<T> *__restrict__ pos, WlC<T> c,
-                                                  V4<T> *__restrict__ acc, double *__restrict__ scal) {
+__global__ void __launch_bounds__(256) k_wl_big_ext(WlBig bg, const int *__restrict__ net_start,
+                                                    const int *__restrict__ pin_inst, const V4<T> *__restrict__ off,
+                                                    const V4<T> *__restrict__ pos, WlC<T> c,
+                                                    NetExt<T> *__restrict__ ext_part, NetExt<T> *__restrict__ ext) {
   __shared__ NetExt<T> sx[8];
-  __shared__ Sums<T> ss[8];
-  const int e = net0 + blockIdx.x;
-  const int s0 = net_start[e], d = net_start[e + 1] - s0;
+  const int4 ch = bg.chunk[blockIdx.x];
+  const int s0 = net_start[ch.x];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   NetExt<T> X;
   X.init();
-  for (int k = tid; k < d; k += blockDim.x) X.add(load_pin(s0 + k, pin_inst, off, pos, c), k);
+  for (int k = tid; k < ch.z; k += blockDim.x) X.add(load_pin(ch.y + k, pin_inst, off, pos, c), ch.y + k - s0);
   X.template shfl_reduce<32>();
   if (lane == 0) sx[warp] = X;
   __syncthreads();
   if (tid == 0) {
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) sx[0].merge(sx[w]);
+    ext_part[blockIdx.x] = sx[0];
   }
-  __syncthreads();
-  X = sx[0];
+  const int2 nt = bg.net[ch.w];
+  if (big_last_block(bg, ch.w, nt.y) && tid == 0) {
+    NetExt<T> m = ld_l2(ext_part + nt.x);
+    for (int k = 1; k < nt.y; ++k) m.merge(ld_l2(ext_part + nt.x + k));
+    ext[ch.w] = m;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_wl_big_sums(WlBig bg, const int *__restrict__ pin_inst,
+                                                     const V4<T> *__restrict__ off, const V4<T> *__restrict__ pos,
+                                                     WlC<T> c, const NetExt<T> *__restrict__ ext,
+                                                     Sums<T> *__restrict__ sum_part, Sums<T> *__restrict__ sums,
+                                                     double *__restrict__ scal) {
+  __shared__ Sums<T> ss[8];
+  const int4 ch = bg.chunk[blockIdx.x];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const NetExt<T> X = ext[ch.w];
   Sums<T> S;
   S.init();
-  for (int k = tid; k < d; k += blockDim.x) pin_sums(S, load_pin(s0 + k, pin_inst, off, pos, c), X, c);
+  for (int k = tid; k < ch.z; k += blockDim.x) pin_sums(S, load_pin(ch.y + k, pin_inst, off, pos, c), X, c);
   S.template shfl_reduce<32>();
   if (lane == 0) ss[warp] = S;
   __syncthreads();
   if (tid == 0) {
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) ss[0].merge(ss[w]);
+    sum_part[blockIdx.x] = ss[0];
   }
-  __syncthreads();
-  S = ss[0];
+  const int2 nt = bg.net[ch.w];
+  if (big_last_block(bg, ch.w, nt.y) && tid == 0) {
+    Sums<T> m = ld_l2(sum_part + nt.x);
+    for (int k = 1; k < nt.y; ++k) m.merge(ld_l2(sum_part + nt.x + k));
+    sums[ch.w] = m;
+    const NetScal<T> N = net_scalars(X, m, c);
+    atomicAdd(scal + S_WL_BI, (double)N.ax[0].what + (double)N.ax[1].what);
+    if (!c.mode2d) atomicAdd(scal + S_WL_Z, (double)N.pz);
+    atomicAdd(scal + S_HPWL, (double)N.wcur);
+    if (X.ntop > 0 && X.ntop < X.n) atomicAdd(scal + S_NCROSS, 1.0);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_wl_big_out(WlBig bg, const int *__restrict__ net_start,
+                                                    const int *__restrict__ pin_inst, const V4<T> *__restrict__ off,
+                                                    const V4<T> *__restrict__ pos, WlC<T> c,
+                                                    const NetExt<T> *__restrict__ ext,
+                                                    const Sums<T> *__restrict__ sums, V4<T> *__restrict__ acc) {
+  const int4 ch = bg.chunk[blockIdx.x];
+  const int s0 = net_start[ch.x];
+  const NetExt<T> X = ext[ch.w];
+  const Sums<T> S = sums[ch.w];
   const NetScal<T> N = net_scalars(X, S, c);
-  for (int k = tid; k < d; k += blockDim.x) {
-    const Pin<T> p = load_pin(s0 + k, pin_inst, off, pos, c);
+  for (int k = threadIdx.x; k < ch.z; k += blockDim.x) {
+    const Pin<T> p = load_pin(ch.y + k, pin_inst, off, pos, c);
     if (c.mode2d) {
       pin_outputs_2d(p, X, N, c, acc);
     } else {
       T ex[6];
       pin_exps(p, X, c, ex, p.top);
-      pin_outputs(p, k, ex, X, S, N, c, acc);
+      pin_outputs(p, ch.y + k - s0, ex, X, S, N, c, acc);
     }
-  }
-  if (tid == 0) {
-    atomicAdd(scal + S_WL_BI, (double)N.ax[0].what + (double)N.ax[1].what);
-    if (!c.mode2d) atomicAdd(scal + S_WL_Z, (double)N.pz);
-    atomicAdd(scal + S_HPWL, (double)N.wcur);
-    if (X.ntop > 0 && X.ntop < X.n) atomicAdd(scal + S_NCROSS, 1.0);
   }
 }
 

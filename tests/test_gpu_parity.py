@@ -260,6 +260,44 @@ def test_tiles_with_wide_cells():
     _check_fp32(p, x, y, z)
 
 
+def _with_big_nets(sizes=(300, 1500, 2004), seed=9):
+    """cells_2k plus nets of the given pin counts on distinct instances (the
+    largest covers every instance): nets above 128 pins are split into
+    chunks of 1,024 pins, so these take one, two and two chunks."""
+    p = synth.make_problem("cells_2k")
+    rng = np.random.default_rng(seed)
+    n = p["n_inst"]
+    ns = list(np.asarray(p["net_start"], np.int64))
+    pins = list(np.asarray(p["pin_inst"], np.int64))
+    offs = [list(np.asarray(p[k], np.float64)) for k in ("off_bx", "off_by", "off_tx", "off_ty")]
+    for d in sizes:
+        inst = rng.choice(n, size=d, replace=False)
+        ox = rng.uniform(-0.5, 0.5, d)
+        oy = rng.uniform(-0.4, 0.4, d)
+        pins += list(inst)
+        for lst, v in zip(offs, (ox, oy, 0.8 * ox, 0.8 * oy)):
+            lst += list(v)
+        ns.append(ns[-1] + d)
+    q = dict(p)
+    q["net_start"] = np.asarray(ns, np.int32)
+    q["pin_inst"] = np.asarray(pins, np.int32)
+    for k, lst in zip(("off_bx", "off_by", "off_tx", "off_ty"), offs):
+        q[k] = np.asarray(lst, np.float64)
+    q["n_net"] = len(ns) - 1
+    q["n_pin"] = int(ns[-1])
+    return q
+
+
+def test_high_fanout_nets_split_across_blocks():
+    """Nets of 300, 1,500 and 2,004 pins, each split into 1,024-pin chunks
+    handled by separate blocks whose partial extremes and WA sums are merged
+    per net: FP64 within 1e-9 of the oracle (incremental FD included, which
+    needs the exact 1st/2nd extremes across chunks), FP32 within its bar."""
+    q = _with_big_nets()
+    _check_fp64(q, q["x"], q["y"], q["z"])
+    _check_fp32(q, q["x"], q["y"], q["z"])
+
+
 # ---- dummy fillers (Sec. III-A): pinless instances, z-fixed ones with a zero z-gradient ----
 def _with_fillers(wl, u, positions, seed=5):
     from oracle import Oracle
