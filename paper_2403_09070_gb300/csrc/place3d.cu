@@ -378,9 +378,10 @@ int launch_wl(place3d_handle *h, const Bucket &b, int G, int PPL, cudaStream_t w
     count_launch(h, ST_WIRELENGTH);
     return 0;
   }
-  if (G == 1 && PPL == 1) {  // 2-pin nets, closed form
-    k_wl_pair<T><<<grid_for(b.count, 256), 256, 0, w>>>(b.pin0, b.count, h->pin_inst, off, pos, c, acc, part);
-    return grid_for(b.count, 256) * (256 / 32);
+  if (G == 1 && PPL == 1) {  // 2-pin nets, closed form, kPairNets nets per thread
+    const int gr = grid_for(b.count, 256 * kPairNets);
+    k_wl_pair<T><<<gr, 256, 0, w>>>(b.pin0, b.count, h->pin_inst, off, pos, c, acc, part);
+    return gr * (256 / 32);
   }
   constexpr int BS = wl_block<T>();
   const int blocks = grid_for((long long)b.count * G, BS);

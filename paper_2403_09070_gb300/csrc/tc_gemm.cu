@@ -33,15 +33,14 @@
 namespace p3d_tc {
 using namespace p3d;
 
-// Pipeline depth: 4 stages (193 KiB of shared memory, one CTA per SM) when
-// a launch has at most one tile per SM; 2 stages (97 KiB, two CTAs per SM,
-// and room beside the wirelength kernels running concurrently) otherwise.
+// Pipeline depth: 4 stages (193 KiB of shared memory, one persistent CTA
+// per SM).
 constexpr int BM = 128, BN = 64, BK = 64;
 constexpr int A_BYTES = BM * BK * 2;                    // one BF16 plane of an A tile (16 KiB)
 constexpr int W_BYTES = BN * BK * 2;                    // one BF16 plane of a W tile (8 KiB)
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * W_BYTES;  // 48 KiB
 template <int STAGES> constexpr int smem_bytes() { return STAGES * STAGE_BYTES + 1024; }
-constexpr int TMEM_COLS = BN;                           // FP32 accumulator columns
+constexpr int TMEM_COLS = BN;                           // FP32 accumulator columns of one buffer (two are allocated)
 constexpr long long kWaitCycles = 4000000000LL;         // about 2 s at 2 GHz
 
 enum { OUT_F32 = 0, OUT_SPLIT = 1 };
@@ -173,35 +172,57 @@ __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, vola
 }
 
 // ------------------------------------------------------------------ kernel
-template <int STAGES>
-__global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Group g) {
-  extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t bars[2 * STAGES + 1];
-  __shared__ uint32_t tmem_slot;
-  __shared__ int abort_flag;
-  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  int tile = blockIdx.x, pi = 0;
+// Persistent: CTA c takes tiles c, c + gridDim.x, ... of the group.  The
+// shared-memory pipeline runs continuously across a CTA's tiles (k-block
+// counter `it`), and the accumulator is double-buffered in tensor memory
+// (2 x BN columns): the MMA thread fills buffer j & 1 for the CTA's j-th
+// tile while the epilogue warps drain the other, so one tile's epilogue
+// overlaps the next tile's loads and MMAs.  acc_full[b] (MMA commit ->
+// epilogue) and acc_empty[b] (four epilogue warps -> MMA) hand the buffers
+// over.
+__device__ __forceinline__ void tile_coords(const Group &g, int tile, int &pi, int &b, int &m0, int &n0) {
+  pi = 0;
   while (pi + 1 < g.count && tile >= g.tile_start[pi + 1]) ++pi;
   const Prob &P = g.p[pi];
   tile -= g.tile_start[pi];
   const int per_b = P.tiles_m * P.tiles_n;
-  const int b = tile / per_b, r = tile - (tile / per_b) * per_b;
-  const int m0 = (r % P.tiles_m) * BM, n0 = (r / P.tiles_m) * BN;
-  const int nk = P.K / BK;
+  b = tile / per_b;
+  const int r = tile - b * per_b;
+  m0 = (r % P.tiles_m) * BM;
+  n0 = (r / P.tiles_m) * BN;
+}
 
-  const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[STAGES]), accf = smem_u32(&bars[2 * STAGES]);
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <int STAGES>
+__global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Group g) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2 * STAGES + 5];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = g.tile_start[g.count];
+
+  const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[STAGES]);
+  const uint32_t accf0 = smem_u32(&bars[2 * STAGES]), acce0 = smem_u32(&bars[2 * STAGES + 2]);
+  const uint32_t done = smem_u32(&bars[2 * STAGES + 4]);
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(accf, 1);
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(accf0 + 8 * k, 1);
+      mbar_init(acce0 + 8 * k, 4);  // one arrival per epilogue warp
+    }
+    mbar_init(done, 1);
     abort_flag = 0;
     fence_barrier_init();
   }
-  if (warp == 1) tmem_alloc(smem_u32(&tmem_slot), TMEM_COLS);
+  if (warp == 1) tmem_alloc(smem_u32(&tmem_slot), 2 * TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -211,21 +232,30 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Grou
   if (warp == 0) {
     if (lane == 0) {
       // ---- TMA producer ----
-      const CUtensorMap *am = &g.amap[pi], *wm = &g.wmap[pi];
-      int issued = 0;
-      for (int kb = 0; kb < (g.skip_loads ? 0 : nk); ++kb) {
-        const int s = kb % STAGES, round = kb / STAGES;
-        if (kb >= STAGES && !wait_bounded(empty0 + 8 * s, (round - 1) & 1, abort_p, g.err, ERR_EMPTY, g.wait_cycles))
-          break;
-        const uint32_t st = smem_u32(smem + s * STAGE_BYTES), fb = full0 + 8 * s;
-        mbar_expect_tx(fb, STAGE_BYTES);
-        tma_load_4d(am, st, fb, kb * BK, m0, b, 0);
-        tma_load_4d(am, st + A_BYTES, fb, kb * BK, m0, b, 1);
-        tma_load_3d(wm, st + 2 * A_BYTES, fb, kb * BK, n0, 0);
-        tma_load_3d(wm, st + 2 * A_BYTES + W_BYTES, fb, kb * BK, n0, 1);
-        issued = kb + 1;
+      int it = 0;
+      bool stop = false;
+      for (int tile = blockIdx.x; tile < ntiles && !stop && !g.skip_loads; tile += gridDim.x) {
+        int pi, b, m0, n0;
+        tile_coords(g, tile, pi, b, m0, n0);
+        const CUtensorMap *am = &g.amap[pi], *wm = &g.wmap[pi];
+        const int nk = g.p[pi].K / BK;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % STAGES, round = it / STAGES;
+          if (it >= STAGES &&
+              !wait_bounded(empty0 + 8 * s, (round - 1) & 1, abort_p, g.err, ERR_EMPTY, g.wait_cycles)) {
+            stop = true;
+            break;
+          }
+          const uint32_t st = smem_u32(smem + s * STAGE_BYTES), fb = full0 + 8 * s;
+          mbar_expect_tx(fb, STAGE_BYTES);
+          tma_load_4d(am, st, fb, kb * BK, m0, b, 0);
+          tma_load_4d(am, st + A_BYTES, fb, kb * BK, m0, b, 1);
+          tma_load_3d(wm, st + 2 * A_BYTES, fb, kb * BK, n0, 0);
+          tma_load_3d(wm, st + 2 * A_BYTES + W_BYTES, fb, kb * BK, n0, 1);
+        }
       }
       // every armed stage's last copy must have landed before the CTA exits
+      const int issued = it;
       for (int s = 0; s < STAGES && s < issued; ++s) {
         const int last = s + ((issued - 1 - s) / STAGES) * STAGES;
         const long long t0 = clock64();
@@ -236,60 +266,92 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Grou
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer ----
-      for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % STAGES, round = kb / STAGES;
-        if (!wait_bounded(full0 + 8 * s, round & 1, abort_p, g.err, ERR_FULL, g.wait_cycles)) break;
+      int it = 0, j = 0;
+      bool stop = false;
+      for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x, ++j) {
+        int pi, b, m0, n0;
+        tile_coords(g, tile, pi, b, m0, n0);
+        const int nk = g.p[pi].K / BK;
+        const int buf = j & 1;
+        if (j >= 2 && !wait_bounded(acce0 + 8 * buf, ((j >> 1) - 1) & 1, abort_p, g.err, ERR_ACC, g.wait_cycles))
+          break;
         tc_fence_after();
-        const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES), a_lo = a_hi + A_BYTES;
-        const uint32_t w_hi = a_hi + 2 * A_BYTES, w_lo = w_hi + W_BYTES;
+        const uint32_t td = tmem + (uint32_t)(buf * TMEM_COLS);
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % STAGES, round = it / STAGES;
+          if (!wait_bounded(full0 + 8 * s, round & 1, abort_p, g.err, ERR_FULL, g.wait_cycles)) {
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES), a_lo = a_hi + A_BYTES;
+          const uint32_t w_hi = a_hi + 2 * A_BYTES, w_lo = w_hi + W_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint64_t dah = desc_k_sw128(a_hi + kk * 32), dal = desc_k_sw128(a_lo + kk * 32);
-          const uint64_t dwh = desc_k_sw128(w_hi + kk * 32), dwl = desc_k_sw128(w_lo + kk * 32);
-          mma_bf16(tmem, dah, dwh, kIdesc, (kb | kk) != 0);
-          mma_bf16(tmem, dah, dwl, kIdesc, 1u);
-          mma_bf16(tmem, dal, dwh, kIdesc, 1u);
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t dah = desc_k_sw128(a_hi + kk * 32), dal = desc_k_sw128(a_lo + kk * 32);
+            const uint64_t dwh = desc_k_sw128(w_hi + kk * 32), dwl = desc_k_sw128(w_lo + kk * 32);
+            mma_bf16(td, dah, dwh, kIdesc, (kb | kk) != 0);
+            mma_bf16(td, dah, dwl, kIdesc, 1u);
+            mma_bf16(td, dal, dwh, kIdesc, 1u);
+          }
+          mma_commit(empty0 + 8 * s);  // frees the stage once these MMAs have read it
         }
-        mma_commit(empty0 + 8 * s);  // frees the stage once these MMAs have read it
+        mma_commit(accf0 + 8 * buf);  // this tile's accumulator is complete (also after an abort)
       }
-      mma_commit(accf);  // accumulator complete (also after an abort, so nobody waits forever)
+      mma_commit(done);  // every MMA this CTA issued has completed
     }
   } else {
     // ---- epilogue: TMEM -> registers -> global, transposed ----
-    const bool ok = wait_bounded(accf, 0, abort_p, g.err, ERR_ACC, g.wait_cycles);
-    tc_fence_after();
     const int q = warp & 3;  // this warp's TMEM lane quarter
-    const int m = m0 + q * 32 + lane;
-    const long long base = (long long)b * P.o_bstride + m;
+    int j = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
+      int pi, b, m0, n0;
+      tile_coords(g, tile, pi, b, m0, n0);
+      const Prob &P = g.p[pi];
+      const int buf = j & 1;
+      if (!wait_bounded(accf0 + 8 * buf, (j >> 1) & 1, abort_p, g.err, ERR_ACC, g.wait_cycles)) break;
+      tc_fence_after();
+      const int m = m0 + q * 32 + lane;
+      const long long base = (long long)b * P.o_bstride + m;
+      const uint32_t ta = tmem + (uint32_t)(buf * TMEM_COLS) + ((uint32_t)(q * 32) << 16);
 #pragma unroll
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      uint32_t v[16];
-      tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-      if (!ok || *abort_p) continue;
-      if (P.kind == OUT_F32) {
-        float *o = static_cast<float *>(P.out);
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t v[16];
+        tmem_ld16(ta + (uint32_t)c0, v);
+        if (P.kind == OUT_F32) {
+          float *o = static_cast<float *>(P.out);
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          o[(base + (long long)(n0 + c0 + j) * P.M) * P.ostride] = __uint_as_float(v[j]);
-      } else {
-        __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(P.out);
+          for (int jj = 0; jj < 16; ++jj)
+            o[(base + (long long)(n0 + c0 + jj) * P.M) * P.ostride] = __uint_as_float(v[jj]);
+        } else {
+          __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(P.out);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float f = __uint_as_float(v[j]);
-          const __nv_bfloat16 h = __float2bfloat16_rn(f);
-          const long long id = base + (long long)(n0 + c0 + j) * P.M;
-          o[id] = h;
-          o[id + P.plane] = __float2bfloat16_rn(f - __bfloat162float(h));
+          for (int jj = 0; jj < 16; ++jj) {
+            const float f = __uint_as_float(v[jj]);
+            const __nv_bfloat16 h = __float2bfloat16_rn(f);
+            const long long id = base + (long long)(n0 + c0 + jj) * P.M;
+            o[id] = h;
+            o[id + P.plane] = __float2bfloat16_rn(f - __bfloat162float(h));
+          }
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce0 + 8 * buf);  // this warp's quarter of the buffer is drained
     }
-    tc_fence_before();
   }
   __syncthreads();
   if (warp == 1) {
+    // no MMA may still write tensor memory when it is freed: wait (bounded,
+    // whatever the abort state) for the commit that follows the last one
+    if (lane == 0) {
+      const long long t0 = clock64();
+      while (!mbar_try_wait(done, 0) && clock64() - t0 < g.wait_cycles) {
+      }
+    }
     __syncwarp();
     tc_fence_after();
-    tmem_dealloc(tmem, TMEM_COLS);
+    tmem_dealloc(tmem, 2 * TMEM_COLS);
   }
 }
 
@@ -409,19 +471,16 @@ static int sm_count() {
   return n > 0 ? n : 1;
 }
 
+// One persistent CTA per SM at most (4-stage pipeline, 193 KiB of shared
+// memory); a CTA loops over its tiles.
 static void launch(const Group &g, cudaStream_t s) {
   const int tiles = group_tiles(g);
-  if (tiles <= sm_count())
-    k_tc_gemm<4><<<tiles, 192, smem_bytes<4>(), s>>>(g);
-  else
-    k_tc_gemm<2><<<tiles, 192, smem_bytes<2>(), s>>>(g);
+  k_tc_gemm<4><<<std::min(tiles, sm_count()), 192, smem_bytes<4>(), s>>>(g);
 }
 
 static bool reserve_smem() {
   return cudaFuncSetAttribute(k_tc_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<4>()) ==
-             cudaSuccess &&
-         cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<2>()) ==
-             cudaSuccess;
+         cudaSuccess;
 }
 
 // Round-to-nearest-even FP32 -> BF16 on the host.

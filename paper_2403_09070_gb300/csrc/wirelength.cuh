@@ -421,33 +421,78 @@ __device__ __forceinline__ T wa_pair(T va, T vb, T inv_g, T &ga) {
 
 // The bucket's nets all have two pins, stored back to back from pin0: net t
 // holds pins pin0 + 2t and pin0 + 2t + 1 (no net_start load on the chain).
+// Each thread takes kPairNets nets, t and t + (number of threads), with
+// every load of all its nets issued before the first use, so that the
+// dependent chains (pin -> instance position) of its nets overlap.
+constexpr int kPairNets = 2;
+template <typename T>
+__device__ __forceinline__ void pair_net(const Pin<T> &a, const Pin<T> &b, const WlC<T> &c, V4<T> *__restrict__ acc,
+                                         T (&vals)[4]) {
+  T gx, gy, gz;
+  const T wx = wa_pair(a.px, b.px, c.inv_g, gx);
+  const T wy = wa_pair(a.py, b.py, c.inv_g, gy);
+  const T wz = wa_pair(a.pz, b.pz, c.inv_gz, gz);
+  const T dx = a.px - b.px, dy = a.py - b.py;
+  const T W = fabs(dx) + fabs(dy);
+  const T Wa = fabs(a.qx - b.px) + fabs(a.qy - b.py);  // a on the other die
+  const T Wb = fabs(a.px - b.qx) + fabs(a.py - b.qy);  // b on the other die
+  const T fa = c.fd_scale * (a.top ? W - Wa : Wa - W);
+  const T fb = c.fd_scale * (b.top ? W - Wb : Wb - W);
+  acc_add(acc + a.inst, gx, gy, fa, gz);
+  acc_add(acc + b.inst, -gx, -gy, fb, -gz);
+  vals[0] += wx + wy;
+  vals[1] += wz;
+  vals[2] += W;
+  vals[3] += a.top != b.top ? T(1) : T(0);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_wl_pair(int pin0, int nnets,
                                                  const int *__restrict__ pin_inst, const V4<T> *__restrict__ off,
                                                  const V4<T> *__restrict__ pos, WlC<T> c, V4<T> *__restrict__ acc,
                                                  T *__restrict__ part) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   T vals[4] = {0, 0, 0, 0};
-  if (t < nnets) {
-    const int s0 = pin0 + 2 * t;
-    const Pin<T> a = load_pin<T, false>(s0, pin_inst, off, pos, c);
-    const Pin<T> b = load_pin<T, false>(s0 + 1, pin_inst, off, pos, c);
-    T gx, gy, gz;
-    const T wx = wa_pair(a.px, b.px, c.inv_g, gx);
-    const T wy = wa_pair(a.py, b.py, c.inv_g, gy);
-    const T wz = wa_pair(a.pz, b.pz, c.inv_gz, gz);
-    const T dx = a.px - b.px, dy = a.py - b.py;
-    const T W = fabs(dx) + fabs(dy);
-    const T Wa = fabs(a.qx - b.px) + fabs(a.qy - b.py);  // a on the other die
-    const T Wb = fabs(a.px - b.qx) + fabs(a.py - b.qy);  // b on the other die
-    const T fa = c.fd_scale * (a.top ? W - Wa : Wa - W);
-    const T fb = c.fd_scale * (b.top ? W - Wb : Wb - W);
-    acc_add(acc + a.inst, gx, gy, fa, gz);
-    acc_add(acc + b.inst, -gx, -gy, fb, -gz);
-    vals[0] = wx + wy;
-    vals[1] = wz;
-    vals[2] = W;
-    vals[3] = a.top != b.top ? T(1) : T(0);
+  int ia[kPairNets], ib[kPairNets];
+  V4<T> oa[kPairNets], ob[kPairNets], sa[kPairNets], sb[kPairNets];
+  bool ok[kPairNets];
+#pragma unroll
+  for (int u = 0; u < kPairNets; ++u) {
+    const int t = t0 + u * nth;
+    ok[u] = t < nnets;
+    const int s0 = pin0 + 2 * (ok[u] ? t : 0);
+    ia[u] = __ldg(pin_inst + s0);
+    ib[u] = __ldg(pin_inst + s0 + 1);
+    oa[u] = off[s0];
+    ob[u] = off[s0 + 1];
+  }
+#pragma unroll
+  for (int u = 0; u < kPairNets; ++u) {
+    sa[u] = pos[ia[u]];
+    sb[u] = pos[ib[u]];
+  }
+#pragma unroll
+  for (int u = 0; u < kPairNets; ++u) {
+    if (!ok[u]) continue;
+    Pin<T> pa, pb;
+    const V4<T> *o[2] = {&oa[u], &ob[u]};
+    const V4<T> *q[2] = {&sa[u], &sb[u]};
+    Pin<T> *pp[2] = {&pa, &pb};
+    const int ii[2] = {ia[u], ib[u]};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      Pin<T> &P = *pp[k];
+      const V4<T> &oo = *o[k], &ss = *q[k];
+      P.hbt = false;
+      P.inst = ii[k];
+      P.top = ss.z > c.zmid;
+      P.px = ss.x + (P.top ? oo.z : oo.x);
+      P.py = ss.y + (P.top ? oo.w : oo.y);
+      P.qx = ss.x + (P.top ? oo.x : oo.z);
+      P.qy = ss.y + (P.top ? oo.y : oo.w);
+      P.pz = ss.z;
+    }
+    pair_net(pa, pb, c, acc, vals);
   }
   warp_sum_part<4>(vals, part);  // (W^_Bi, p^(z), W_Bi, crossing) rows
 }
