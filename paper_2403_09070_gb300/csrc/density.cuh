@@ -520,6 +520,7 @@ __global__ void k_final_macro_out(int nm, const int *__restrict__ macro_ids, con
 // it is wider than the halo allows) uses the global map directly.
 constexpr int kTile = 16;
 constexpr int kChunk = 1024;  // cells per work item: bounds the window's split sums (k_scatter_tiles)
+constexpr int kTileMinInst = 100000;  // default: tiles from this many instances up
 constexpr int kCountPerThread = 8;
 // The tile counters lie one per 128-byte line: the count blocks' atomics on
 // different tiles then never queue on the same line in the L2.

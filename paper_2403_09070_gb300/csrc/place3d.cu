@@ -95,6 +95,7 @@ struct place3d_handle {
   bool macro_direct = true;  // bin-parallel direct macro gather (else Theorem 1 suffix sums)
   // tile-bucketed scatter / gather
   bool tiles = false;
+  bool host_out = false;  // the evaluation being enqueued writes host-mapped gradient arrays
   TileC tcfg{};
   int ntiles = 0, max_items = 0;
   size_t smem_scatter = 0, smem_final = 0;
@@ -668,7 +669,10 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     void *ox = direct ? gx : h->gout;
     void *oy = direct ? gy : (char *)h->gout + (size_t)n * sizeof(T);
     void *oz = direct ? gz : (char *)h->gout + (size_t)2 * n * sizeof(T);
-    if (n > 0 && h->tiles) {
+    // host-mapped outputs: the per-cell gather, whose stores to host memory
+    // (coalesced, by instance) overlap its computation; the tiled gather
+    // would write them afterwards in one copy pass over the CPU-GPU link
+    if (n > 0 && h->tiles && !h->host_out) {
       const int rt = odt == PLACE3D_F64
                          ? launch_final_tiles<T, double>(h, s, ms, split, dc, fc, (double *)ox, (double *)oy, (double *)oz)
                          : launch_final_tiles<T, float>(h, s, ms, split, dc, fc, (float *)ox, (float *)oy, (float *)oz);
@@ -1051,7 +1055,10 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
     const size_t wbins = (size_t)h->tcfg.WX * h->tcfg.WY * p->nz;
     h->smem_scatter = wbins * 8;  // two 32-bit words per bin
     h->smem_final = wbins * 4 * (p->precision == PLACE3D_FP64 ? 8 : 4);  // one (E_x, E_y, E_z, -) vector per bin
-    h->tiles = !(p->flags & PLACE3D_FLAG_NO_TILES) && R <= 8 && h->ntiles <= 8192 && n < (1 << 24) &&
+    // small problems are launch-bound: the sort's extra launches do not pay
+    // below kTileMinInst instances unless PLACE3D_FLAG_TILES asks for tiles
+    const bool want = (p->flags & PLACE3D_FLAG_TILES) || n >= kTileMinInst;
+    h->tiles = want && !(p->flags & PLACE3D_FLAG_NO_TILES) && R <= 8 && h->ntiles <= 8192 && n < (1 << 24) &&
                h->smem_final <= 200 * 1024 && h->smem_scatter <= 200 * 1024;
     h->max_items = (n + kChunk - 1) / kChunk + h->ntiles;
   }
@@ -1376,7 +1383,7 @@ static cudaError_t install_graph(cudaGraphExec_t *exec, cudaGraph_t graph) {
 // handle's stream, writing the gradient into tgt (device arrays of the
 // handle's dtype); recaptured (and the executable graph updated in place)
 // when tgt or the parameter version changes.
-static int eval_via_graph(place3d_handle *h, void *const tgt[3]) {
+static int eval_via_graph(place3d_handle *h, void *const tgt[3], bool host_out) {
   const bool same = h->egexec && h->egversion == h->version && h->egptr[0] == tgt[0] && h->egptr[1] == tgt[1] &&
                     h->egptr[2] == tgt[2];
   if (!same) {
@@ -1386,8 +1393,10 @@ static int eval_via_graph(place3d_handle *h, void *const tgt[3]) {
     h->stream = h->cap_stream;
     P3D_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     const int hdt = h->precision == PLACE3D_FP64 ? PLACE3D_F64 : PLACE3D_F32;
+    h->host_out = host_out;
     const int rc = h->precision == PLACE3D_FP64 ? eval_impl<double>(h, tgt[0], tgt[1], tgt[2], hdt, PLACE3D_MEM_DEVICE)
                                                 : eval_impl<float>(h, tgt[0], tgt[1], tgt[2], hdt, PLACE3D_MEM_DEVICE);
+    h->host_out = false;
     h->stream = keep;
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
@@ -1429,7 +1438,7 @@ int place3d_eval_objective_and_grad(place3d_handle *h, place3d_result *out, void
     }
     if (direct)
       for (int k = 0; k < 3; ++k) tgt[k] = hd[k];
-    const int rc = eval_via_graph(h, tgt);
+    const int rc = eval_via_graph(h, tgt, direct);
     if (rc != PLACE3D_OK) return rc;
     if (ng && n > 0 && !direct) {
       const cudaMemcpyKind kind = mem == PLACE3D_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;

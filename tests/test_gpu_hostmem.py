@@ -28,15 +28,19 @@ def _np(a):
     return a.cpu().numpy() if torch.is_tensor(a) else np.asarray(a)
 
 
+@pytest.mark.parametrize("flags", [0, P.FLAG_TILES])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_host_memory_kinds_agree(precision):
+def test_host_memory_kinds_agree(precision, flags):
+    """flags = PLACE3D_FLAG_TILES: the tiled scatter; device gradients then
+    come from the tiled gather, page-locked host ones from the per-cell
+    gather (whose host stores overlap its work): the same results."""
     p = synth.make_problem("cells_2k")
     n = p["n_inst"]
     dt = torch.float64 if precision == "fp64" else torch.float32
     tol = 1e-12 if precision == "fp64" else 1e-5
     rng = np.random.default_rng(3)
     pos_sets = [[p["x"], p["y"], p["z"]], list(synth.draw_positions(rng, p, "uniform"))]
-    with P.Place3D(p, precision=precision) as h:
+    with P.Place3D(p, precision=precision, flags=flags) as h:
         ref = []
         for pos in pos_sets:
             xyz = _arrays("device", pos, dt)

@@ -220,6 +220,23 @@ def test_every_reduction_form(precision):
             h.set_wl_form(bi, G, ppl)
 
 
+@pytest.mark.parametrize("kind", ["default", "outside", "hifanout", "zfixed", "nz1", "single", "nonets"])
+def test_tiled_path_edge_cases(kind):
+    """The tile-sorted scatter/gather (forced with PLACE3D_FLAG_TILES on these
+    small problems, where the default is per cell) on the edge cases:
+    bit-exact map, FP64 1e-9, FP32 bars."""
+    p, x, y, z = _edge(kind)
+    _check_fp64(p, x, y, z, flags=16)
+    _check_fp32(p, x, y, z, flags=16)
+
+
+@pytest.mark.parametrize("positions", ["uniform", "center"])
+def test_tiled_path_cells_2k(positions):
+    p = synth.make_problem("cells_2k", positions=positions)
+    _check_fp64(p, p["x"], p["y"], p["z"], flags=16)
+    _check_fp32(p, p["x"], p["y"], p["z"], flags=16)
+
+
 @pytest.mark.parametrize("kind", ["default", "outside", "hifanout", "zfixed", "nz1"])
 def test_per_cell_scatter_gather_path(kind):
     """The per-cell scatter/gather (PLACE3D_FLAG_NO_TILES: one thread per
@@ -256,8 +273,8 @@ def test_tiles_with_wide_cells():
     x = rng.uniform(die[0], die[2], n)
     y = rng.uniform(die[1], die[3], n)
     z = rng.uniform(dz / 4, 3 * dz / 4, n)
-    _check_fp64(p, x, y, z)
-    _check_fp32(p, x, y, z)
+    _check_fp64(p, x, y, z, flags=16)
+    _check_fp32(p, x, y, z, flags=16)
 
 
 def _with_big_nets(sizes=(300, 1500, 2004), seed=9):
