@@ -535,8 +535,10 @@ def main():
     # run alone, so a stage's time is its kernels' own launch durations (the
     # roofline); region B's stage times are the concurrent ones
     hs = P.Place3D(prob, precision=precision, device=local, stream=stream, flags=P.FLAG_SERIAL)
-    for bi, (_, G, PPL) in enumerate(h_forms):
-        hs.set_wl_form(bi, G, PPL)
+    hs.set_wl_plan(h_forms)  # the autotuned degree thresholds and forms
+    h_tiles = h.tc_tiles()
+    if h_tiles:
+        hs.set_tc_tiles(h_tiles)
     hs.set_positions(*xyz)
     for _ in range(max(a.warmup, 1)):
         hs.eval(*grads, sync=False)
@@ -657,6 +659,7 @@ def main():
                             "over K steps (L2 flushed between steps); stages_concurrent: the separate-launch timed "
                             "region, both paths concurrent"),
             "wl_forms": h_forms,
+            "tc_tile_columns": h_tiles,
         }
         if cpu is not None:
             line["cpu_baseline"] = {"value": cpu["value"], "unit": UNIT, "cores": cpu["workers"], "kind": "oracle",

@@ -211,24 +211,48 @@ int place3d_eval_objective_and_grad(place3d_handle *h, place3d_result *out,
                                     void *gx, void *gy, void *gz, int dtype,
                                     int mem);
 
-/* Autotune the per-net reductions: for every net-degree bucket, time each
- * supported (lanes per net, pins per lane) form of the wirelength kernel
- * `repeats` times at the current positions and keep the fastest.  Call after
- * place3d_set_positions; synchronises the device.  Results are unchanged up
- * to floating-point summation order. */
+/* Autotune the launch configuration at the current positions (call after
+ * place3d_set_positions; synchronises the device):
+ * - degree thresholds and reduction forms of the wirelength stage: the nets
+ *   are held in degree classes (2, 3, 4, 5-6, 7-8, 9-12, 13-16, 17-24,
+ *   25-32, 33-48, 49-64, 65-128, above 128); every run of adjacent classes
+ *   up to 128 pins is timed `repeats` times with every (lanes per net, pins
+ *   per lane) form that fits it, and the split into runs (one launch each)
+ *   with the least total time is kept (dynamic programming); nets above 128
+ *   pins keep the chunked form;
+ * - with PLACE3D_FP32_TC, the tile width (64 or 128 columns) of each of the
+ *   four tensor-core product groups.
+ * Results are unchanged up to floating-point summation order. */
 int place3d_autotune(place3d_handle *h, int repeats);
 
-/* The degree buckets and their chosen forms: writes up to cap entries of
- * (largest degree, lanes per net (0 = one block per net), pins per lane) and
- * returns the number of buckets. */
+/* The wirelength launch groups and their forms: writes up to cap entries of
+ * (largest degree, lanes per net (0 = the chunked form for nets above 128
+ * pins), pins per lane) and returns the number of groups. */
 int place3d_wl_forms(const place3d_handle *h, int32_t *dmax, int32_t *lanes,
                      int32_t *pins, int cap);
 
-/* Force the form of one bucket (index as listed by place3d_wl_forms): lanes
- * per net in {1,2,4,8,16,32}, pins per lane in {1,2,4} with lanes*pins at
- * least the bucket's largest degree (the supported pairs are those the
- * autotuner tries).  INVALID_ARG otherwise. */
+/* Force the form of one launch group (index as listed by place3d_wl_forms):
+ * lanes per net in {1,2,4,8,16,32}, pins per lane in {1,2,4} with
+ * lanes*pins at least the group's largest degree (the supported pairs are
+ * those the autotuner tries).  INVALID_ARG otherwise. */
 int place3d_set_wl_form(place3d_handle *h, int bucket, int lanes, int pins);
+
+/* Set the whole wirelength launch plan, as place3d_wl_forms lists it
+ * (typically another handle's autotuned plan for the same netlist): group g
+ * covers the degree classes above group g-1's largest degree up to
+ * dmax[g], with form (lanes[g], pins[g]).  count = 0 restores the default
+ * plan.  INVALID_ARG when the plan does not match this netlist's classes or
+ * a form does not fit. */
+int place3d_set_wl_plan(place3d_handle *h, const int32_t *dmax,
+                        const int32_t *lanes, const int32_t *pins, int count);
+
+/* PLACE3D_FP32_TC: the tile width (64 or 128 output columns) of the four
+ * tensor-core product groups (x forward, y forward, x inverse, y inverse).
+ * place3d_tc_tiles writes up to cap of them and returns 4 (0 without
+ * tensor-core transforms); place3d_set_tc_tiles sets all four (INVALID_ARG
+ * for other widths or a handle without them). */
+int place3d_tc_tiles(const place3d_handle *h, int32_t *cols, int cap);
+int place3d_set_tc_tiles(place3d_handle *h, const int32_t *cols, int count);
 
 /* Synchronise the handle's stream and return the scalars of the last
  * evaluation. */

@@ -129,6 +129,10 @@ struct place3d_handle {
   void *gout = nullptr;  // internal gradient output [3][n] (handle precision)
   void *stage_in = nullptr;  // staging for host positions [3][n] doubles
   int *check_flag = nullptr;
+  // degree classes of the reordered netlist (contiguous, by ascending
+  // degree) and the launch groups over them: each bucket is a run of
+  // adjacent classes evaluated by one launch with one reduction form
+  std::vector<Bucket> fine;
   std::vector<Bucket> buckets;
   // nets above 128 pins split into chunks (k_wl_big_*): chunk and net
   // tables, per-net pass counters, per-chunk partial and per-net merged
@@ -357,6 +361,49 @@ void launch_gemm(place3d_handle *h, cudaStream_t s, std::initializer_list<GemmPr
   g.tile_start[g.count] = tiles;
   k_gemm_simt<T><<<tiles, 256, 0, s>>>(g);
   count_launch(h, stage);
+}
+
+// Net-degree classes (largest degree of each, ascending) and the default
+// launch groups over them: {2}, {3-4}, {5-8}, {9-16}, {17-32}, {33-64},
+// {65-128}, {>128} with their default forms (lanes, pins per lane);
+// place3d_autotune regroups the classes and picks the forms by timing.
+const int kClassMax[] = {2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 128, 1 << 30};
+const int kNumClasses = sizeof(kClassMax) / sizeof(kClassMax[0]);
+const int kDefaultGroupMax[] = {2, 4, 8, 16, 32, 64, 128, 1 << 30};
+const int kDefaultForm[][2] = {{1, 1}, {1, 4}, {8, 1}, {16, 1}, {32, 1}, {32, 2}, {32, 4}, {0, 0}};
+
+// The launch group over classes fine[i..j] with form (G, PPL).
+Bucket make_group_of(const place3d_handle *h, int i, int j, int G, int PPL) {
+  Bucket b = h->fine[i];
+  b.count = 0;
+  for (int k = i; k <= j; ++k) b.count += h->fine[k].count;
+  b.dmax = h->fine[j].dmax;
+  b.G = G;
+  b.PPL = PPL;
+  return b;
+}
+
+// Whether form (G, PPL) can evaluate a group whose largest degree is dmax.
+bool form_fits(const place3d_handle *h, int dmax, int G, int PPL) {
+  if (dmax > 128) return G == 0;
+  if (G == 0) return false;
+  if (G == 1 && PPL == 1) return dmax == 2 && !h->mode2d;  // 2-pin closed form
+  return G * PPL >= dmax && G * PPL <= 4 * std::max(dmax, 8);
+}
+
+void default_groups(place3d_handle *h) {
+  h->buckets.clear();
+  const int nf = (int)h->fine.size();
+  for (int i = 0; i < nf;) {
+    int g = 0;
+    while (h->fine[i].dmax > kDefaultGroupMax[g]) ++g;
+    int j = i;
+    while (j + 1 < nf && h->fine[j + 1].dmax <= kDefaultGroupMax[g]) ++j;
+    int G = kDefaultForm[g][0], PPL = kDefaultForm[g][1];
+    if (G == 1 && PPL == 1 && h->mode2d) PPL = 2;  // 2D mode: no 2-pin closed form
+    h->buckets.push_back(make_group_of(h, i, j, G, PPL));
+    i = j + 1;
+  }
 }
 
 // Launches one bucket's wirelength kernel; the group and pair forms write
@@ -979,32 +1026,27 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
     return code;
   };
 
-  // net-degree buckets: nets of degree < 2 are dropped (they contribute 0)
-  const int kLimits[8] = {2, 4, 8, 16, 32, 64, 128, 1 << 30};
-  // default forms (lanes, pins per lane) per bucket; place3d_autotune refines them
-  const int kDefault[8][2] = {{1, 1}, {1, 4}, {8, 1}, {16, 1}, {32, 1}, {32, 2}, {32, 4}, {0, 0}};
-  std::vector<std::vector<int>> cls(8);
+  // net-degree classes: nets of degree < 2 are dropped (they contribute 0)
+  std::vector<std::vector<int>> cls(kNumClasses);
   for (int e = 0; e < p->n_net; ++e) {
     const int d = p->net_start[e + 1] - p->net_start[e];
     if (d < 2) continue;
     int k = 0;
-    while (d > kLimits[k]) ++k;
+    while (d > kClassMax[k]) ++k;
     cls[k].push_back(e);
   }
   std::vector<int> order, new_start(1, 0);
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < kNumClasses; ++k) {
     if (cls[k].empty()) continue;
     int dmax = 0;
     for (int e : cls[k]) dmax = std::max(dmax, p->net_start[e + 1] - p->net_start[e]);
-    // 2D mode has no closed form for 2-pin nets (one lane, two pins instead)
-    const bool pair = kDefault[k][0] == 1 && kDefault[k][1] == 1;
-    h->buckets.push_back({(int)order.size(), (int)cls[k].size(), dmax, kDefault[k][0],
-                          pair && h->mode2d ? 2 : kDefault[k][1], new_start.back()});
+    h->fine.push_back({(int)order.size(), (int)cls[k].size(), dmax, 0, 0, new_start.back()});
     for (int e : cls[k]) {
       order.push_back(e);
       new_start.push_back(new_start.back() + (p->net_start[e + 1] - p->net_start[e]));
     }
   }
+  default_groups(h);
   h->nnet = (int)order.size();
   h->npin = new_start.back();
   // macros
@@ -1100,9 +1142,10 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
     // partial-sum rows (one per warp) for the largest grids any bucket form
     // may use (G <= 32)
     const int bs = h->precision == PLACE3D_FP64 ? wl_block<double>() : wl_block<float>();
+    // rows of any grouping of the classes: a group of c nets writes at most
+    // c * G / 32 + bs / 32 rows (G <= 32), the 2-pin form fewer
     size_t rw = 1216 * 8;  // k_norms
-    for (const Bucket &b : h->buckets)
-      rw += (size_t)std::max(grid_for((long long)b.count * 32, bs) * (bs / 32), grid_for(b.count, 256) * 8);
+    for (const Bucket &b : h->fine) rw += (size_t)b.count + (size_t)bs / 32 + 8;
     const size_t rd = (size_t)std::max(grid_for((long long)h->nx * h->ny, 256), 1) * 8;
     if (p3d_malloc((void **)&h->part_w, sizeof(double) * 4 * rw) != cudaSuccess ||
         p3d_malloc((void **)&h->part_d, sizeof(double) * 3 * rd) != cudaSuccess) {
@@ -1627,36 +1670,111 @@ int place3d_autotune(place3d_handle *h, int repeats) {
   P3D_CUDA(h, cudaEventCreate(&e0));
   P3D_CUDA(h, cudaEventCreate(&e1));
   P3D_CUDA(h, cudaStreamSynchronize(h->stream));
-  for (Bucket &b : h->buckets) {
-    if (b.G == 0) continue;  // high-fanout nets: block form only
-    float best = 1e30f;
-    int bg = b.G, bp = b.PPL;
-    for (int f = 0; f < kNumForms; ++f) {
-      const int G = kForms[f][0], PPL = kForms[f][1];
-      const bool pair = G == 1 && PPL == 1;
-      if (pair ? (b.dmax != 2 || h->mode2d) : (G * PPL < b.dmax || G * PPL > 4 * std::max(b.dmax, 8))) continue;
-      float ms = 1e30f;  // the fastest of `repeats` timed runs after one warm-up run
-      for (int r = 0; r <= repeats; ++r) {
-        cudaEventRecord(e0, w);
-        if (h->precision == PLACE3D_FP64)
-          launch_wl<double>(h, b, G, PPL, w, wl_consts<double>(h), as<double>(h->part_w));
-        else
-          launch_wl<float>(h, b, G, PPL, w, wl_consts<float>(h), as<float>(h->part_w));
-        cudaEventRecord(e1, w);
-        P3D_CUDA(h, cudaEventSynchronize(e1));
-        float t = 0;
-        cudaEventElapsedTime(&t, e0, e1);
-        if (r > 0) ms = std::min(ms, t);
-      }
-      if (ms < best) { best = ms; bg = G; bp = PPL; }
+  // the fastest of `repeats` timed runs of one launch group, after one warm-up run
+  auto time_group = [&](const Bucket &b) -> float {
+    float ms = 1e30f;
+    for (int r = 0; r <= repeats; ++r) {
+      cudaEventRecord(e0, w);
+      if (h->precision == PLACE3D_FP64)
+        launch_wl<double>(h, b, b.G, b.PPL, w, wl_consts<double>(h), as<double>(h->part_w));
+      else
+        launch_wl<float>(h, b, b.G, b.PPL, w, wl_consts<float>(h), as<float>(h->part_w));
+      cudaEventRecord(e1, w);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0f;
+      float t = 0;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (r > 0) ms = std::min(ms, t);
     }
-    b.G = bg;
-    b.PPL = bp;
+    return ms;
+  };
+  // Degree thresholds and forms: the classes up to 128 pins are split into
+  // runs of adjacent classes, one launch each; best[j] is the least total
+  // time of classes 0..j-1 over all splits and forms (dynamic programming
+  // over the measured time of every run with every form that fits it).
+  const int nf = (int)h->fine.size();
+  int nd = nf;
+  while (nd > 0 && h->fine[nd - 1].dmax > 128) --nd;
+  std::vector<double> best(nd + 1, 1e300);
+  std::vector<int> from(nd + 1, 0), fG(nd + 1, 0), fP(nd + 1, 0);
+  best[0] = 0;
+  bool bad = false;
+  for (int j = 0; j < nd && !bad; ++j)
+    for (int i = 0; i <= j && !bad; ++i)
+      for (int f = 0; f < kNumForms; ++f) {
+        const int G = kForms[f][0], PPL = kForms[f][1];
+        if (!form_fits(h, h->fine[j].dmax, G, PPL)) continue;
+        const float t = time_group(make_group_of(h, i, j, G, PPL));
+        if (t < 0) {
+          bad = true;
+          break;
+        }
+        if (best[i] + t < best[j + 1]) {
+          best[j + 1] = best[i] + t;
+          from[j + 1] = i;
+          fG[j + 1] = G;
+          fP[j + 1] = PPL;
+        }
+      }
+  if (!bad && nd > 0) {
+    std::vector<Bucket> groups;
+    for (int j = nd; j > 0; j = from[j]) groups.push_back(make_group_of(h, from[j], j - 1, fG[j], fP[j]));
+    std::reverse(groups.begin(), groups.end());
+    if (nd < nf) groups.push_back(make_group_of(h, nd, nf - 1, 0, 0));  // above 128 pins: the chunked form
+    h->buckets = groups;
   }
+  if (!bad && h->tc && p3d_tc::autotune(h->tc, w, repeats) != 0) bad = true;
   ++h->version;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (bad) return cuda_fail(h, cudaGetLastError(), "autotune");
   P3D_CUDA(h, cudaGetLastError());
+  return PLACE3D_OK;
+}
+
+int place3d_set_wl_plan(place3d_handle *h, const int32_t *dmax, const int32_t *lanes, const int32_t *pins,
+                        int count) {
+  if (!h || count < 0 || (count > 0 && (!dmax || !lanes || !pins)))
+    return fail(h, PLACE3D_ERR_INVALID_ARG, "bad launch plan arguments");
+  if (count == 0) {
+    default_groups(h);
+    ++h->version;
+    return PLACE3D_OK;
+  }
+  std::vector<Bucket> groups;
+  const int nf = (int)h->fine.size();
+  int i = 0;
+  for (int g = 0; g < count; ++g) {
+    if (i >= nf) return fail(h, PLACE3D_ERR_INVALID_ARG, "the plan has more groups than the netlist's degrees");
+    if (h->fine[i].dmax > dmax[g])
+      return fail(h, PLACE3D_ERR_INVALID_ARG, "a group's largest degree is below its first class");
+    int j = i;
+    while (j + 1 < nf && h->fine[j + 1].dmax <= dmax[g]) ++j;
+    const Bucket b = make_group_of(h, i, j, lanes[g], pins[g]);
+    if (b.dmax != dmax[g] || !form_fits(h, b.dmax, b.G, b.PPL))
+      return fail(h, PLACE3D_ERR_INVALID_ARG, "the plan does not match this netlist's degree classes");
+    groups.push_back(b);
+    i = j + 1;
+  }
+  if (i != nf) return fail(h, PLACE3D_ERR_INVALID_ARG, "the plan leaves degree classes uncovered");
+  h->buckets = groups;
+  ++h->version;
+  return PLACE3D_OK;
+}
+
+int place3d_tc_tiles(const place3d_handle *h, int32_t *cols, int cap) {
+  if (!h || !h->tc) return 0;
+  for (int k = 0; k < 4 && k < cap; ++k)
+    if (cols) cols[k] = p3d_tc::tile_columns(h->tc, k);
+  return 4;
+}
+
+int place3d_set_tc_tiles(place3d_handle *h, const int32_t *cols, int count) {
+  if (!h || !cols || count != 4) return fail(h, PLACE3D_ERR_INVALID_ARG, "four tile widths expected");
+  if (!h->tc) return fail(h, PLACE3D_ERR_INVALID_ARG, "the handle has no tensor-core transforms");
+  for (int k = 0; k < 4; ++k)
+    if (cols[k] != 64 && cols[k] != 128) return fail(h, PLACE3D_ERR_INVALID_ARG, "tile widths are 64 or 128");
+  for (int k = 0; k < 4; ++k) p3d_tc::set_tile_columns(h->tc, k, cols[k]);
+  ++h->version;
   return PLACE3D_OK;
 }
 

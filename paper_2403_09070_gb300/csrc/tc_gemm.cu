@@ -33,14 +33,24 @@
 namespace p3d_tc {
 using namespace p3d;
 
-// Pipeline depth: 4 stages (193 KiB of shared memory, one persistent CTA
-// per SM).
-constexpr int BM = 128, BN = 64, BK = 64;
-constexpr int A_BYTES = BM * BK * 2;                    // one BF16 plane of an A tile (16 KiB)
-constexpr int W_BYTES = BN * BK * 2;                    // one BF16 plane of a W tile (8 KiB)
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * W_BYTES;  // 48 KiB
-template <int STAGES> constexpr int smem_bytes() { return STAGES * STAGE_BYTES + 1024; }
-constexpr int TMEM_COLS = BN;                           // FP32 accumulator columns of one buffer (two are allocated)
+// Tile shapes: M = 128 rows, K-blocks of 64, and N = 64 or 128 columns
+// (chosen per product group by the autotuner: N = 128 reads each A tile for
+// twice the outputs, N = 64 gives twice the tiles to spread over the SMs).
+// Pipeline depth: 4 stages of 48 KiB (N = 64) or 3 stages of 64 KiB
+// (N = 128), one persistent CTA per SM.
+constexpr int BM = 128, BK = 64;
+constexpr int A_BYTES = BM * BK * 2;  // one BF16 plane of an A tile (16 KiB)
+template <int BN> struct TileCfg {
+  static constexpr int W_BYTES = BN * BK * 2;                    // one BF16 plane of a W tile
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * W_BYTES;  // A hi, A lo, W hi, W lo
+  static constexpr int STAGES = BN == 64 ? 4 : 3;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+  static constexpr int TMEM_COLS = BN;  // FP32 accumulator columns of one buffer (two are allocated)
+  // instruction descriptor: D FP32, A and B BF16, both K-major, M = BM, N = BN
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                    ((uint32_t)(BM >> 4) << 24);
+};
+constexpr int kMinBN = 64;  // every product's N and K are multiples of this
 constexpr long long kWaitCycles = 4000000000LL;         // about 2 s at 2 GHz
 
 enum { OUT_F32 = 0, OUT_SPLIT = 1 };
@@ -56,9 +66,10 @@ struct Prob {
 
 struct Group {
   CUtensorMap amap[3];  // A: dims {K, M, batch, plane}
-  CUtensorMap wmap[3];  // W: dims {K, N, plane}
+  CUtensorMap wmap[3];  // W: dims {K, N, plane}, box of bn rows
   Prob p[3];
   int count;
+  int bn;               // tile columns (64 or 128)
   int tile_start[4];
   int *err;
   long long wait_cycles;  // clock budget of every mbarrier wait (kWaitCycles)
@@ -153,10 +164,6 @@ __device__ __forceinline__ uint64_t desc_k_sw128(uint32_t saddr) {
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// Instruction descriptor: D FP32, A and B BF16, both K-major, M = BM, N = BN.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
-
 __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, volatile int *abort_flag,
                                              int *err, int code, long long budget) {
   const long long t0 = clock64();
@@ -189,15 +196,17 @@ __device__ __forceinline__ void tile_coords(const Group &g, int tile, int &pi, i
   b = tile / per_b;
   const int r = tile - b * per_b;
   m0 = (r % P.tiles_m) * BM;
-  n0 = (r / P.tiles_m) * BN;
+  n0 = (r / P.tiles_m) * g.bn;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-template <int STAGES>
+template <int BN>
 __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Group g) {
+  using C = TileCfg<BN>;
+  constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES, W_BYTES = C::W_BYTES, TMEM_COLS = C::TMEM_COLS;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bars[2 * STAGES + 5];
   __shared__ uint32_t tmem_slot;
@@ -290,9 +299,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Grou
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint64_t dah = desc_k_sw128(a_hi + kk * 32), dal = desc_k_sw128(a_lo + kk * 32);
             const uint64_t dwh = desc_k_sw128(w_hi + kk * 32), dwl = desc_k_sw128(w_lo + kk * 32);
-            mma_bf16(td, dah, dwh, kIdesc, (kb | kk) != 0);
-            mma_bf16(td, dah, dwl, kIdesc, 1u);
-            mma_bf16(td, dal, dwh, kIdesc, 1u);
+            mma_bf16(td, dah, dwh, C::IDESC, (kb | kk) != 0);
+            mma_bf16(td, dah, dwl, C::IDESC, 1u);
+            mma_bf16(td, dal, dwh, C::IDESC, 1u);
           }
           mma_commit(empty0 + 8 * s);  // frees the stage once these MMAs have read it
         }
@@ -395,12 +404,12 @@ static bool map_a(CUtensorMap *m, const void *base, int K, int M, int batches, l
 }
 
 // W operand: BF16 planes [plane][N][K].
-static bool map_w(CUtensorMap *m, const void *base, int K, int N, long long plane, std::string *why) {
+static bool map_w(CUtensorMap *m, const void *base, int K, int N, long long plane, int bn, std::string *why) {
   EncodeTiledFn f = encode_fn(why);
   if (!f) return false;
   cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)N, 2};
   cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)plane * 2};
-  cuuint32_t box[3] = {BK, BN, 1};
+  cuuint32_t box[3] = {BK, (cuuint32_t)bn, 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, es,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -425,20 +434,21 @@ struct ProbSpec {
   int ostride;  // 0 or 1: contiguous
 };
 
-static bool make_group(Group *g, std::initializer_list<ProbSpec> specs, int *err, std::string *why) {
+static bool make_group(Group *g, std::initializer_list<ProbSpec> specs, int *err, std::string *why, int bn = 64) {
   std::memset(g, 0, sizeof(Group));
   g->err = err;
+  g->bn = bn;
   g->wait_cycles = kWaitCycles;
   g->skip_loads = 0;
   int tiles = 0;
   for (const ProbSpec &s : specs) {
-    if (s.M % BM || s.N % BN || s.K % BK) {
-      if (why) *why = "product sizes must be multiples of 128 (M) and 64 (N, K)";
+    if (s.M % BM || s.N % bn || s.K % BK) {
+      if (why) *why = "product sizes must be multiples of 128 (M), the tile width (N) and 64 (K)";
       return false;
     }
     const int i = g->count;
     if (!map_a(&g->amap[i], s.A, s.K, s.M, s.batches, s.a_bstride, s.a_plane, why)) return false;
-    if (!map_w(&g->wmap[i], s.W, s.K, s.N, s.w_plane, why)) return false;
+    if (!map_w(&g->wmap[i], s.W, s.K, s.N, s.w_plane, bn, why)) return false;
     Prob &p = g->p[i];
     p.out = s.out;
     p.plane = s.o_plane;
@@ -448,7 +458,7 @@ static bool make_group(Group *g, std::initializer_list<ProbSpec> specs, int *err
     p.K = s.K;
     p.batches = s.batches;
     p.tiles_m = s.M / BM;
-    p.tiles_n = s.N / BN;
+    p.tiles_n = s.N / bn;
     p.kind = s.kind;
     p.ostride = s.ostride > 1 ? s.ostride : 1;
     g->tile_start[i] = tiles;
@@ -474,13 +484,18 @@ static int sm_count() {
 // One persistent CTA per SM at most (4-stage pipeline, 193 KiB of shared
 // memory); a CTA loops over its tiles.
 static void launch(const Group &g, cudaStream_t s) {
-  const int tiles = group_tiles(g);
-  k_tc_gemm<4><<<std::min(tiles, sm_count()), 192, smem_bytes<4>(), s>>>(g);
+  const int ctas = std::min(group_tiles(g), sm_count());
+  if (g.bn == 128)
+    k_tc_gemm<128><<<ctas, 192, TileCfg<128>::SMEM, s>>>(g);
+  else
+    k_tc_gemm<64><<<ctas, 192, TileCfg<64>::SMEM, s>>>(g);
 }
 
 static bool reserve_smem() {
-  return cudaFuncSetAttribute(k_tc_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<4>()) ==
-         cudaSuccess;
+  return cudaFuncSetAttribute(k_tc_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, TileCfg<64>::SMEM) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, TileCfg<128>::SMEM) ==
+             cudaSuccess;
 }
 
 // Round-to-nearest-even FP32 -> BF16 on the host.
@@ -515,7 +530,11 @@ struct TcPlan {
   __nv_bfloat16 *Wfx = nullptr, *Wfy = nullptr, *Wbx = nullptr, *Wcy = nullptr, *Wsy = nullptr;
   const ZStageC *zc = nullptr;
   int *err = nullptr;
-  Group g_fx, g_fy, g_ix, g_iy;
+  // the four product groups (x forward, y forward, x inverse, y inverse),
+  // each built with 64- and 128-column tiles; pick[k] is the variant used
+  enum { FX = 0, FY = 1, IX = 2, IY = 3 };
+  Group g[4][2];
+  int pick[4] = {0, 0, 0, 0};
 };
 
 static void free_plan(TcPlan *p) {
@@ -593,24 +612,31 @@ TcPlan *create(int device, int nx, int ny, int nz, double dx, double dy, double 
   }
   const long long pl = (long long)nx * ny, snb = (long long)nb;
   const long long wx = (long long)nx * nx, wy = (long long)ny * ny;
-  if (ok)  // x forward: rho[z][y][x] -> t1[z][j][y] (split)
-    ok = make_group(&p->g_fx, {{p->rho, pl, snb, p->Wfx, wx, p->t1, pl, snb, OUT_SPLIT, nz, ny, nx, nx}}, p->err, why);
-  if (ok)  // y forward: t1[z][j][y] -> t2[z][k][j] (FP32, for the z stage)
-    ok = make_group(&p->g_fy, {{p->t1, pl, snb, p->Wfy, wy, p->t2, pl, 0, OUT_F32, nz, nx, ny, ny}}, p->err, why);
-  if (ok)  // x inverse: [S_x; C_x] Czpsi -> xinv[z][2nx][ny], C_x Szpsi -> x2[z][nx][ny]
-    ok = make_group(&p->g_ix,
-                    {{p->cz, pl, snb, p->Wbx, 2 * wx, p->xinv, 2 * pl, 2 * snb, OUT_SPLIT, nz, ny, 2 * nx, nx},
-                     {p->sz, pl, snb, p->Wbx + wx, 2 * wx, p->x2, pl, snb, OUT_SPLIT, nz, ny, nx, nx}},
-                    p->err, why);
-  // y inverse: E_x = C_y (S_x C_z psi), E_y = S_y (C_x C_z psi), E_z = C_y (C_x S_z psi), written
-  // interleaved into e4[z][y][x] = (E_x, E_y, E_z, -) so the gather reads one vector per bin
   float *e = static_cast<float *>(e4);
-  if (ok)
-    ok = make_group(&p->g_iy,
-                    {{p->xinv, 2 * pl, 2 * snb, p->Wcy, wy, e + 0, pl, 0, OUT_F32, nz, nx, ny, ny, 4},
-                     {p->xinv + pl, 2 * pl, 2 * snb, p->Wsy, wy, e + 1, pl, 0, OUT_F32, nz, nx, ny, ny, 4},
-                     {p->x2, pl, snb, p->Wcy, wy, e + 2, pl, 0, OUT_F32, nz, nx, ny, ny, 4}},
-                    p->err, why);
+  for (int v = 0; v < 2 && ok; ++v) {
+    const int bn = v ? 128 : 64;
+    // x forward: rho[z][y][x] -> t1[z][j][y] (split)
+    ok = make_group(&p->g[TcPlan::FX][v], {{p->rho, pl, snb, p->Wfx, wx, p->t1, pl, snb, OUT_SPLIT, nz, ny, nx, nx}},
+                    p->err, why, bn);
+    // y forward: t1[z][j][y] -> t2[z][k][j] (FP32, for the z stage)
+    if (ok)
+      ok = make_group(&p->g[TcPlan::FY][v], {{p->t1, pl, snb, p->Wfy, wy, p->t2, pl, 0, OUT_F32, nz, nx, ny, ny}},
+                      p->err, why, bn);
+    // x inverse: [S_x; C_x] Czpsi -> xinv[z][2nx][ny], C_x Szpsi -> x2[z][nx][ny]
+    if (ok)
+      ok = make_group(&p->g[TcPlan::IX][v],
+                      {{p->cz, pl, snb, p->Wbx, 2 * wx, p->xinv, 2 * pl, 2 * snb, OUT_SPLIT, nz, ny, 2 * nx, nx},
+                       {p->sz, pl, snb, p->Wbx + wx, 2 * wx, p->x2, pl, snb, OUT_SPLIT, nz, ny, nx, nx}},
+                      p->err, why, bn);
+    // y inverse: E_x = C_y (S_x C_z psi), E_y = S_y (C_x C_z psi), E_z = C_y (C_x S_z psi), written
+    // interleaved into e4[z][y][x] = (E_x, E_y, E_z, -) so the gather reads one vector per bin
+    if (ok)
+      ok = make_group(&p->g[TcPlan::IY][v],
+                      {{p->xinv, 2 * pl, 2 * snb, p->Wcy, wy, e + 0, pl, 0, OUT_F32, nz, nx, ny, ny, 4},
+                       {p->xinv + pl, 2 * pl, 2 * snb, p->Wsy, wy, e + 1, pl, 0, OUT_F32, nz, nx, ny, ny, 4},
+                       {p->x2, pl, snb, p->Wcy, wy, e + 2, pl, 0, OUT_F32, nz, nx, ny, ny, 4}},
+                      p->err, why, bn);
+  }
   if (!ok) {
     free_plan(p);
     return nullptr;
@@ -623,8 +649,8 @@ void densify(TcPlan *p, cudaStream_t s, int nxy, int nz, const long long *q, con
 }
 
 int forward(TcPlan *p, cudaStream_t s) {
-  launch(p->g_fx, s);
-  launch(p->g_fy, s);
+  launch(p->g[TcPlan::FX][p->pick[TcPlan::FX]], s);
+  launch(p->g[TcPlan::FY][p->pick[TcPlan::FY]], s);
   return 2;
 }
 
@@ -644,10 +670,48 @@ int zstage(TcPlan *p, cudaStream_t s, float *part) {
 }
 
 int inverse(TcPlan *p, cudaStream_t s) {
-  launch(p->g_ix, s);
-  launch(p->g_iy, s);
+  launch(p->g[TcPlan::IX][p->pick[TcPlan::IX]], s);
+  launch(p->g[TcPlan::IY][p->pick[TcPlan::IY]], s);
   return 2;
 }
+
+int autotune(TcPlan *p, cudaStream_t s, int repeats) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return -1;
+  }
+  int rc = 0;
+  for (int k = 0; k < 4 && rc == 0; ++k) {
+    float best = 1e30f;
+    for (int v = 0; v < 2; ++v) {
+      float ms = 1e30f;  // fastest of `repeats` timed launches after one warm-up launch
+      for (int r = 0; r <= repeats; ++r) {
+        cudaEventRecord(e0, s);
+        launch(p->g[k][v], s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          rc = -1;
+          break;
+        }
+        float t = 0;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (r > 0) ms = std::min(ms, t);
+      }
+      if (rc == 0 && ms < best) {
+        best = ms;
+        p->pick[k] = v;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc != 0 || cudaGetLastError() != cudaSuccess ? -1 : 0;
+}
+
+int tile_columns(const TcPlan *p, int group) { return p->g[group][p->pick[group]].bn; }
+void set_tile_columns(TcPlan *p, int group, int bn) { p->pick[group] = bn == 128 ? 1 : 0; }
 
 int error_code(TcPlan *p) {
   int e = 0;
@@ -667,7 +731,7 @@ extern "C" int place3d_tc_selftest(int M, int N, int K, int batches, const float
                                    int *wait_error) {
   using namespace p3d_tc;
   if (M <= 0 || N <= 0 || K <= 0 || batches <= 0 || !A || !W || !out) return PLACE3D_ERR_INVALID_ARG;
-  if (M % BM || N % BN || K % BK) return PLACE3D_ERR_INVALID_ARG;
+  if (M % BM || N % kMinBN || K % BK) return PLACE3D_ERR_INVALID_ARG;
   int dev = 0;
   cudaDeviceProp prop;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess ||
@@ -718,7 +782,7 @@ extern "C" int place3d_tc_timeout_selftest(long long wait_cycles, int *wait_erro
       prop.major != 10 || prop.minor != 3)
     return PLACE3D_ERR_UNSUPPORTED;
   if (!reserve_smem()) return PLACE3D_ERR_CUDA;
-  const int M = BM, N = BN, K = BK;
+  const int M = BM, N = kMinBN, K = BK;
   std::vector<double> av((size_t)M * K, 0.0), wv((size_t)N * K, 0.0);
   std::string why;
   __nv_bfloat16 *da = nullptr, *dw = nullptr;

@@ -28,6 +28,13 @@ void densify(TcPlan *p, cudaStream_t s, int nxy, int nz, const long long *q, con
 int forward(TcPlan *p, cudaStream_t s);
 int zstage(TcPlan *p, cudaStream_t s, float *part);  // per-block energy rows (see k_zstage)
 int inverse(TcPlan *p, cudaStream_t s);
+// Times both tile widths (64 and 128 columns) of each of the four product
+// groups on stream s and keeps the faster (0, or -1 on a CUDA error).
+int autotune(TcPlan *p, cudaStream_t s, int repeats);
+// Tile columns in use for group k (0 x forward, 1 y forward, 2 x inverse,
+// 3 y inverse), and a way to set them (64 or 128).
+int tile_columns(const TcPlan *p, int group);
+void set_tile_columns(TcPlan *p, int group, int bn);
 // Error code left by a bounded wait of the tensor-core kernel (0 = none);
 // synchronises with the device.
 int error_code(TcPlan *p);

@@ -71,7 +71,8 @@ EXPORTS = ("place3d_create", "place3d_geometry", "place3d_alpha", "place3d_set_p
            "place3d_batch_create", "place3d_batch_eval", "place3d_batch_destroy", "place3d_set_layer_weights",
            "place3d_tc_timeout_selftest", "place3d_debug_fail_alloc", "place3d_ll2f_selftest",
            "place3d_graph_captures", "place3d_nesterov_init", "place3d_nesterov_precondition",
-           "place3d_nesterov_update", "place3d_nesterov_step")
+           "place3d_nesterov_update", "place3d_nesterov_step", "place3d_set_wl_plan", "place3d_tc_tiles",
+           "place3d_set_tc_tiles")
 NOALLOC_MAX_BINS = 262144
 
 _lib = None
@@ -123,6 +124,9 @@ def load_library(build_if_missing: bool = True):
     L.place3d_set_params.argtypes = [vp, d, d, d, d]
     L.place3d_set_layer_weights.argtypes = [vp, vp]
     L.place3d_wl_forms.argtypes = [vp, vp, vp, vp, i32]
+    L.place3d_set_wl_plan.argtypes = [vp, vp, vp, vp, i32]
+    L.place3d_tc_tiles.argtypes = [vp, vp, i32]
+    L.place3d_set_tc_tiles.argtypes = [vp, vp, i32]
     L.place3d_tc_selftest.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp]
     L.place3d_tc_timeout_selftest.argtypes = [C.c_longlong, vp]
     L.place3d_debug_fail_alloc.argtypes = [i32]
@@ -338,6 +342,23 @@ class Place3D:
 
     def set_wl_form(self, bucket: int, lanes: int, pins: int):
         self._check(self._L.place3d_set_wl_form(self._h, int(bucket), int(lanes), int(pins)))
+
+    def set_wl_plan(self, plan):
+        """Set the wirelength launch plan [(largest degree, lanes, pins)], as
+        wl_forms() lists it; [] restores the default plan."""
+        d, l_, p_ = (np.ascontiguousarray([int(v[k]) for v in plan], dtype=np.int32) for k in range(3))
+        self._check(self._L.place3d_set_wl_plan(self._h, d.ctypes.data, l_.ctypes.data, p_.ctypes.data,
+                                                len(plan)))
+
+    def tc_tiles(self) -> list:
+        """Tile widths of the four tensor-core product groups ([] without them)."""
+        a = np.zeros(4, np.int32)
+        k = self._L.place3d_tc_tiles(self._h, a.ctypes.data, 4)
+        return [int(v) for v in a[:k]]
+
+    def set_tc_tiles(self, cols):
+        a = np.ascontiguousarray(cols, dtype=np.int32)
+        self._check(self._L.place3d_set_tc_tiles(self._h, a.ctypes.data, int(a.size)))
 
     def _dev(self, arrs):
         b = [_buf(a) for a in arrs]

@@ -101,3 +101,59 @@ def test_batch_sees_set_params_of_one_instance():
     b.close()
     for h in hs:
         h.close()
+
+
+def test_autotuned_plan_keeps_results_and_transfers():
+    """place3d_autotune regroups the degree classes and picks the forms and
+    the tensor-core tile widths; the results stay those of the default plan
+    (up to summation order), and the plan set on a second handle
+    (place3d_set_wl_plan, place3d_set_tc_tiles) reproduces them."""
+    p = synth.make_problem("cells_200k")
+    x, y, z = (np.asarray(p[k], np.float32) for k in ("x", "y", "z"))
+    n = p["n_inst"]
+    with P.Place3D(p, precision="fp32_tc") as h:
+        h.set_positions(x, y, z)
+        g0 = [np.zeros(n, np.float32) for _ in range(3)]
+        r0 = h.eval(*g0)
+        default = h.wl_forms()
+        h.autotune(1)
+        plan, tiles = h.wl_forms(), h.tc_tiles()
+        g1 = [np.zeros(n, np.float32) for _ in range(3)]
+        r1 = h.eval(*g1)
+    maxdeg = int(np.diff(p["net_start"]).max())
+    assert [f[0] for f in default][:5] == [2, 4, 8, 16, 32] and default[-1][0] == maxdeg
+    assert len(tiles) == 4 and set(tiles) <= {64, 128}
+    assert plan[-1][0] == default[-1][0]  # every degree is covered
+    assert r1["obj"] == pytest.approx(r0["obj"], rel=1e-5)
+    for a, b in zip(g1, g0):
+        np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-4 * np.abs(b).max())
+    with P.Place3D(p, precision="fp32_tc") as h2:
+        h2.set_wl_plan(plan)
+        h2.set_tc_tiles(tiles)
+        assert h2.wl_forms() == plan and h2.tc_tiles() == tiles
+        h2.set_positions(x, y, z)
+        g2 = [np.zeros(n, np.float32) for _ in range(3)]
+        r2 = h2.eval(*g2)
+        assert r2["obj"] == pytest.approx(r1["obj"], rel=1e-6)
+        with pytest.raises(P.Place3DError):
+            h2.set_wl_plan([(3, 1, 4)])  # leaves classes uncovered
+        with pytest.raises(P.Place3DError):
+            h2.set_tc_tiles([64, 96, 64, 64])
+        h2.set_wl_plan([])
+        assert h2.wl_forms() == default
+
+
+@pytest.mark.parametrize("cols", [[64, 64, 64, 64], [128, 128, 128, 128], [128, 64, 64, 128]])
+def test_tensor_core_tile_widths_agree(cols):
+    """Every tile width of the tensor-core products gives the same fields."""
+    p = synth.make_problem("cells_200k")
+    x, y, z = (np.asarray(p[k], np.float32) for k in ("x", "y", "z"))
+    out = []
+    for c in ([64, 64, 64, 64], cols):
+        with P.Place3D(p, precision="fp32_tc") as h:
+            h.set_tc_tiles(c)
+            h.set_positions(x, y, z)
+            r = h.eval()
+            out.append((r["energy"], h.copy_map(P.MAP_EX)))
+    assert out[1][0] == pytest.approx(out[0][0], rel=1e-6)
+    np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-5, atol=1e-5 * np.abs(out[0][1]).max())
