@@ -81,6 +81,78 @@ __device__ __forceinline__ double r_exp2(double a) { return exp2(a); }
 __device__ __forceinline__ float r_rcp(float a) { return __fdividef(1.0f, a); }
 __device__ __forceinline__ double r_rcp(double a) { return 1.0 / a; }
 
+// Packed FP32 pair arithmetic (sm_100 and later): (d0, d1) = (a0 b0 + c0,
+// a1 b1 + c1) in one instruction, each lane rounded to nearest as a single
+// FMA.  Used where the x and y axes take the same steps.
+__device__ __forceinline__ void fma2(float a0, float a1, float b0, float b1, float &c0, float &c1) {
+  asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%0, %1};\n\t"
+      "fma.rn.f32x2 rc, ra, rb, rc;\n\t"
+      "mov.b64 {%0, %1}, rc;\n\t}"
+      : "+f"(c0), "+f"(c1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void fma2(double a0, double a1, double b0, double b1, double &c0, double &c1) {
+  c0 = fma(a0, b0, c0);
+  c1 = fma(a1, b1, c1);
+}
+// (a0 - b0, a1 - b1) * (s0, s1), the subtraction and the product each rounded.
+__device__ __forceinline__ void submul2(float a0, float a1, float b0, float b1, float s0, float s1, float &d0,
+                                        float &d1) {
+  asm("{\n\t.reg .b64 ra, rb, rs, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rs, {%6, %7};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\t"
+      "mul.rn.f32x2 rd, rd, rs;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d0), "=f"(d1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1), "f"(s0), "f"(s1));
+}
+__device__ __forceinline__ void submul2(double a0, double a1, double b0, double b1, double s0, double s1, double &d0,
+                                        double &d1) {
+  d0 = (a0 - b0) * s0;
+  d1 = (a1 - b1) * s1;
+}
+// WA gradient of both axes at once: g_a = (e+_a A_a)(1 + (v_a - B_a) ig) -
+// (e-_a C_a)(1 - (v_a - D_a) ig), a = x, y.
+__device__ __forceinline__ void wa_grad2(const float (&ep)[2], const float (&em)[2], const float (&v)[2],
+                                         const float (&A)[2], const float (&B)[2], const float (&C)[2],
+                                         const float (&D)[2], float ig, float (&g)[2]) {
+  asm("{\n\t.reg .b64 ep, em, v, A, B, C, D, ig, nig, one, t1, t2, u1, u2, r;\n\t"
+      "mov.b64 ep, {%2, %3};\n\t"
+      "mov.b64 em, {%4, %5};\n\t"
+      "mov.b64 v, {%6, %7};\n\t"
+      "mov.b64 A, {%8, %9};\n\t"
+      "mov.b64 B, {%10, %11};\n\t"
+      "mov.b64 C, {%12, %13};\n\t"
+      "mov.b64 D, {%14, %15};\n\t"
+      "mov.b64 ig, {%16, %16};\n\t"
+      "mov.b64 nig, {%18, %18};\n\t"
+      "mov.b64 one, {%17, %17};\n\t"
+      "mul.rn.f32x2 t1, ep, A;\n\t"
+      "mul.rn.f32x2 t2, em, C;\n\t"
+      "sub.rn.f32x2 u1, v, B;\n\t"
+      "sub.rn.f32x2 u2, v, D;\n\t"
+      "fma.rn.f32x2 u1, u1, ig, one;\n\t"
+      "fma.rn.f32x2 u2, u2, nig, one;\n\t"
+      "mul.rn.f32x2 r, t1, u1;\n\t"
+      "mul.rn.f32x2 t2, t2, u2;\n\t"
+      "sub.rn.f32x2 r, r, t2;\n\t"
+      "mov.b64 {%0, %1}, r;\n\t}"
+      : "=f"(g[0]), "=f"(g[1])
+      : "f"(ep[0]), "f"(ep[1]), "f"(em[0]), "f"(em[1]), "f"(v[0]), "f"(v[1]), "f"(A[0]), "f"(A[1]), "f"(B[0]),
+        "f"(B[1]), "f"(C[0]), "f"(C[1]), "f"(D[0]), "f"(D[1]), "f"(ig), "f"(1.0f), "f"(-ig));
+}
+__device__ __forceinline__ void wa_grad2(const double (&ep)[2], const double (&em)[2], const double (&v)[2],
+                                         const double (&A)[2], const double (&B)[2], const double (&C)[2],
+                                         const double (&D)[2], double ig, double (&g)[2]) {
+  for (int a = 0; a < 2; ++a)
+    g[a] = (ep[a] * A[a]) * (1.0 + (v[a] - B[a]) * ig) - (em[a] * C[a]) * (1.0 - (v[a] - D[a]) * ig);
+}
+
 template <typename T> __device__ __forceinline__ T big();
 template <> __device__ __forceinline__ float big<float>() { return 3.0e38f; }
 template <> __device__ __forceinline__ double big<double>() { return 1.0e300; }

@@ -209,14 +209,11 @@ __device__ __forceinline__ void sums_add(Sums<T> &S, const Pin<T> &p, const T (&
 #pragma unroll
   for (int q = 0; q < 2; ++q) {  // q = 0: the + exponential, 1: the - one
     const T ea = ex[q], eb = ex[2 + q];
-    S.v[0][1][2 * q] = fma(mt, ea, S.v[0][1][2 * q]);
-    S.v[0][0][2 * q] = fma(mb, ea, S.v[0][0][2 * q]);
-    S.v[0][1][2 * q + 1] = fma(xt, ea, S.v[0][1][2 * q + 1]);
-    S.v[0][0][2 * q + 1] = fma(xb, ea, S.v[0][0][2 * q + 1]);
-    S.v[1][1][2 * q] = fma(mt, eb, S.v[1][1][2 * q]);
-    S.v[1][0][2 * q] = fma(mb, eb, S.v[1][0][2 * q]);
-    S.v[1][1][2 * q + 1] = fma(yt, eb, S.v[1][1][2 * q + 1]);
-    S.v[1][0][2 * q + 1] = fma(yb, eb, S.v[1][0][2 * q + 1]);
+    // x and y in step: one packed FMA per (side, sum) pair
+    fma2(mt, mt, ea, eb, S.v[0][1][2 * q], S.v[1][1][2 * q]);
+    fma2(mb, mb, ea, eb, S.v[0][0][2 * q], S.v[1][0][2 * q]);
+    fma2(xt, yt, ea, eb, S.v[0][1][2 * q + 1], S.v[1][1][2 * q + 1]);
+    fma2(xb, yb, ea, eb, S.v[0][0][2 * q + 1], S.v[1][0][2 * q + 1]);
   }
   if (!p.hbt) {  // an HBT has no depth
     S.z[0] += ex[4];
@@ -548,10 +545,13 @@ __device__ __forceinline__ void pin_exps_sh(const Pin<T> &p, const WlShared<T, G
   const int s = side ? 1 : 0;
   const T xmx = sh.f[F_EXT + (0 + s) * 4 + 0][grp], xmn = sh.f[F_EXT + (0 + s) * 4 + 2][grp];
   const T ymx = sh.f[F_EXT + (2 + s) * 4 + 0][grp], ymn = sh.f[F_EXT + (2 + s) * 4 + 2][grp];
-  ex[0] = r_exp2((p.px - xmx) * c.inv_g2);
-  ex[1] = r_exp2((xmn - p.px) * c.inv_g2);
-  ex[2] = r_exp2((p.py - ymx) * c.inv_g2);
-  ex[3] = r_exp2((ymn - p.py) * c.inv_g2);
+  T ax, ay, bx, by;  // x and y arguments in step (packed pairs in FP32)
+  submul2(p.px, p.py, xmx, ymx, c.inv_g2, c.inv_g2, ax, ay);
+  submul2(xmn, ymn, p.px, p.py, c.inv_g2, c.inv_g2, bx, by);
+  ex[0] = r_exp2(ax);
+  ex[1] = r_exp2(bx);
+  ex[2] = r_exp2(ay);
+  ex[3] = r_exp2(by);
   ex[4] = r_exp2((p.pz - sh.f[F_Z + 0][grp]) * c.inv_gz2);
   ex[5] = r_exp2((sh.f[F_Z + 1][grp] - p.pz) * c.inv_gz2);
 }
@@ -715,12 +715,17 @@ __global__ void __launch_bounds__(wl_block<T>()) k_wl_group(int net0, int nnets,
         const int s = p.top ? 1 : 0;
         T g[2];
         const T v[2] = {p.px, p.py};
+        T cA[2], cB[2], cC[2], cD[2];
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
           const int b = F_COEF + (a * 2 + s) * 4;
-          const T A = sh.f[b + 0][grp], B = sh.f[b + 1][grp], C = sh.f[b + 2][grp], D = sh.f[b + 3][grp];
-          g[a] = (ex[2 * a] * A) * (T(1) + (v[a] - B) * c.inv_g) - (ex[2 * a + 1] * C) * (T(1) - (v[a] - D) * c.inv_g);
+          cA[a] = sh.f[b + 0][grp];
+          cB[a] = sh.f[b + 1][grp];
+          cC[a] = sh.f[b + 2][grp];
+          cD[a] = sh.f[b + 3][grp];
         }
+        const T ep[2] = {ex[0], ex[2]}, em[2] = {ex[1], ex[3]};
+        wa_grad2(ep, em, v, cA, cB, cC, cD, c.inv_g, g);  // both axes in step
         const T gz = wa_grad(p.pz, ex[4], sh.f[F_ZC + 0][grp], sh.f[F_ZC + 1][grp], ex[5], sh.f[F_ZC + 2][grp],
                              sh.f[F_ZC + 3][grp], c.inv_gz);
         const int ns = s ? ntop : n - ntop, no = n - ns, slot = lane + r * G;
