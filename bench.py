@@ -594,9 +594,9 @@ def main():
                 "frac": ach / hbm_peak if ach else None, "traffic": prof_traffic,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
         if dom == "wirelength":
-            roof["limiter"] = ("instruction issue, not DRAM: ncu shows the group kernels issuing on ~50 % of "
-                               "active cycles at 31 % occupancy (96 registers) with 17-22 % of DRAM peak, "
-                               "about 20 warp instructions per pin (profiles/ncu_wirelength_scatter_cells_1m.md)")
+            roof["limiter"] = ("instruction issue, not DRAM: ncu shows the group kernels issuing on 56-58 % of "
+                               "active cycles at 28 % occupancy (96 registers) with 14-19 % of DRAM peak, "
+                               "16-30 warp instructions per pin (profiles/ncu_wirelength_cells_1m.md)")
     roof["timing"] = ("the stage's kernels timed alone (serial stream, CUDA events over K steps, L2 flushed "
                       "between steps); "
                       f"timed concurrently with the other path: {stages_conc.get(dom, {}).get('gbs')} GB/s")
