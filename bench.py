@@ -411,6 +411,8 @@ def run_batch(a):
                                    f"5k..300k, grids 64x64x2..512x512x4, one CUDA-graph launch per step",
                        "l2": "flushed between timed steps", "parallelism": f"replicas x{world}"},
             "sequential_graphs_evals_per_s": job_throughput(world, a.steps * len(probs), ms_seq),
+            "shared_stages": ("wirelength stage (zeroing, packing, degree groups, norms, reductions): one launch "
+                              "per stage for all 24 instances" if batch.shared_stages() else "none"),
             "e2e": {"value": job_throughput(world, a.steps * len(probs), e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": 12 * n_total, "d2h_bytes_per_step": 12 * n_total},
             "gpu_launches": a.steps * sum(h.launches_per_eval() + 1 for h in hs),

@@ -279,7 +279,8 @@ int place3d_eval_graph(place3d_handle *h, const void *x, const void *y,
  * place3d_eval_graph), captures on first use or when any pointer or any
  * handle's gamma, gamma_z, alpha or reduction form changes (updating the
  * executable graph in place when it can), and launches on cuda_stream after
- * the handles' last parameter writes.  Per-instance results via
+ * the handles' last parameter writes (see place3d_batch_shared_stages for
+ * the launches the instances share).  Per-instance results via
  * place3d_get_result.  Errors: INVALID_ARG, CUDA (the message, naming the
  * failing call or instance, from place3d_last_error(NULL) on the calling
  * thread). */
@@ -291,6 +292,16 @@ int place3d_batch_eval(place3d_batch *b, const void *const *xs,
                        void *const *gxs, void *const *gys, void *const *gzs,
                        int dtype, void *cuda_stream);
 void place3d_batch_destroy(place3d_batch *b);
+/* Stages the last captured batch graph runs as one launch shared by all its
+ * instances: 1 when the wirelength stage (with the zeroing of the scalars
+ * and accumulators, the position packing, the L1 norms and their
+ * reductions) is shared -- every instance FP32 or FP32_TC in 3D mode, float
+ * positions, no net above 128 pins; its launch groups are those of the
+ * instance with the most nets when their forms fit every instance, else the
+ * default plan -- and 0 when each instance runs its own (FP64, 2D mode,
+ * high-fanout nets).  The density path and the transforms stay per
+ * instance (one graph branch each). */
+int place3d_batch_shared_stages(const place3d_batch *b);
 
 /* Enqueue, on the handle's stream, a copy of the last evaluation's scalars
  * into dst (a DEVICE buffer of 10 doubles, in place3d_result order: obj,

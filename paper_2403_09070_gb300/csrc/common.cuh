@@ -229,10 +229,12 @@ __device__ __forceinline__ void block_sum_atomic(T (&v)[NV], double *dst) {
 // rows stay FP32: widening each to FP64 here would put one conversion per
 // warp and value on the FP64 pipe, which is narrow on this GPU.
 // One-dimensional grids with whole warps; every lane must call it.
+// bid: the block's index in its grid (a batched launch passes the block's
+// index within its instance's share of the grid).
 template <int NV, typename T>
-__device__ __forceinline__ void warp_sum_part(T (&v)[NV], T *__restrict__ part) {
+__device__ __forceinline__ void warp_sum_part(T (&v)[NV], T *__restrict__ part, int bid = blockIdx.x) {
   const int lane = threadIdx.x & 31;
-  const size_t row = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const size_t row = ((size_t)bid * blockDim.x + threadIdx.x) >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
     T s = v[k];
@@ -259,13 +261,22 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float v) {
 // the rows' precision (FP32 rows as hi + lo pairs), one block reduction
 // widened to FP64 per warp and one FP64 atomic per block and value.
 constexpr int kSumBlocks = 256;
+// Body of k_sum_parts for block bid of nblk (256 threads each).
+template <int NV, typename TP>
+__device__ __forceinline__ void sum_parts_body(const TP *__restrict__ part, int rows, double *__restrict__ dst,
+                                               int bid, int nblk);
 template <int NV, typename TP>
 __global__ void __launch_bounds__(256) k_sum_parts(const TP *__restrict__ part, int rows,
                                                    double *__restrict__ dst) {
+  sum_parts_body<NV, TP>(part, rows, dst, blockIdx.x, gridDim.x);
+}
+template <int NV, typename TP>
+__device__ __forceinline__ void sum_parts_body(const TP *__restrict__ part, int rows, double *__restrict__ dst,
+                                               int bid, int nblk) {
   TP hi[NV], lo[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) hi[k] = lo[k] = TP(0);
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x)
+  for (int r = bid * blockDim.x + threadIdx.x; r < rows; r += nblk * blockDim.x)
 #pragma unroll
     for (int k = 0; k < NV; ++k) ff_add(hi[k], lo[k], part[(size_t)r * NV + k]);
   __shared__ double red[8][NV];

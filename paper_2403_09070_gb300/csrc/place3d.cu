@@ -19,6 +19,7 @@
 #include "transform.cuh"
 #include "wirelength.cuh"
 #include "nesterov.cuh"
+#include "batch.cuh"
 
 using namespace p3d;
 
@@ -570,13 +571,23 @@ int launch_final_tiles(place3d_handle *h, cudaStream_t s, cudaStream_t ms, bool 
   return PLACE3D_OK;
 }
 
-template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void *gz, int dtype, int mem) {
+// Batch capture with a shared wirelength stage: the scalars, the WL
+// accumulators and the packed positions are set by the batch's own launches
+// before this instance's branch starts, the WL stage runs once for the whole
+// batch, and the final assembly waits for `wl_done` instead of this handle's
+// own WL path.
+struct BatchHook {
+  cudaEvent_t wl_done;
+};
+
+template <typename T>
+int eval_impl(place3d_handle *h, void *gx, void *gy, void *gz, int dtype, int mem, const BatchHook *bh = nullptr) {
   const bool serial = (h->flags & PLACE3D_FLAG_SERIAL) != 0;
   cudaStream_t caller = h->stream, s = serial ? caller : h->dens, w = serial ? caller : h->side;
   const int n = h->n;
   const DensC<T> dc = dens_consts<T>(h, h->xl, h->yl);
   h->launches = 0;
-  P3D_CUDA(h, cudaMemsetAsync(h->scal, 0, sizeof(double) * S_COUNT, caller));  // before the fork: both paths add
+  if (!bh) P3D_CUDA(h, cudaMemsetAsync(h->scal, 0, sizeof(double) * S_COUNT, caller));  // before the fork: both paths add
   P3D_CUDA(h, cudaEventRecord(h->ev_fork, caller));
   if (s != caller) P3D_CUDA(h, cudaStreamWaitEvent(s, h->ev_fork, 0));
   // macros on their own stream (direct field gather, untiled scatter)
@@ -587,31 +598,33 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
   cudaStream_t ms = serial ? s : h->mac;
   if (ms != s) P3D_CUDA(h, cudaStreamWaitEvent(ms, h->ev_fork, 0));
   cudaStream_t mcs = split ? ms : s;  // stream of the macros' kernels
-  // ---------------- wirelength path (side stream) ----------------
-  P3D_CUDA(h, cudaStreamWaitEvent(w, h->ev_fork, 0));
-  {
-    StageScope sc(h, ST_WIRELENGTH, w);
-    P3D_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(V4<T>) * (size_t)std::max(n, 1), w));
-    const WlC<T> c = wl_consts<T>(h);
-    int rows = 0;
-    for (const Bucket &b : h->buckets) {
-      rows += launch_wl<T>(h, b, b.G, b.PPL, w, c, as<T>(h->part_w) + 4 * (size_t)rows);
-      count_launch(h, ST_WIRELENGTH);
+  if (!bh) {  // (in a batch with a shared WL stage, the batch runs it)
+    // ---------------- wirelength path (side stream) ----------------
+    P3D_CUDA(h, cudaStreamWaitEvent(w, h->ev_fork, 0));
+    {
+      StageScope sc(h, ST_WIRELENGTH, w);
+      P3D_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(V4<T>) * (size_t)std::max(n, 1), w));
+      const WlC<T> c = wl_consts<T>(h);
+      int rows = 0;
+      for (const Bucket &b : h->buckets) {
+        rows += launch_wl<T>(h, b, b.G, b.PPL, w, c, as<T>(h->part_w) + 4 * (size_t)rows);
+        count_launch(h, ST_WIRELENGTH);
+      }
+      if (rows > 0) {
+        k_sum_parts<4, T><<<sum_grid(rows), 256, 0, w>>>(as<T>(h->part_w), rows, h->scal + S_WL_BI);
+        count_launch(h, ST_WIRELENGTH);
+      }
     }
-    if (rows > 0) {
-      k_sum_parts<4, T><<<sum_grid(rows), 256, 0, w>>>(as<T>(h->part_w), rows, h->scal + S_WL_BI);
-      count_launch(h, ST_WIRELENGTH);
+    {
+      StageScope sc(h, ST_NORMS, w);
+      const int gn = std::min(grid_for(std::max(n, 1), 256), 1216);
+      k_norms<T><<<gn, 256, 0, w>>>(n, as<V4<T>>(h->acc), as<T>(h->part_w));
+      k_sum_parts<3, T><<<sum_grid(gn * 8), 256, 0, w>>>(as<T>(h->part_w), gn * 8, h->scal + S_SX);
+      count_launch(h, ST_NORMS);
+      count_launch(h, ST_NORMS);
     }
+    P3D_CUDA(h, cudaEventRecord(h->ev_join, w));
   }
-  {
-    StageScope sc(h, ST_NORMS, w);
-    const int gn = std::min(grid_for(std::max(n, 1), 256), 1216);
-    k_norms<T><<<gn, 256, 0, w>>>(n, as<V4<T>>(h->acc), as<T>(h->part_w));
-    k_sum_parts<3, T><<<sum_grid(gn * 8), 256, 0, w>>>(as<T>(h->part_w), gn * 8, h->scal + S_SX);
-    count_launch(h, ST_NORMS);
-    count_launch(h, ST_NORMS);
-  }
-  P3D_CUDA(h, cudaEventRecord(h->ev_join, w));
   // ---------------- density path (caller's stream) ----------------
   {
     StageScope sc(h, ST_SCATTER, s);
@@ -701,7 +714,7 @@ template <typename T> int eval_impl(place3d_handle *h, void *gx, void *gy, void 
     count_launch(h, ST_MACRO_GATHER);
   }
   // ---------------- join + final assembly ----------------
-  P3D_CUDA(h, cudaStreamWaitEvent(s, h->ev_join, 0));
+  P3D_CUDA(h, cudaStreamWaitEvent(s, bh ? bh->wl_done : h->ev_join, 0));
   {
     StageScope sc(h, ST_FINAL, s);
     FinalC<T> fc;
@@ -1809,18 +1822,19 @@ int place3d_wl_forms(const place3d_handle *h, int32_t *dmax, int32_t *lanes, int
 
 // Capture pack + evaluation of one handle on `cs` (the handle's streams are
 // redirected to cs for the capture; the side stream forks from it).
-static int capture_eval(place3d_handle *h, cudaStream_t cs, const void *const *ptr, int dtype) {
+static int capture_eval(place3d_handle *h, cudaStream_t cs, const void *const *ptr, int dtype,
+                        const BatchHook *bh = nullptr) {
   const bool prof = h->profiling;
   cudaStream_t keep = h->stream;
   h->profiling = false;
   h->stream = cs;
-  int rc = enqueue_pack(h, ptr[0], ptr[1], ptr[2], dtype);
+  int rc = bh ? PLACE3D_OK : enqueue_pack(h, ptr[0], ptr[1], ptr[2], dtype);  // (the batch packs)
   if (rc == PLACE3D_OK)
     rc = h->precision == PLACE3D_FP64
              ? eval_impl<double>(h, const_cast<void *>(ptr[3]), const_cast<void *>(ptr[4]), const_cast<void *>(ptr[5]),
-                                 dtype, PLACE3D_MEM_DEVICE)
+                                 dtype, PLACE3D_MEM_DEVICE, bh)
              : eval_impl<float>(h, const_cast<void *>(ptr[3]), const_cast<void *>(ptr[4]), const_cast<void *>(ptr[5]),
-                                dtype, PLACE3D_MEM_DEVICE);
+                                dtype, PLACE3D_MEM_DEVICE, bh);
   h->stream = keep;
   h->profiling = prof;
   return rc;
@@ -2011,10 +2025,32 @@ struct place3d_batch {
   std::vector<unsigned> versions;  // each handle's parameter version at capture
   int dtype = -1, device = 0;
   std::string err;
+  // shared wirelength stage (one launch per stage for every instance):
+  // its stream, the events after the packing and after the stage, the
+  // per-instance descriptors and the block-prefix tables of its launches
+  bool shared_wl = false;
+  cudaStream_t wls = nullptr;
+  cudaEvent_t ev_prep = nullptr, ev_wl = nullptr;
+  BWl *d_wl = nullptr;
+  int *d_tab = nullptr;
+};
+
+// Host plan of the shared wirelength stage: per launch, its kernel form,
+// its grid, and the offset of its block-prefix table in d_tab.
+struct BatchWlPlan {
+  int ngroups = 0;
+  int G[kBatchGroups], PPL[kBatchGroups];
+  int grid[kBatchGroups + 4], tab[kBatchGroups + 4];  // groups, then prep, sum, norms, norm sums
+  int norm_rows_tab = 0;                              // offset of the per-instance norm-row counts
 };
 
 static void batch_free(place3d_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->wls) cudaStreamDestroy(b->wls);
+  if (b->ev_prep) cudaEventDestroy(b->ev_prep);
+  if (b->ev_wl) cudaEventDestroy(b->ev_wl);
+  if (b->d_wl) cudaFree(b->d_wl);
+  if (b->d_tab) cudaFree(b->d_tab);
   for (auto s : b->streams) cudaStreamDestroy(s);
   for (auto e : b->done) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -2053,6 +2089,140 @@ int place3d_batch_create(place3d_handle *const *handles, int count, place3d_batc
   return PLACE3D_OK;
 }
 
+// Whether every instance can join the shared wirelength stage (FP32
+// arithmetic, 3D mode, float positions, no net above 128 pins), and the
+// common launch groups: the plan of the instance with the most nets, if its
+// forms fit every instance's degree classes, else the default plan.
+static bool batch_wl_plan(const place3d_batch *b, int dtype, BatchWlPlan &pl, std::vector<BWl> &desc,
+                          std::vector<int> &tab, const std::vector<const void *> &ptr) {
+  if (dtype != PLACE3D_F32) return false;
+  const place3d_handle *big = nullptr;
+  for (const place3d_handle *h : b->hs) {
+    if (h->precision == PLACE3D_FP64 || h->mode2d || h->profiling) return false;
+    if (!h->fine.empty() && h->fine.back().dmax > 128) return false;
+    if (!big || h->nnet > big->nnet) big = h;
+  }
+  std::vector<int> bound, fg, fp;
+  for (const Bucket &g : big->buckets) {
+    bound.push_back(g.dmax);
+    fg.push_back(g.G);
+    fp.push_back(g.PPL);
+  }
+  if (!bound.empty()) bound.back() = 128;  // the last group takes every class up to 128 pins
+  auto fits = [&](void) {
+    for (const place3d_handle *h : b->hs)
+      for (const Bucket &c : h->fine) {
+        size_t g = 0;
+        while (g < bound.size() && c.dmax > bound[g]) ++g;
+        if (g == bound.size() || !form_fits(h, c.dmax, fg[g], fp[g])) return false;
+      }
+    return true;
+  };
+  if (bound.empty() || (int)bound.size() > kBatchGroups || !fits()) {
+    bound.assign(kDefaultGroupMax, kDefaultGroupMax + 7);
+    fg.clear();
+    fp.clear();
+    for (int g = 0; g < 7; ++g) {
+      fg.push_back(kDefaultForm[g][0]);
+      fp.push_back(kDefaultForm[g][1]);
+    }
+    if (!fits()) return false;
+  }
+  const int ng = (int)bound.size(), nh = (int)b->hs.size();
+  pl.ngroups = ng;
+  for (int g = 0; g < ng; ++g) {
+    pl.G[g] = fg[g];
+    pl.PPL[g] = fp[g];
+  }
+  desc.assign(nh, BWl{});
+  std::vector<std::vector<int>> blocks(ng + 4, std::vector<int>(nh, 0));
+  std::vector<int> nrows(nh, 0);
+  constexpr int BS = wl_block<float>();
+  for (int i = 0; i < nh; ++i) {
+    const place3d_handle *h = b->hs[i];
+    BWl &w = desc[i];
+    w.n = h->n;
+    w.x = (const float *)ptr[6 * i];
+    w.y = (const float *)ptr[6 * i + 1];
+    w.z = (const float *)ptr[6 * i + 2];
+    w.pos = as<V4<float>>(h->pos);
+    w.acc = as<V4<float>>(h->acc);
+    w.off = as<V4<float>>(h->off);
+    w.net_start = h->net_start;
+    w.pin_inst = h->pin_inst;
+    w.part = as<float>(h->part_w);
+    w.scal = h->scal;
+    w.c = wl_consts<float>(h);
+    int row = 0;
+    size_t k = 0;
+    for (int g = 0; g < ng; ++g) {
+      w.gfirst[g] = w.gcount[g] = w.gpin0[g] = 0;
+      bool first = true;
+      while (k < h->fine.size() && h->fine[k].dmax <= bound[g]) {
+        if (first) {
+          w.gfirst[g] = h->fine[k].first;
+          w.gpin0[g] = h->fine[k].pin0;
+          first = false;
+        }
+        w.gcount[g] += h->fine[k].count;
+        ++k;
+      }
+      const bool pair = fg[g] == 1 && fp[g] == 1;
+      const int nb = w.gcount[g] == 0 ? 0
+                     : pair       ? grid_for(w.gcount[g], 256 * kPairNets)
+                                  : grid_for((long long)w.gcount[g] * fg[g], BS);
+      blocks[g][i] = nb;
+      w.grow[g] = row;
+      row += nb * (pair ? 256 / 32 : BS / 32);
+    }
+    w.rows_wl = row;
+    const int gn = std::min(grid_for(std::max(h->n, 1), 256), 1216);
+    blocks[ng][i] = std::min(grid_for(std::max(h->n, 1), 256), 1024);  // prep
+    blocks[ng + 1][i] = sum_grid(std::max(row, 1));                     // WL rows -> scalars
+    blocks[ng + 2][i] = gn;                                              // norms
+    nrows[i] = gn * 8;
+    blocks[ng + 3][i] = sum_grid(gn * 8);                                // norm rows -> scalars
+  }
+  tab.clear();
+  for (int l = 0; l < ng + 4; ++l) {
+    pl.tab[l] = (int)tab.size();
+    int acc = 0;
+    for (int i = 0; i < nh; ++i) {
+      tab.push_back(acc);
+      acc += blocks[l][i];
+    }
+    tab.push_back(acc);
+    pl.grid[l] = acc;
+  }
+  pl.norm_rows_tab = (int)tab.size();
+  tab.insert(tab.end(), nrows.begin(), nrows.end());
+  return true;
+}
+
+// The shared wirelength stage's launches on stream w.
+static void batch_wl_launch(const place3d_batch *b, const BatchWlPlan &pl, cudaStream_t w) {
+  const int nh = (int)b->hs.size(), ng = pl.ngroups;
+  for (int g = 0; g < ng; ++g) {
+    const int grid = pl.grid[g];
+    if (grid == 0) continue;
+    const int *t = b->d_tab + pl.tab[g];
+    const int G = pl.G[g], PPL = pl.PPL[g];
+    if (G == 1 && PPL == 1) {
+      k_b_wl_pair<<<grid, 256, 0, w>>>(b->d_wl, t, nh, g);
+      continue;
+    }
+#define P3D_BWL(GG, PP) \
+  if (G == GG && PPL == PP) k_b_wl_group<GG, PP><<<grid, wl_block<float>(), 0, w>>>(b->d_wl, t, nh, g);
+    P3D_BWL(1, 2) P3D_BWL(1, 4) P3D_BWL(2, 2) P3D_BWL(4, 1) P3D_BWL(2, 4) P3D_BWL(8, 1) P3D_BWL(4, 4)
+    P3D_BWL(16, 1) P3D_BWL(8, 4) P3D_BWL(32, 1) P3D_BWL(16, 4) P3D_BWL(32, 2) P3D_BWL(32, 4)
+#undef P3D_BWL
+  }
+  k_b_sum_wl<<<pl.grid[ng + 1], 256, 0, w>>>(b->d_wl, b->d_tab + pl.tab[ng + 1], nh);
+  k_b_norms<<<pl.grid[ng + 2], 256, 0, w>>>(b->d_wl, b->d_tab + pl.tab[ng + 2], nh);
+  k_b_sum_norms<<<pl.grid[ng + 3], 256, 0, w>>>(b->d_wl, b->d_tab + pl.tab[ng + 3], b->d_tab + pl.norm_rows_tab,
+                                                 nh);
+}
+
 int place3d_batch_eval(place3d_batch *b, const void *const *xs, const void *const *ys, const void *const *zs,
                        void *const *gxs, void *const *gys, void *const *gzs, int dtype, void *cuda_stream) {
   if (!b || !xs || !ys || !zs || !gxs || !gys || !gzs) return fail(nullptr, PLACE3D_ERR_INVALID_ARG, "NULL argument");
@@ -2071,6 +2241,27 @@ int place3d_batch_eval(place3d_batch *b, const void *const *xs, const void *cons
   for (auto *h : b->hs) vers.push_back(h->version);
   if (!b->exec || b->dtype != dtype || b->ptrs != ptr || b->versions != vers) {
     for (auto *h : b->hs) P3D_CUDA(nullptr, cudaStreamSynchronize(h->stream));
+    // shared wirelength stage: descriptors and block tables uploaded before
+    // the capture (they hold this capture's pointers and plans)
+    BatchWlPlan pl;
+    std::vector<BWl> desc;
+    std::vector<int> tab;
+    b->shared_wl = batch_wl_plan(b, dtype, pl, desc, tab, ptr);
+    if (b->shared_wl) {
+      if (!b->wls) {
+        P3D_CUDA(nullptr, cudaStreamCreateWithFlags(&b->wls, cudaStreamNonBlocking));
+        P3D_CUDA(nullptr, cudaEventCreateWithFlags(&b->ev_prep, cudaEventDisableTiming));
+        P3D_CUDA(nullptr, cudaEventCreateWithFlags(&b->ev_wl, cudaEventDisableTiming));
+      }
+      if (b->d_wl) cudaFree(b->d_wl);
+      if (b->d_tab) cudaFree(b->d_tab);
+      b->d_wl = nullptr;
+      b->d_tab = nullptr;
+      P3D_CUDA(nullptr, cudaMalloc((void **)&b->d_wl, sizeof(BWl) * desc.size()));
+      P3D_CUDA(nullptr, cudaMalloc((void **)&b->d_tab, sizeof(int) * tab.size()));
+      P3D_CUDA(nullptr, cudaMemcpy(b->d_wl, desc.data(), sizeof(BWl) * desc.size(), cudaMemcpyHostToDevice));
+      P3D_CUDA(nullptr, cudaMemcpy(b->d_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice));
+    }
     P3D_CUDA(nullptr, cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal));
     int rc = PLACE3D_OK;
     std::string why;
@@ -2079,13 +2270,33 @@ int place3d_batch_eval(place3d_batch *b, const void *const *xs, const void *cons
       rc = PLACE3D_ERR_CUDA;
       why = std::string("cudaEventRecord(fork): ") + cudaGetErrorString(ce);
     }
+    BatchHook hook{b->ev_wl};
+    cudaEvent_t start = b->fork;
+    if (rc == PLACE3D_OK && b->shared_wl) {
+      // scalars and accumulators zeroed, positions packed: one launch, then
+      // the wirelength stage of every instance on its own stream
+      const int ng = pl.ngroups;
+      k_b_prep<<<pl.grid[ng], 256, 0, b->root>>>(b->d_wl, b->d_tab + pl.tab[ng], n);
+      if ((ce = cudaGetLastError()) != cudaSuccess || (ce = cudaEventRecord(b->ev_prep, b->root)) != cudaSuccess ||
+          (ce = cudaStreamWaitEvent(b->wls, b->ev_prep, 0)) != cudaSuccess) {
+        rc = PLACE3D_ERR_CUDA;
+        why = std::string("shared wirelength stage: ") + cudaGetErrorString(ce);
+      } else {
+        batch_wl_launch(b, pl, b->wls);
+        if ((ce = cudaGetLastError()) != cudaSuccess || (ce = cudaEventRecord(b->ev_wl, b->wls)) != cudaSuccess) {
+          rc = PLACE3D_ERR_CUDA;
+          why = std::string("shared wirelength stage: ") + cudaGetErrorString(ce);
+        }
+      }
+      start = b->ev_prep;
+    }
     for (int i = 0; i < n && rc == PLACE3D_OK; ++i) {
-      if ((ce = cudaStreamWaitEvent(b->streams[i], b->fork, 0)) != cudaSuccess) {
+      if ((ce = cudaStreamWaitEvent(b->streams[i], start, 0)) != cudaSuccess) {
         rc = PLACE3D_ERR_CUDA;
         why = std::string("cudaStreamWaitEvent(fork): ") + cudaGetErrorString(ce);
         break;
       }
-      rc = capture_eval(b->hs[i], b->streams[i], &ptr[6 * i], dtype);
+      rc = capture_eval(b->hs[i], b->streams[i], &ptr[6 * i], dtype, b->shared_wl ? &hook : nullptr);
       if (rc != PLACE3D_OK) {
         why = "instance " + std::to_string(i) + ": " + b->hs[i]->err;
         break;
@@ -2095,6 +2306,10 @@ int place3d_batch_eval(place3d_batch *b, const void *const *xs, const void *cons
         rc = PLACE3D_ERR_CUDA;
         why = std::string("joining instance ") + std::to_string(i) + ": " + cudaGetErrorString(ce);
       }
+    }
+    if (rc == PLACE3D_OK && b->shared_wl && (ce = cudaStreamWaitEvent(b->root, b->ev_wl, 0)) != cudaSuccess) {
+      rc = PLACE3D_ERR_CUDA;
+      why = std::string("joining the shared wirelength stage: ") + cudaGetErrorString(ce);
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(b->root, &graph);
@@ -2117,6 +2332,8 @@ int place3d_batch_eval(place3d_batch *b, const void *const *xs, const void *cons
   }
   return PLACE3D_OK;
 }
+
+int place3d_batch_shared_stages(const place3d_batch *b) { return b && b->exec && b->shared_wl ? 1 : 0; }
 
 void place3d_batch_destroy(place3d_batch *b) {
   if (!b) return;

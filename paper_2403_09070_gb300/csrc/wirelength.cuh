@@ -443,12 +443,24 @@ __device__ __forceinline__ void pair_net(const Pin<T> &a, const Pin<T> &b, const
   vals[3] += a.top != b.top ? T(1) : T(0);
 }
 
+// Body for block bid of nblk (a batched launch passes the block's place in
+// its instance's share of the grid).
+template <typename T>
+__device__ __forceinline__ void wl_pair_body(int pin0, int nnets, const int *__restrict__ pin_inst,
+                                             const V4<T> *__restrict__ off, const V4<T> *__restrict__ pos, WlC<T> c,
+                                             V4<T> *__restrict__ acc, T *__restrict__ part, int bid, int nblk);
 template <typename T>
 __global__ void __launch_bounds__(256) k_wl_pair(int pin0, int nnets,
                                                  const int *__restrict__ pin_inst, const V4<T> *__restrict__ off,
                                                  const V4<T> *__restrict__ pos, WlC<T> c, V4<T> *__restrict__ acc,
                                                  T *__restrict__ part) {
-  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  wl_pair_body<T>(pin0, nnets, pin_inst, off, pos, c, acc, part, blockIdx.x, gridDim.x);
+}
+template <typename T>
+__device__ __forceinline__ void wl_pair_body(int pin0, int nnets, const int *__restrict__ pin_inst,
+                                             const V4<T> *__restrict__ off, const V4<T> *__restrict__ pos, WlC<T> c,
+                                             V4<T> *__restrict__ acc, T *__restrict__ part, int bid, int nblk) {
+  const int t0 = bid * blockDim.x + threadIdx.x, nth = nblk * blockDim.x;
   T vals[4] = {0, 0, 0, 0};
   int ia[kPairNets], ib[kPairNets];
   V4<T> oa[kPairNets], ob[kPairNets], sa[kPairNets], sb[kPairNets];
@@ -491,7 +503,7 @@ __global__ void __launch_bounds__(256) k_wl_pair(int pin0, int nnets,
     }
     pair_net(pa, pb, c, acc, vals);
   }
-  warp_sum_part<4>(vals, part);  // (W^_Bi, p^(z), W_Bi, crossing) rows
+  warp_sum_part<4>(vals, part, bid);  // (W^_Bi, p^(z), W_Bi, crossing) rows
 }
 
 // ---- nets of degree <= G*PPL, one group of G lanes per net ----
@@ -579,19 +591,33 @@ __device__ __forceinline__ T moved_sh(const WlShared<T, GR> &sh, int grp, int a,
 
 // M2D: multi-die 2D mode (compile-time, so the 3D kernels carry none of the
 // HBT and partial-net-only cases).
+// Body for block bid (a batched launch passes the block's place in its
+// instance's share of the grid).
+template <typename T, int G, int PPL, bool M2D>
+__device__ __forceinline__ void wl_group_body(int net0, int nnets, const int *__restrict__ net_start,
+                                              const int *__restrict__ pin_inst, const V4<T> *__restrict__ off,
+                                              const V4<T> *__restrict__ pos, WlC<T> c0, V4<T> *__restrict__ acc,
+                                              T *__restrict__ part, int bid);
 template <typename T, int G, int PPL, bool M2D>
 __global__ void __launch_bounds__(wl_block<T>()) k_wl_group(int net0, int nnets, const int *__restrict__ net_start,
                                                             const int *__restrict__ pin_inst,
                                                             const V4<T> *__restrict__ off,
                                                             const V4<T> *__restrict__ pos, WlC<T> c0,
                                                             V4<T> *__restrict__ acc, T *__restrict__ part) {
+  wl_group_body<T, G, PPL, M2D>(net0, nnets, net_start, pin_inst, off, pos, c0, acc, part, blockIdx.x);
+}
+template <typename T, int G, int PPL, bool M2D>
+__device__ __forceinline__ void wl_group_body(int net0, int nnets, const int *__restrict__ net_start,
+                                              const int *__restrict__ pin_inst, const V4<T> *__restrict__ off,
+                                              const V4<T> *__restrict__ pos, WlC<T> c0, V4<T> *__restrict__ acc,
+                                              T *__restrict__ part, int bid) {
   WlC<T> c = c0;
   c.mode2d = M2D ? 1 : 0;
   constexpr int GR = wl_block<T>() / G;  // groups (nets) per block
   __shared__ WlShared<T, GR> sh;
   const int lane = threadIdx.x & (G - 1);
   const int grp = threadIdx.x / G;
-  const int gid = blockIdx.x * GR + grp;
+  const int gid = bid * GR + grp;
   const bool valid = gid < nnets;
   int s0 = 0, d = 0;
   if (valid) {
@@ -734,7 +760,7 @@ __global__ void __launch_bounds__(wl_block<T>()) k_wl_group(int net0, int nnets,
         acc_add(acc + p.inst, g[0], g[1], fd, gz);
       }
   }
-  warp_sum_part<4>(vals, part);  // (W^_Bi, p^(z), W_Bi, crossing) rows
+  warp_sum_part<4>(vals, part, bid);  // (W^_Bi, p^(z), W_Bi, crossing) rows
 }
 
 // ---- high-fanout nets, split across blocks ----
@@ -866,15 +892,20 @@ __global__ void __launch_bounds__(256) k_wl_big_out(WlBig bg, const int *__restr
 
 // ---- a9: L1 norms S_x, S_y, S_z of the wirelength gradient (FP64) ----
 template <typename T>
-__global__ void __launch_bounds__(256) k_norms(int n, const V4<T> *__restrict__ acc, T *__restrict__ part) {
+__device__ __forceinline__ void norms_body(int n, const V4<T> *__restrict__ acc, T *__restrict__ part, int bid,
+                                           int nblk) {
   T v[3] = {0, 0, 0};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
     const V4<T> a = acc[i];
     v[0] += fabs(a.x);
     v[1] += fabs(a.y);
     v[2] += fabs(a.z);
   }
-  warp_sum_part<3>(v, part);  // (S_x, S_y, S_z) rows
+  warp_sum_part<3>(v, part, bid);  // (S_x, S_y, S_z) rows
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_norms(int n, const V4<T> *__restrict__ acc, T *__restrict__ part) {
+  norms_body<T>(n, acc, part, blockIdx.x, gridDim.x);
 }
 
 }  // namespace p3d

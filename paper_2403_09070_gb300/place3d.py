@@ -72,7 +72,7 @@ EXPORTS = ("place3d_create", "place3d_geometry", "place3d_alpha", "place3d_set_p
            "place3d_tc_timeout_selftest", "place3d_debug_fail_alloc", "place3d_ll2f_selftest",
            "place3d_graph_captures", "place3d_nesterov_init", "place3d_nesterov_precondition",
            "place3d_nesterov_update", "place3d_nesterov_step", "place3d_set_wl_plan", "place3d_tc_tiles",
-           "place3d_set_tc_tiles")
+           "place3d_set_tc_tiles", "place3d_batch_shared_stages")
 NOALLOC_MAX_BINS = 262144
 
 _lib = None
@@ -121,6 +121,7 @@ def load_library(build_if_missing: bool = True):
     L.place3d_batch_eval.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, vp]
     L.place3d_batch_destroy.argtypes = [vp]
     L.place3d_batch_destroy.restype = None
+    L.place3d_batch_shared_stages.argtypes = [vp]
     L.place3d_set_params.argtypes = [vp, d, d, d, d]
     L.place3d_set_layer_weights.argtypes = [vp, vp]
     L.place3d_wl_forms.argtypes = [vp, vp, vp, vp, i32]
@@ -489,6 +490,11 @@ class Batch:
         rc = self._L.place3d_batch_eval(self._b, *arrs, dts.pop(), C.c_void_p(stream or 0))
         if rc != 0:
             raise Place3DError(rc, "place3d_batch_eval: " + self._L.place3d_last_error(None).decode())
+
+    def shared_stages(self) -> int:
+        """1 when the last captured batch graph shares the wirelength stage's
+        launches among its instances, 0 when each instance runs its own."""
+        return int(self._L.place3d_batch_shared_stages(self._b))
 
     def close(self):
         if getattr(self, "_b", None):

@@ -54,6 +54,7 @@ def test_batch_of_uneven_instances_in_one_graph():
     for rep in range(2):
         b.eval(*[[v[k] for v in xyz] for k in range(3)], *[[v[k] for v in gs] for k in range(3)])
         torch.cuda.synchronize()
+        assert b.shared_stages() == 1  # the wirelength stage: one launch per stage for all instances
         for p, h, v, g in zip(probs, hs, xyz, gs):
             prec = "fp32_tc" if p["nx"] % 128 == 0 else "fp32"
             r = h.get_result()
@@ -157,3 +158,24 @@ def test_tensor_core_tile_widths_agree(cols):
             out.append((r["energy"], h.copy_map(P.MAP_EX)))
     assert out[1][0] == pytest.approx(out[0][0], rel=1e-6)
     np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-5, atol=1e-5 * np.abs(out[0][1]).max())
+
+
+def test_fp64_batch_runs_each_instance_on_its_own():
+    """An FP64 batch has no shared stage (each instance's graph branch runs
+    its whole evaluation) and equals the plain evaluations."""
+    probs = synth.make_batch(count=3, seed=13, n_min=3000, n_max=9000)
+    hs = [P.Place3D(p, precision="fp64") for p in probs]
+    xyz = [[torch.tensor(p[k], device="cuda", dtype=torch.float64) for k in ("x", "y", "z")] for p in probs]
+    gs = [[torch.empty(p["n_inst"], device="cuda", dtype=torch.float64) for _ in range(3)] for p in probs]
+    b = P.Batch(hs)
+    b.eval(*[[v[k] for v in xyz] for k in range(3)], *[[v[k] for v in gs] for k in range(3)])
+    torch.cuda.synchronize()
+    assert b.shared_stages() == 0
+    for p, h, v, g in zip(probs, hs, xyz, gs):
+        ref, gref = _plain(p, "fp64", *(t.cpu().numpy() for t in v))
+        assert h.get_result()["obj"] == pytest.approx(ref["obj"], rel=1e-10)
+        for a, c in zip(g, gref):
+            np.testing.assert_allclose(a.cpu().numpy(), c, rtol=1e-10, atol=1e-10 * np.abs(c).max())
+    b.close()
+    for h in hs:
+        h.close()

@@ -151,7 +151,8 @@ def test_device_nesterov_loop_follows_oracle_loop(positions):
 
 def test_batch24_every_instance_matches_oracle():
     """The 24 uneven instances of the batching workload (5k-300k cells, grids
-    64x64x2 to 512x512x4), evaluated by ONE batch graph launch: every
+    64x64x2 to 512x512x4), evaluated by ONE batch graph launch (the
+    wirelength stage shared by all instances, one launch per stage): every
     instance's fixed-point map equals the oracle's float replica bit for bit,
     its objective is within 2e-5 and each gradient component within 1e-4
     (L2) of the FP64 oracle."""
@@ -166,6 +167,7 @@ def test_batch24_every_instance_matches_oracle():
     b = P.Batch(hs)
     b.eval(*[[v[k] for v in xyz] for k in range(3)], *[[v[k] for v in gs] for k in range(3)])
     torch.cuda.synchronize()
+    assert b.shared_stages() == 1  # the wirelength stage shared by the 24 instances
     for p, h, v, g in zip(probs, hs, xyz, gs):
         r = h.get_result()
         qmap = h.copy_map(P.MAP_RHO_FIXED)
