@@ -72,9 +72,10 @@ extern "C" {
  * uses one thread per cell
  * with global int64 atomics and global field loads instead.  Both give the
  * same fixed-point map bit for bit and the same gradient up to rounding.
- * The tiled form is the default from 100,000 instances up (below that the
- * sort's extra launches cost more than they save); PLACE3D_FLAG_TILES asks
- * for it at any size.  It needs fewer than 2^24 instances, at most 8192
+ * The tiled form is the default in 3D mode from 100,000 instances up (below
+ * that the sort's extra launches cost more than they save, and in 2D mode an
+ * instance covers too few bins for the sort to pay); PLACE3D_FLAG_TILES asks
+ * for it in any case.  It needs fewer than 2^24 instances, at most 8192
  * tiles and a halo of at most 8 bins (cells at most ~16 bins wide);
  * otherwise the per-cell form is used.  An evaluation whose gradient goes
  * to page-locked host arrays gathers per cell (its host stores then overlap

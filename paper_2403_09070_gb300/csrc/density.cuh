@@ -744,12 +744,13 @@ __global__ void __launch_bounds__(256) k_scatter_tiles(const int2 *__restrict__ 
 #pragma unroll
         for (int bb = 0; bb < 3; ++bb) t[bb][a] = rn_mul(wo, oy[bb]);
       }
-      // all 27 slots without branches: a slot past the cuboid's last bin has a
-      // zero overlap, so its value is 0 and its (possibly out-of-window) add is
-      // skipped by predicate
+      // the cuboid's z bins (3 in 3D mode nearly always, 1 in 2D mode: the
+      // same count across a warp), each with 9 (y, x) slots without
+      // branches: a slot past the cuboid's last bin has a zero overlap, so
+      // its value is 0 and its (possibly out-of-window) add is skipped by
+      // predicate
       const int wbase = (b0[2] * tc.WY + (b0[1] - y0)) * tc.WX + (b0[0] - x0);
-#pragma unroll
-      for (int cz = 0; cz < 3; ++cz)
+      for (int cz = 0; cz < nzb; ++cz)
 #pragma unroll
         for (int bb = 0; bb < 3; ++bb) {
           const int wrow = wbase + (cz * tc.WY + bb) * tc.WX;
@@ -840,15 +841,16 @@ __global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ it
         axis_ov3(cl[0], chh[0], b0[0], nxb, ox);
         axis_ov3(cl[1], chh[1], b0[1], nyb, oy);
         axis_ov3(cl[2], chh[2], b0[2], nzb, oz);
-        // all 27 slots without branches: a slot past the cuboid's last bin has
-        // weight 0 and reads the cuboid's first bin (always in the window)
+        // the cuboid's z bins (3 in 3D mode nearly always, 1 in 2D mode),
+        // each with 9 (y, x) slots without branches: a slot past the
+        // cuboid's last bin has weight 0 and reads the cuboid's first bin of
+        // that row (always in the window)
         const int wbase = (b0[2] * tc.WY + (b0[1] - y0)) * tc.WX + (b0[0] - x0);
-#pragma unroll
-        for (int cz = 0; cz < 3; ++cz)
+        for (int cz = 0; cz < nzb; ++cz)
 #pragma unroll
           for (int bb = 0; bb < 3; ++bb) {
             const T oyz = oy[bb] * oz[cz];
-            const int wrow = wbase + (cz < nzb ? cz : 0) * tc.WY * tc.WX + (bb < nyb ? bb : 0) * tc.WX;
+            const int wrow = wbase + cz * tc.WY * tc.WX + (bb < nyb ? bb : 0) * tc.WX;
 #pragma unroll
             for (int aa = 0; aa < 3; ++aa) {
               const V4<T> e = fw[wrow + (aa < nxb ? aa : 0)];

@@ -1111,8 +1111,10 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
     h->smem_scatter = wbins * 8;  // two 32-bit words per bin
     h->smem_final = wbins * 4 * (p->precision == PLACE3D_FP64 ? 8 : 4);  // one (E_x, E_y, E_z, -) vector per bin
     // small problems are launch-bound: the sort's extra launches do not pay
-    // below kTileMinInst instances unless PLACE3D_FLAG_TILES asks for tiles
-    const bool want = (p->flags & PLACE3D_FLAG_TILES) || n >= kTileMinInst;
+    // below kTileMinInst instances; in 2D mode an instance covers one layer
+    // (about 6 bins instead of 17), too little work per cell for the sort to
+    // pay; PLACE3D_FLAG_TILES asks for tiles anyway
+    const bool want = (p->flags & PLACE3D_FLAG_TILES) || (n >= kTileMinInst && p->mode != PLACE3D_MODE_2D);
     h->tiles = want && !(p->flags & PLACE3D_FLAG_NO_TILES) && R <= 8 && h->ntiles <= 8192 && n < (1 << 24) &&
                h->smem_final <= 200 * 1024 && h->smem_scatter <= 200 * 1024;
     h->max_items = (n + kChunk - 1) / kChunk + h->ntiles;

@@ -31,11 +31,11 @@ def _problem2d(wl="cells_2k", seed=3, big_net=0, **kw):
     return synth.to_problem2d(p, seed=seed, lam_layer=LAM)
 
 
-def _run(q, precision, pos=None):
+def _run(q, precision, pos=None, flags=0):
     from paper_2403_09070_gb300 import place3d as P
     dt = np.float64 if precision == "fp64" else np.float32
     x, y, z = (np.asarray(q[k] if pos is None else pos[i], dt) for i, k in enumerate(("x", "y", "z")))
-    with P.Place3D(q, precision=precision) as h:
+    with P.Place3D(q, precision=precision, flags=flags) as h:
         h.set_positions(x, y, z)
         g = [np.zeros(q["n_inst"], dt) for _ in range(3)]
         r = h.eval(*g)
@@ -43,8 +43,8 @@ def _run(q, precision, pos=None):
     return r, g, qmap, [a.astype(np.float64) for a in (x, y, z)]
 
 
-def _check(q, precision):
-    r, g, qmap, (x, y, z) = _run(q, precision)
+def _check(q, precision, flags=0):
+    r, g, qmap, (x, y, z) = _run(q, precision, flags=flags)
     o = Oracle(q)
     assert np.array_equal(qmap, o.density_fixed(x, y, z, use_float=precision != "fp64")), "2D fixed-point maps"
     if precision == "fp64":
@@ -71,6 +71,14 @@ def _check(q, precision):
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_2d_cells_2k(precision):
     _check(_problem2d(), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_2d_tiled_density_path(precision):
+    """The tile-sorted scatter and gather forced in 2D mode (PLACE3D_FLAG_TILES;
+    the default there is per cell): every instance in one layer, HBTs on the
+    third, the same maps and gradients."""
+    _check(_problem2d(), precision, flags=16)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
