@@ -36,14 +36,17 @@ using namespace p3d;
 // Tile shapes: M = 128 rows, K-blocks of 64, and N = 64 or 128 columns
 // (chosen per product group by the autotuner: N = 128 reads each A tile for
 // twice the outputs, N = 64 gives twice the tiles to spread over the SMs).
-// Pipeline depth: 4 stages of 48 KiB (N = 64) or 3 stages of 64 KiB
-// (N = 128), one persistent CTA per SM.
+// Pipeline depth: 3 stages of 48 KiB (N = 64) or of 64 KiB (N = 128), one
+// persistent CTA per SM.  (A fourth 48 KiB stage measured no faster alone,
+// and it left too little shared memory beside the CTA for the wirelength
+// blocks that run concurrently on the other stream: the evaluation was
+// 2 % slower.)
 constexpr int BM = 128, BK = 64;
 constexpr int A_BYTES = BM * BK * 2;  // one BF16 plane of an A tile (16 KiB)
 template <int BN> struct TileCfg {
   static constexpr int W_BYTES = BN * BK * 2;                    // one BF16 plane of a W tile
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * W_BYTES;  // A hi, A lo, W hi, W lo
-  static constexpr int STAGES = BN == 64 ? 4 : 3;
+  static constexpr int STAGES = 3;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
   static constexpr int TMEM_COLS = BN;  // FP32 accumulator columns of one buffer (two are allocated)
   // instruction descriptor: D FP32, A and B BF16, both K-major, M = BM, N = BN
