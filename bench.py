@@ -610,6 +610,7 @@ def main():
         h.set_positions(*hx)
         h.eval(*hg, sync=True)
     e2e_s = 0.0
+    torch.cuda.nvtx.range_push("timed_e2e")
     for _ in range(a.steps):
         flush.zero_()
         torch.cuda.synchronize()
@@ -617,6 +618,7 @@ def main():
         h.set_positions(*hx)
         r2 = h.eval(*hg, sync=True)
         e2e_s += time.perf_counter() - t0
+    torch.cuda.nvtx.range_pop()
     e2e_ms = max_over_ranks(e2e_s * 1000.0, dist if world > 1 else None, "cuda")
     h.close()
 
