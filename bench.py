@@ -369,7 +369,9 @@ def run_batch(a):
     torch.cuda.synchronize()
     clk = Clocks(local)
     clk.start()
+    torch.cuda.nvtx.range_push("timed_batch")
     ms = timed(one_graph, a.steps)
+    torch.cuda.nvtx.range_pop()
     per_step = timed.last
     extend_clock_window(clk, one_graph, torch)
     clocks = clk.stop()
