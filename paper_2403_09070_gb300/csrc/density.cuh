@@ -750,7 +750,7 @@ __global__ void __launch_bounds__(256) k_scatter_tiles(const int2 *__restrict__ 
       // its value is 0 and its (possibly out-of-window) add is skipped by
       // predicate
       const int wbase = (b0[2] * tc.WY + (b0[1] - y0)) * tc.WX + (b0[0] - x0);
-      for (int cz = 0; cz < nzb; ++cz)
+      auto slots = [&](int cz) {
 #pragma unroll
         for (int bb = 0; bb < 3; ++bb) {
           const int wrow = wbase + (cz * tc.WY + bb) * tc.WX;
@@ -764,6 +764,13 @@ __global__ void __launch_bounds__(256) k_scatter_tiles(const int2 *__restrict__ 
             }
           }
         }
+      };
+      if (nzb == 3) {  // the usual 3D case, fully unrolled
+#pragma unroll
+        for (int cz = 0; cz < 3; ++cz) slots(cz);
+      } else {
+        for (int cz = 0; cz < nzb; ++cz) slots(cz);
+      }
       continue;
     }
     T ez = (T)b0[2];
@@ -846,7 +853,7 @@ __global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ it
         // cuboid's last bin has weight 0 and reads the cuboid's first bin of
         // that row (always in the window)
         const int wbase = (b0[2] * tc.WY + (b0[1] - y0)) * tc.WX + (b0[0] - x0);
-        for (int cz = 0; cz < nzb; ++cz)
+        auto slots = [&](int cz) {
 #pragma unroll
           for (int bb = 0; bb < 3; ++bb) {
             const T oyz = oy[bb] * oz[cz];
@@ -860,6 +867,13 @@ __global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ it
               sz += v * e.z;
             }
           }
+        };
+        if (nzb == 3) {  // the usual 3D case, fully unrolled
+#pragma unroll
+          for (int cz = 0; cz < 3; ++cz) slots(cz);
+        } else {
+          for (int cz = 0; cz < nzb; ++cz) slots(cz);
+        }
       } else {
         for (int k = b0[2]; k <= b1[2]; ++k) {
           const T oz = ov_axis(cl[2], chh[2], k);
