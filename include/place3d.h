@@ -217,13 +217,18 @@ int place3d_eval_objective_and_grad(place3d_handle *h, place3d_result *out,
  * - degree thresholds and reduction forms of the wirelength stage: the nets
  *   are held in degree classes (2, 3, 4, 5-6, 7-8, 9-12, 13-16, 17-24,
  *   25-32, 33-48, 49-64, 65-128, above 128); every run of adjacent classes
- *   up to 128 pins is timed `repeats` times with every (lanes per net, pins
- *   per lane) form that fits it, and the split into runs (one launch each)
- *   with the least total time is kept (dynamic programming); nets above 128
+ *   up to 128 pins is timed alone `repeats` times with every (lanes per
+ *   net, pins per lane) form that fits it; the splits into runs (one launch
+ *   each) with the least total time, with runs of at most two classes and
+ *   with single classes are found by dynamic programming, and of these up
+ *   to three plans the one whose whole evaluations (one graph launch each,
+ *   beside the density path as usual) run fastest is kept; nets above 128
  *   pins keep the chunked form;
  * - with PLACE3D_FP32_TC, the tile width (64 or 128 columns) of each of the
- *   four tensor-core product groups.
- * Results are unchanged up to floating-point summation order. */
+ *   four tensor-core product groups (each group timed alone).
+ * The timed evaluations run at the current positions, so afterwards
+ * place3d_get_result reports them.  Results are unchanged up to
+ * floating-point summation order. */
 int place3d_autotune(place3d_handle *h, int repeats);
 
 /* The wirelength launch groups and their forms: writes up to cap entries of

@@ -801,20 +801,22 @@ __global__ void __launch_bounds__(256) k_scatter_tiles(const int2 *__restrict__ 
   }
 }
 
-// ---- a10 + a9 + a11 for the cells of one work item, field from shared memory ----
-// Writes (gx, gy, gz, 0) per instance into the interleaved buffer g4 (one
-// 16- or 32-byte write per cell); k_split_grad copies it to the caller's
-// arrays with coalesced stores.  Cells covering at most 3 bins per axis sum
-// the window with 3 overlaps per axis computed once.
+// ---- a10 (density part) for the cells of one work item, field from shared memory ----
+// Writes each cell's lambda-weighted density force (lambda dgx, lambda dgy,
+// lambda dgz, 0) into the interleaved buffer d4 (one 16- or 32-byte write
+// per cell).  Nothing here depends on the wirelength path, so the gather
+// runs while that path is still going; k_combine adds the two per instance
+// once both are done.  Cells covering at most 3 bins per axis sum the window
+// with 3 overlaps per axis computed once.
 template <typename T>
 __global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ items, const int *__restrict__ nitems,
                                                      const int *__restrict__ start,
                                                      const TileRec<T> *__restrict__ rec, DensC<T> c, TileC tc,
-                                                     const V4<T> *__restrict__ e4, const V4<T> *__restrict__ acc,
-                                                     FinalC<T> fc, V4<T> *__restrict__ g4) {
+                                                     const V4<T> *__restrict__ e4, FinalC<T> fc,
+                                                     V4<T> *__restrict__ d4) {
   extern __shared__ __align__(16) unsigned char fwin_raw[];
   V4<T> *fw = reinterpret_cast<V4<T> *>(fwin_raw);
-  __shared__ T g_sh, lam_sh[4];
+  __shared__ T lam_sh[4];
   if ((int)blockIdx.x >= *nitems) return;
   const int2 it = items[blockIdx.x];
   int x0, y0;
@@ -826,15 +828,12 @@ __global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ it
     if (xx >= 0 && xx < c.nx && yy >= 0 && yy < c.ny) e = e4[((size_t)zz * c.ny + yy) * c.nx + xx];
     fw[k] = e;
   }
-  if (threadIdx.x == 0) g_sh = g_scale_t<T>(fc.scal);
   if (threadIdx.x < 4) lam_sh[threadIdx.x] = fc.lam_dev[threadIdx.x];
   __syncthreads();
-  const T g = g_sh;
   const int c0 = start[it.x] + it.y * kChunk, c1 = min(start[it.x + 1], c0 + kChunk);
   for (int s = c0 + threadIdx.x; s < c1; s += blockDim.x) {
     const TileRec<T> r = rec[s];
-    const int i = r.idx_flags & 0xffffff, f = (r.idx_flags >> 24) & 0xff;
-    const V4<T> a = acc[i];
+    const int i = r.idx_flags & 0xffffff;
     T cl[3], chh[3];
     int b0[3], b1[3];
     T sx = 0, sy = 0, sz = 0;
@@ -894,51 +893,43 @@ __global__ void __launch_bounds__(256) k_final_tiles(const int2 *__restrict__ it
     const T kk = -r.om * fc.volb;
     // 2D mode: the layer is the cuboid's z bin (0 bottom, 1 top, 2 HBT)
     const T lam = fc.mode2d ? lam_sh[1 + (int)r.lo[2]] : lam_sh[0];
-    T ozg = g * a.z + fc.alpha * a.w + lam * (kk * sz);
-    if ((f & 2) || fc.mode2d) ozg = T(0);
-    V4<T> o;
-    o.x = a.x + lam * (kk * sx);
-    o.y = a.y + lam * (kk * sy);
-    o.z = ozg;
-    o.w = T(0);
-    g4[i] = o;
+    d4[i] = V4<T>{lam * (kk * sx), lam * (kk * sy), lam * (kk * sz), T(0)};
   }
 }
 
-// Final gradient of the macros into g4 (their density part comes from mgrad).
+// The macros' lambda-weighted density force into d4 (from mgrad).
 template <typename T>
 __global__ void k_final_macros(int nm, const int *__restrict__ macro_ids, const V4<T> *__restrict__ pos,
-                               const uint8_t *__restrict__ flags, const double *__restrict__ mgrad,
-                               const V4<T> *__restrict__ acc, FinalC<T> fc, T zmid, V4<T> *__restrict__ g4) {
+                               const double *__restrict__ mgrad, FinalC<T> fc, T zmid, V4<T> *__restrict__ d4) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= nm) return;
   const int i = macro_ids[m];
-  const T g = g_scale_t<T>(fc.scal);
   // 2D mode: the weight of the macro's die layer
   const T lam = fc.mode2d ? fc.lam_dev[pos[i].z > zmid ? 2 : 1] : fc.lam_dev[0];
   T dgx, dgy, dgz;
   macro_force(mgrad, m, fc.volb, dgx, dgy, dgz);
-  const V4<T> a = acc[i];
-  T ozg = g * a.z + fc.alpha * a.w + lam * dgz;
-  if ((flags[i] & 2) || fc.mode2d) ozg = T(0);
-  V4<T> o;
-  o.x = a.x + lam * dgx;
-  o.y = a.y + lam * dgy;
-  o.z = ozg;
-  o.w = T(0);
-  g4[i] = o;
+  d4[i] = V4<T>{lam * dgx, lam * dgy, lam * dgz, T(0)};
 }
 
-// Interleaved gradient -> the caller's three arrays (coalesced).
+// a9 + a11 per instance, coalesced: x, y = WL + the density force from d4;
+// z = g FD + alpha dp(z)/dz + the density force (0 for z-fixed instances and
+// in 2D mode), written to the caller's three arrays.
 template <typename T, typename TO>
-__global__ void __launch_bounds__(256) k_split_grad(int n, const V4<T> *__restrict__ g4, TO *__restrict__ gx,
-                                                    TO *__restrict__ gy, TO *__restrict__ gz) {
+__global__ void __launch_bounds__(256) k_combine(int n, const V4<T> *__restrict__ acc, const V4<T> *__restrict__ d4,
+                                                 const uint8_t *__restrict__ flags, FinalC<T> fc,
+                                                 TO *__restrict__ gx, TO *__restrict__ gy, TO *__restrict__ gz) {
+  __shared__ T g_sh;
+  if (threadIdx.x == 0) g_sh = g_scale_t<T>(fc.scal);  // once per block
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const V4<T> v = g4[i];
-  gx[i] = (TO)v.x;
-  gy[i] = (TO)v.y;
-  gz[i] = (TO)v.z;
+  const V4<T> a = acc[i], d = d4[i];
+  const T g = g_sh;
+  T ozg = g * a.z + fc.alpha * a.w + d.z;
+  if ((flags[i] & 2) || fc.mode2d) ozg = T(0);
+  gx[i] = (TO)(a.x + d.x);
+  gy[i] = (TO)(a.y + d.y);
+  gz[i] = (TO)ozg;
 }
 
 }  // namespace p3d

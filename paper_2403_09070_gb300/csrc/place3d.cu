@@ -102,7 +102,7 @@ struct place3d_handle {
   size_t smem_scatter = 0, smem_final = 0;
   int2 *tkey = nullptr, *titems = nullptr;
   void *trec = nullptr;  // TileRec<T>[n] in tile order
-  void *g4 = nullptr;    // interleaved gradient V4<T>[n]
+  void *g4 = nullptr;    // interleaved density force V4<T>[n] (tiled final)
   int *tcount = nullptr, *tstart = nullptr, *tnitems = nullptr;
   int n = 0, nm = 0, nnet = 0, npin = 0;
   int nx = 0, ny = 0, nz = 0;
@@ -546,29 +546,20 @@ void run_transforms_tc(place3d_handle *h, cudaStream_t s, cudaStream_t rs) {
   }
 }
 
-// Tiled final assembly: the cells' gather into g4, then (once the macros'
-// field gather on the macro stream is done, when split) the macros' rows of
-// g4, then one coalesced copy of g4 into the three output arrays.
-template <typename T, typename TO>
-int launch_final_tiles(place3d_handle *h, cudaStream_t s, cudaStream_t ms, bool split, const DensC<T> &dc,
-                       const FinalC<T> &fc, TO *ox, TO *oy, TO *oz) {
+// Tiled final assembly, density part (before the join: nothing in it waits
+// for the wirelength path): the cells' windowed field gather writes their
+// lambda-weighted density force into d4 (the handle's g4 buffer), and the
+// macros' rows follow on the stream of their field gather.
+template <typename T>
+void launch_final_dens(place3d_handle *h, cudaStream_t s, cudaStream_t mgs, const DensC<T> &dc, const FinalC<T> &fc) {
   k_final_tiles<T><<<h->max_items, 256, h->smem_final, s>>>(h->titems, h->tnitems, h->tstart, as<TileRec<T>>(h->trec),
-                                                            dc, h->tcfg, as<V4<T>>(h->e4), as<V4<T>>(h->acc), fc,
-                                                            as<V4<T>>(h->g4));
+                                                            dc, h->tcfg, as<V4<T>>(h->e4), fc, as<V4<T>>(h->g4));
   count_launch(h, ST_FINAL);
   if (h->nm > 0) {
-    if (split) {
-      P3D_CUDA(h, cudaEventRecord(h->ev_mgrad, ms));
-      P3D_CUDA(h, cudaStreamWaitEvent(s, h->ev_mgrad, 0));
-    }
-    k_final_macros<T><<<grid_for(h->nm, 128), 128, 0, s>>>(h->nm, h->macro_ids, as<V4<T>>(h->pos), h->flags_d,
-                                                           h->mgrad, as<V4<T>>(h->acc), fc, dc.zmid,
-                                                           as<V4<T>>(h->g4));
+    k_final_macros<T><<<grid_for(h->nm, 128), 128, 0, mgs>>>(h->nm, h->macro_ids, as<V4<T>>(h->pos), h->mgrad, fc,
+                                                             dc.zmid, as<V4<T>>(h->g4));
     count_launch(h, ST_FINAL);
   }
-  k_split_grad<T, TO><<<grid_for(h->n, 256), 256, 0, s>>>(h->n, as<V4<T>>(h->g4), ox, oy, oz);
-  count_launch(h, ST_FINAL);
-  return PLACE3D_OK;
 }
 
 // Batch capture with a shared wirelength stage: the scalars, the WL
@@ -713,30 +704,42 @@ int eval_impl(place3d_handle *h, void *gx, void *gy, void *gz, int dtype, int me
                                                                as<V4<T>>(h->size), dc, h->suffix, h->nb, h->mgrad);
     count_launch(h, ST_MACRO_GATHER);
   }
+  FinalC<T> fc;
+  fc.alpha = (T)h->alpha;
+  fc.volb = (T)(h->mode2d ? h->wb * h->hb : h->wb * h->hb * h->db);  // 2D: bin area
+  fc.scal = h->scal;
+  fc.lam_dev = lam_dev<T>(h);
+  fc.g = T(0);
+  fc.mode2d = h->mode2d ? 1 : 0;
+  // host-mapped outputs: the per-cell gather, whose stores to host memory
+  // (coalesced, by instance) overlap its computation
+  const bool tiled_final = n > 0 && h->tiles && !h->host_out;
+  if (tiled_final) {
+    StageScope sc(h, ST_FINAL, s);
+    cudaStream_t mgs = h->nm > 0 && h->macro_direct ? mcs : s;  // the macros' field gather ran there
+    launch_final_dens<T>(h, s, mgs, dc, fc);
+    if (mgs != s) {
+      P3D_CUDA(h, cudaEventRecord(h->ev_mgrad, mgs));
+      P3D_CUDA(h, cudaStreamWaitEvent(s, h->ev_mgrad, 0));
+    }
+  }
   // ---------------- join + final assembly ----------------
   P3D_CUDA(h, cudaStreamWaitEvent(s, bh ? bh->wl_done : h->ev_join, 0));
   {
     StageScope sc(h, ST_FINAL, s);
-    FinalC<T> fc;
-    fc.alpha = (T)h->alpha;
-    fc.volb = (T)(h->mode2d ? h->wb * h->hb : h->wb * h->hb * h->db);  // 2D: bin area
-    fc.scal = h->scal;
-    fc.lam_dev = lam_dev<T>(h);
-    fc.g = T(0);
-    fc.mode2d = h->mode2d ? 1 : 0;
     const bool direct = mem == PLACE3D_MEM_DEVICE && gx && gy && gz;
     const int odt = direct ? dtype : (sizeof(T) == 8 ? PLACE3D_F64 : PLACE3D_F32);
     void *ox = direct ? gx : h->gout;
     void *oy = direct ? gy : (char *)h->gout + (size_t)n * sizeof(T);
     void *oz = direct ? gz : (char *)h->gout + (size_t)2 * n * sizeof(T);
-    // host-mapped outputs: the per-cell gather, whose stores to host memory
-    // (coalesced, by instance) overlap its computation; the tiled gather
-    // would write them afterwards in one copy pass over the CPU-GPU link
-    if (n > 0 && h->tiles && !h->host_out) {
-      const int rt = odt == PLACE3D_F64
-                         ? launch_final_tiles<T, double>(h, s, ms, split, dc, fc, (double *)ox, (double *)oy, (double *)oz)
-                         : launch_final_tiles<T, float>(h, s, ms, split, dc, fc, (float *)ox, (float *)oy, (float *)oz);
-      if (rt != PLACE3D_OK) return rt;
+    if (tiled_final) {  // the wirelength part and the density force, per instance
+      if (odt == PLACE3D_F64)
+        k_combine<T, double><<<grid_for(n, 256), 256, 0, s>>>(n, as<V4<T>>(h->acc), as<V4<T>>(h->g4), h->flags_d, fc,
+                                                              (double *)ox, (double *)oy, (double *)oz);
+      else
+        k_combine<T, float><<<grid_for(n, 256), 256, 0, s>>>(n, as<V4<T>>(h->acc), as<V4<T>>(h->g4), h->flags_d, fc,
+                                                             (float *)ox, (float *)oy, (float *)oz);
+      count_launch(h, ST_FINAL);
     } else if (n > 0) {
       if (odt == PLACE3D_F64)
         k_final<T, double><<<grid_for(n, 256), 256, 0, s>>>(n, as<V4<T>>(h->pos), as<V4<T>>(h->size), h->flags_d,
@@ -1048,6 +1051,13 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
     while (d > kClassMax[k]) ++k;
     cls[k].push_back(e);
   }
+  // within a class, nets by ascending degree (stable): the nets that one
+  // warp of a group form reduces then have about the same degree, so the
+  // warp skips the pin slots that none of its nets fills
+  for (auto &v : cls)
+    std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
+      return p->net_start[a + 1] - p->net_start[a] < p->net_start[b + 1] - p->net_start[b];
+    });
   std::vector<int> order, new_start(1, 0);
   for (int k = 0; k < kNumClasses; ++k) {
     if (cls[k].empty()) continue;
@@ -1703,15 +1713,14 @@ int place3d_autotune(place3d_handle *h, int repeats) {
     return ms;
   };
   // Degree thresholds and forms: the classes up to 128 pins are split into
-  // runs of adjacent classes, one launch each; best[j] is the least total
-  // time of classes 0..j-1 over all splits and forms (dynamic programming
-  // over the measured time of every run with every form that fits it).
+  // runs of adjacent classes, one launch each.  Every run with every form
+  // that fits it is timed alone; best[j] is the least total time of classes
+  // 0..j-1 over all splits whose runs span at most `span` classes (dynamic
+  // programming over the measured times).
   const int nf = (int)h->fine.size();
   int nd = nf;
   while (nd > 0 && h->fine[nd - 1].dmax > 128) --nd;
-  std::vector<double> best(nd + 1, 1e300);
-  std::vector<int> from(nd + 1, 0), fG(nd + 1, 0), fP(nd + 1, 0);
-  best[0] = 0;
+  std::vector<float> tt((size_t)nd * nd * kNumForms, -1.0f);  // [i][j][form], -1: does not fit
   bool bad = false;
   for (int j = 0; j < nd && !bad; ++j)
     for (int i = 0; i <= j && !bad; ++i)
@@ -1723,21 +1732,86 @@ int place3d_autotune(place3d_handle *h, int repeats) {
           bad = true;
           break;
         }
-        if (best[i] + t < best[j + 1]) {
-          best[j + 1] = best[i] + t;
-          from[j + 1] = i;
-          fG[j + 1] = G;
-          fP[j + 1] = PPL;
-        }
+        tt[((size_t)i * nd + j) * kNumForms + f] = t;
       }
-  if (!bad && nd > 0) {
+  auto plan_for = [&](int span) {
+    std::vector<double> best(nd + 1, 1e300);
+    std::vector<int> from(nd + 1, 0), fG(nd + 1, 0), fP(nd + 1, 0);
+    best[0] = 0;
+    for (int j = 0; j < nd; ++j)
+      for (int i = std::max(0, j - span + 1); i <= j; ++i)
+        for (int f = 0; f < kNumForms; ++f) {
+          const float t = tt[((size_t)i * nd + j) * kNumForms + f];
+          if (t >= 0 && best[i] + t < best[j + 1]) {
+            best[j + 1] = best[i] + t;
+            from[j + 1] = i;
+            fG[j + 1] = kForms[f][0];
+            fP[j + 1] = kForms[f][1];
+          }
+        }
     std::vector<Bucket> groups;
     for (int j = nd; j > 0; j = from[j]) groups.push_back(make_group_of(h, from[j], j - 1, fG[j], fP[j]));
     std::reverse(groups.begin(), groups.end());
     if (nd < nf) groups.push_back(make_group_of(h, nd, nf - 1, 0, 0));  // above 128 pins: the chunked form
-    h->buckets = groups;
-  }
+    return groups;
+  };
+  // the tensor-core products' tile widths, each product group timed alone
   if (!bad && h->tc && p3d_tc::autotune(h->tc, w, repeats) != 0) bad = true;
+  if (!bad && nd > 0) {
+    // Candidates: the least total time alone, and the same with runs of at
+    // most 2 classes and of single classes.  The wirelength launches run
+    // beside the density path, where finer runs can do better than their
+    // serial times say, so the candidates are compared by timing whole
+    // evaluations (one graph launch each, at the current positions) and the
+    // fastest is kept.
+    std::vector<std::vector<Bucket>> cand;
+    for (int span : {nd, 2, 1}) {
+      std::vector<Bucket> g = plan_for(span);
+      bool dup = false;
+      for (const auto &c : cand) {
+        bool same = c.size() == g.size();
+        for (size_t k = 0; same && k < g.size(); ++k)
+          same = c[k].dmax == g[k].dmax && c[k].G == g[k].G && c[k].PPL == g[k].PPL;
+        dup = dup || same;
+      }
+      if (!dup) cand.push_back(g);
+    }
+    size_t pick = 0;
+    if (cand.size() > 1 && !h->profiling && h->n > 0) {
+      const size_t es = h->esz, n = (size_t)h->n;
+      void *tgt[3] = {h->gout, (char *)h->gout + n * es, (char *)h->gout + 2 * n * es};
+      std::vector<float> tbest(cand.size(), 1e30f);
+      const int rounds = std::max(repeats, 3), per = 4;
+      for (int r = 0; r <= rounds && !bad; ++r)  // round 0 captures and warms up
+        for (size_t k = 0; k < cand.size() && !bad; ++k) {
+          h->buckets = cand[k];
+          ++h->version;
+          if (eval_via_graph(h, tgt, false) != PLACE3D_OK) {
+            bad = true;
+            break;
+          }
+          cudaEventRecord(e0, h->stream);
+          for (int q = 0; q < per; ++q)
+            if (eval_via_graph(h, tgt, false) != PLACE3D_OK) bad = true;
+          cudaEventRecord(e1, h->stream);
+          if (bad || cudaEventSynchronize(e1) != cudaSuccess) {
+            bad = true;
+            break;
+          }
+          float t = 0;
+          cudaEventElapsedTime(&t, e0, e1);
+          if (r > 0) tbest[k] = std::min(tbest[k], t);
+        }
+      for (size_t k = 1; k < cand.size(); ++k)
+        if (tbest[k] < tbest[pick]) pick = k;
+      // the timed evaluations ran at the current positions: their results
+      // (scalars, and the gradient in the handle's buffer) are the last
+      // evaluation's
+      h->have_result = !bad;
+      h->gout_fresh = !bad;
+    }
+    h->buckets = cand[pick];
+  }
   ++h->version;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

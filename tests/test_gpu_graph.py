@@ -106,7 +106,9 @@ def test_batch_sees_set_params_of_one_instance():
 
 def test_autotuned_plan_keeps_results_and_transfers():
     """place3d_autotune regroups the degree classes and picks the forms and
-    the tensor-core tile widths; the results stay those of the default plan
+    the tensor-core tile widths (comparing candidate plans by whole
+    evaluations at the current positions, which get_result then reports);
+    the results stay those of the default plan
     (up to summation order), and the plan set on a second handle
     (place3d_set_wl_plan, place3d_set_tc_tiles) reproduces them."""
     p = synth.make_problem("cells_200k")
@@ -118,6 +120,7 @@ def test_autotuned_plan_keeps_results_and_transfers():
         r0 = h.eval(*g0)
         default = h.wl_forms()
         h.autotune(1)
+        ra = h.get_result()  # the autotuner's timed evaluations at these positions
         plan, tiles = h.wl_forms(), h.tc_tiles()
         g1 = [np.zeros(n, np.float32) for _ in range(3)]
         r1 = h.eval(*g1)
@@ -126,6 +129,7 @@ def test_autotuned_plan_keeps_results_and_transfers():
     assert len(tiles) == 4 and set(tiles) <= {64, 128}
     assert plan[-1][0] == default[-1][0]  # every degree is covered
     assert r1["obj"] == pytest.approx(r0["obj"], rel=1e-5)
+    assert ra["obj"] == pytest.approx(r0["obj"], rel=1e-5)
     for a, b in zip(g1, g0):
         np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-4 * np.abs(b).max())
     with P.Place3D(p, precision="fp32_tc") as h2:
