@@ -589,6 +589,125 @@ __device__ __forceinline__ T moved_sh(const WlShared<T, GR> &sh, int grp, int a,
   return hall > ps + po ? hall : ps + po;
 }
 
+// ---- the three per-pin phases and the per-net step, shared by the group
+// forms (pins held in registers) and the streamed forms (pins read again in
+// every phase) ----
+
+// Phase 2 of one pin: its exponentials (shifts from the staged extremes)
+// into the WA sums; in 2D mode an HBT adds to both partial nets.
+template <typename T, int GR, bool M2D>
+__device__ __forceinline__ void pin_phase_sums(Sums<T> &S, const Pin<T> &q, const WlShared<T, GR> &sh, int grp,
+                                               const WlC<T> &c) {
+  T ex[6];
+  if (M2D && q.hbt) {  // 2D mode: a member of both partial nets
+    pin_exps_sh(q, sh, grp, c, ex, false);
+    sums_add(S, q, ex, false);
+    pin_exps_sh(q, sh, grp, c, ex, true);
+    sums_add(S, q, ex, true);
+  } else {
+    pin_exps_sh(q, sh, grp, c, ex, q.top);
+    sums_add(S, q, ex, q.top);
+  }
+}
+
+// The net step (one lane per net, after the sums are reduced): the eq.
+// wl-obj branch and the WA averages, staged as per-side gradient
+// coefficients, and the net's contributions to the scalar rows.
+template <typename T, int GR, bool M2D>
+__device__ __forceinline__ void net_phase(WlShared<T, GR> &sh, int grp, const Sums<T> &S, const WlC<T> &c,
+                                          T (&vals)[4]) {
+  NetExt<T> X;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      Ext<T> &e = X.e[a][q];
+      const int b = F_EXT + (a * 2 + q) * 4;
+      e.mx1 = sh.f[b + 0][grp];
+      e.mx2 = sh.f[b + 1][grp];
+      e.mn1 = sh.f[b + 2][grp];
+      e.mn2 = sh.f[b + 3][grp];
+      e.amx = e.amn = 0;
+    }
+  X.zmx = sh.f[F_Z + 0][grp];
+  X.zmn = sh.f[F_Z + 1][grp];
+  X.ntop = sh.i[I_NTOP][grp];
+  X.n = sh.i[I_N][grp];
+  const NetScal<T> N = net_scalars(X, S, c);
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const AxisNet<T> &A = N.ax[a];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int b = F_COEF + (a * 2 + q) * 4;
+      sh.f[b + 0][grp] = A.all ? A.f[q] * A.iSP : A.iSs[q];
+      sh.f[b + 1][grp] = A.all ? A.M : A.Ms[q];
+      sh.f[b + 2][grp] = A.all ? A.h[q] * A.iSM : A.iSm[q];
+      sh.f[b + 3][grp] = A.all ? A.m : A.ms[q];
+    }
+  }
+  sh.f[F_ZC + 0][grp] = N.izS1;
+  sh.f[F_ZC + 1][grp] = N.zM;
+  sh.f[F_ZC + 2][grp] = N.izS2;
+  sh.f[F_ZC + 3][grp] = N.zm;
+  sh.f[F_WCUR][grp] = N.wcur;
+  vals[0] = N.ax[0].what + N.ax[1].what;
+  vals[1] = M2D ? T(0) : N.pz;
+  vals[2] = N.wcur;
+  vals[3] = (X.ntop > 0 && X.ntop < X.n) ? T(1) : T(0);
+}
+
+// Phase 3 of one pin, 2D mode: split-branch coefficients of each partial
+// net, no FD, no z.
+template <typename T, int GR>
+__device__ __forceinline__ void pin_phase_out_2d(const Pin<T> &p, const WlShared<T, GR> &sh, int grp,
+                                                 const WlC<T> &c, V4<T> *__restrict__ acc) {
+  T g[2] = {T(0), T(0)};
+  const T v[2] = {p.px, p.py};
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    if (!(p.hbt || (side == 1) == p.top)) continue;
+    T ex[6];
+    pin_exps_sh(p, sh, grp, c, ex, side == 1);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const int b = F_COEF + (a * 2 + side) * 4;
+      const T A = sh.f[b + 0][grp], B = sh.f[b + 1][grp], C = sh.f[b + 2][grp], D = sh.f[b + 3][grp];
+      g[a] += (ex[2 * a] * A) * (T(1) + (v[a] - B) * c.inv_g) - (ex[2 * a + 1] * C) * (T(1) - (v[a] - D) * c.inv_g);
+    }
+  }
+  acc_add(acc + p.inst, g[0], g[1], T(0), T(0));
+}
+
+// Phase 3 of one pin, 3D mode: WA gradient on x, y and z, and the
+// incremental FD step (eq. fda-grad) from the staged extremes.
+template <typename T, int GR>
+__device__ __forceinline__ void pin_phase_out(const Pin<T> &p, int slot, const WlShared<T, GR> &sh, int grp,
+                                              const WlC<T> &c, int ntop, int n, T wcur, V4<T> *__restrict__ acc) {
+  T ex[6];  // recomputed: keeping them live across the reductions costs registers
+  pin_exps_sh(p, sh, grp, c, ex, p.top);
+  const int s = p.top ? 1 : 0;
+  T g[2];
+  const T v[2] = {p.px, p.py};
+  T cA[2], cB[2], cC[2], cD[2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const int b = F_COEF + (a * 2 + s) * 4;
+    cA[a] = sh.f[b + 0][grp];
+    cB[a] = sh.f[b + 1][grp];
+    cC[a] = sh.f[b + 2][grp];
+    cD[a] = sh.f[b + 3][grp];
+  }
+  const T ep[2] = {ex[0], ex[2]}, em[2] = {ex[1], ex[3]};
+  wa_grad2(ep, em, v, cA, cB, cC, cD, c.inv_g, g);  // both axes in step
+  const T gz = wa_grad(p.pz, ex[4], sh.f[F_ZC + 0][grp], sh.f[F_ZC + 1][grp], ex[5], sh.f[F_ZC + 2][grp],
+                       sh.f[F_ZC + 3][grp], c.inv_gz);
+  const int ns = s ? ntop : n - ntop, no = n - ns;
+  const T wm = moved_sh(sh, grp, 0, s, ns, no, slot, p.qx) + moved_sh(sh, grp, 1, s, ns, no, slot, p.qy);
+  const T fd = c.fd_scale * (s ? (wcur - wm) : (wm - wcur));
+  acc_add(acc + p.inst, g[0], g[1], fd, gz);
+}
+
 // M2D: multi-die 2D mode (compile-time, so the 3D kernels carry none of the
 // HBT and partial-net-only cases).
 // Body for block bid (a batched launch passes the block's place in its
@@ -648,117 +767,21 @@ __device__ __forceinline__ void wl_group_body(int net0, int nnets, const int *__
     S.init();
 #pragma unroll
     for (int r = 0; r < PPL; ++r)
-      if (has[r]) {
-        T ex[6];
-        const Pin<T> &q = pin[r];
-        if (M2D && q.hbt) {  // 2D mode: a member of both partial nets
-          pin_exps_sh(q, sh, grp, c, ex, false);
-          sums_add(S, q, ex, false);
-          pin_exps_sh(q, sh, grp, c, ex, true);
-          sums_add(S, q, ex, true);
-        } else {
-          pin_exps_sh(q, sh, grp, c, ex, q.top);
-          sums_add(S, q, ex, q.top);
-        }
-      }
+      if (has[r]) pin_phase_sums<T, GR, M2D>(S, pin[r], sh, grp, c);
     S.template shfl_reduce<G>();
-    if (d >= 2 && lane == 0) {
-      // net scalars (eq. wl-obj branch, WA averages), staged as per-side coefficients
-      NetExt<T> X;
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          Ext<T> &e = X.e[a][q];
-          const int b = F_EXT + (a * 2 + q) * 4;
-          e.mx1 = sh.f[b + 0][grp];
-          e.mx2 = sh.f[b + 1][grp];
-          e.mn1 = sh.f[b + 2][grp];
-          e.mn2 = sh.f[b + 3][grp];
-          e.amx = e.amn = 0;
-        }
-      X.zmx = sh.f[F_Z + 0][grp];
-      X.zmn = sh.f[F_Z + 1][grp];
-      X.ntop = sh.i[I_NTOP][grp];
-      X.n = sh.i[I_N][grp];
-      const NetScal<T> N = net_scalars(X, S, c);
-#pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const AxisNet<T> &A = N.ax[a];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int b = F_COEF + (a * 2 + q) * 4;
-          sh.f[b + 0][grp] = A.all ? A.f[q] * A.iSP : A.iSs[q];
-          sh.f[b + 1][grp] = A.all ? A.M : A.Ms[q];
-          sh.f[b + 2][grp] = A.all ? A.h[q] * A.iSM : A.iSm[q];
-          sh.f[b + 3][grp] = A.all ? A.m : A.ms[q];
-        }
-      }
-      sh.f[F_ZC + 0][grp] = N.izS1;
-      sh.f[F_ZC + 1][grp] = N.zM;
-      sh.f[F_ZC + 2][grp] = N.izS2;
-      sh.f[F_ZC + 3][grp] = N.zm;
-      sh.f[F_WCUR][grp] = N.wcur;
-      vals[0] = N.ax[0].what + N.ax[1].what;
-      vals[1] = M2D ? T(0) : N.pz;
-      vals[2] = N.wcur;
-      vals[3] = (X.ntop > 0 && X.ntop < X.n) ? T(1) : T(0);
-    }
+    if (d >= 2 && lane == 0) net_phase<T, GR, M2D>(sh, grp, S, c, vals);
   }
   __syncwarp();
   if (M2D && d >= 2) {
-    // 2D mode: split-branch coefficients of each partial net, no FD, no z
 #pragma unroll
     for (int r = 0; r < PPL; ++r)
-      if (has[r]) {
-        const Pin<T> &p = pin[r];
-        T g[2] = {T(0), T(0)};
-        const T v[2] = {p.px, p.py};
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-          if (!(p.hbt || (side == 1) == p.top)) continue;
-          T ex[6];
-          pin_exps_sh(p, sh, grp, c, ex, side == 1);
-#pragma unroll
-          for (int a = 0; a < 2; ++a) {
-            const int b = F_COEF + (a * 2 + side) * 4;
-            const T A = sh.f[b + 0][grp], B = sh.f[b + 1][grp], C = sh.f[b + 2][grp], D = sh.f[b + 3][grp];
-            g[a] += (ex[2 * a] * A) * (T(1) + (v[a] - B) * c.inv_g) -
-                    (ex[2 * a + 1] * C) * (T(1) - (v[a] - D) * c.inv_g);
-          }
-        }
-        acc_add(acc + p.inst, g[0], g[1], T(0), T(0));
-      }
+      if (has[r]) pin_phase_out_2d(pin[r], sh, grp, c, acc);
   } else if (!M2D && d >= 2) {
     const int ntop = sh.i[I_NTOP][grp], n = sh.i[I_N][grp];
     const T wcur = sh.f[F_WCUR][grp];
 #pragma unroll
     for (int r = 0; r < PPL; ++r)
-      if (has[r]) {
-        const Pin<T> &p = pin[r];
-        T ex[6];  // recomputed: keeping them live across the reductions costs registers
-        pin_exps_sh(p, sh, grp, c, ex, p.top);
-        const int s = p.top ? 1 : 0;
-        T g[2];
-        const T v[2] = {p.px, p.py};
-        T cA[2], cB[2], cC[2], cD[2];
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-          const int b = F_COEF + (a * 2 + s) * 4;
-          cA[a] = sh.f[b + 0][grp];
-          cB[a] = sh.f[b + 1][grp];
-          cC[a] = sh.f[b + 2][grp];
-          cD[a] = sh.f[b + 3][grp];
-        }
-        const T ep[2] = {ex[0], ex[2]}, em[2] = {ex[1], ex[3]};
-        wa_grad2(ep, em, v, cA, cB, cC, cD, c.inv_g, g);  // both axes in step
-        const T gz = wa_grad(p.pz, ex[4], sh.f[F_ZC + 0][grp], sh.f[F_ZC + 1][grp], ex[5], sh.f[F_ZC + 2][grp],
-                             sh.f[F_ZC + 3][grp], c.inv_gz);
-        const int ns = s ? ntop : n - ntop, no = n - ns, slot = lane + r * G;
-        const T wm = moved_sh(sh, grp, 0, s, ns, no, slot, p.qx) + moved_sh(sh, grp, 1, s, ns, no, slot, p.qy);
-        const T fd = c.fd_scale * (s ? (wcur - wm) : (wm - wcur));
-        acc_add(acc + p.inst, g[0], g[1], fd, gz);
-      }
+      if (has[r]) pin_phase_out(pin[r], lane + r * G, sh, grp, c, ntop, n, wcur, acc);
   }
   warp_sum_part<4>(vals, part, bid);  // (W^_Bi, p^(z), W_Bi, crossing) rows
 }
