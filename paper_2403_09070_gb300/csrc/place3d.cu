@@ -1,6 +1,7 @@
 // place3d C ABI: problem validation and upload, net-degree buckets, transform
-// matrices, and the evaluation schedule (density path on the caller's stream,
-// wirelength path on a second stream, joined before the final assembly).
+// matrices, and the evaluation schedule (density path on a high-priority
+// stream, wirelength path on two side streams, joined before the final
+// per-instance combine).
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
@@ -72,6 +73,8 @@ struct place3d_handle {
   bool mode2d = false;                 // multi-die 2D placement (eq. 2d-place)
   double lam_layer[3] = {0, 0, 0};     // 2D mode: density weights of the three layers
   cudaStream_t stream = nullptr, side = nullptr;
+  cudaStream_t side2 = nullptr;  // second wirelength stream: the launch groups alternate between the two
+  cudaEvent_t ev_w2a = nullptr, ev_w2b = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_dens = nullptr;
   // density weights on the device: double[4] then float[4] (lambda, then the
   // 2D layer weights), written on the handle's stream by set_params /
@@ -596,10 +599,22 @@ int eval_impl(place3d_handle *h, void *gx, void *gy, void *gz, int dtype, int me
       StageScope sc(h, ST_WIRELENGTH, w);
       P3D_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(V4<T>) * (size_t)std::max(n, 1), w));
       const WlC<T> c = wl_consts<T>(h);
+      // the launch groups alternate between two streams: one group's tail
+      // (its last blocks) overlaps the next group's start
       int rows = 0;
+      cudaStream_t w2 = serial ? w : h->side2;
+      if (w2 != w) {
+        P3D_CUDA(h, cudaEventRecord(h->ev_w2a, w));
+        P3D_CUDA(h, cudaStreamWaitEvent(w2, h->ev_w2a, 0));
+      }
+      int kb = 0;
       for (const Bucket &b : h->buckets) {
-        rows += launch_wl<T>(h, b, b.G, b.PPL, w, c, as<T>(h->part_w) + 4 * (size_t)rows);
+        rows += launch_wl<T>(h, b, b.G, b.PPL, (kb++ & 1) ? w2 : w, c, as<T>(h->part_w) + 4 * (size_t)rows);
         count_launch(h, ST_WIRELENGTH);
+      }
+      if (w2 != w) {
+        P3D_CUDA(h, cudaEventRecord(h->ev_w2b, w2));
+        P3D_CUDA(h, cudaStreamWaitEvent(w, h->ev_w2b, 0));
       }
       if (rows > 0) {
         k_sum_parts<4, T><<<sum_grid(rows), 256, 0, w>>>(as<T>(h->part_w), rows, h->scal + S_WL_BI);
@@ -842,6 +857,9 @@ void free_all(place3d_handle *h) {
   if (h->ev_z) cudaEventDestroy(h->ev_z);
   if (h->mac) cudaStreamDestroy(h->mac);
   if (h->side) cudaStreamDestroy(h->side);
+  if (h->side2) cudaStreamDestroy(h->side2);
+  if (h->ev_w2a) cudaEventDestroy(h->ev_w2a);
+  if (h->ev_w2b) cudaEventDestroy(h->ev_w2b);
   if (h->dens) cudaStreamDestroy(h->dens);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->egexec) cudaGraphExecDestroy(h->egexec);
@@ -1213,6 +1231,9 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
   int prio_lo = 0, prio_hi = 0;
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->side2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_w2a, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_w2b, cudaEventDisableTiming) != cudaSuccess ||
       cudaStreamCreateWithPriority(&h->dens, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
@@ -2425,6 +2446,7 @@ void place3d_destroy(place3d_handle *h) {
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
   if (h->side) cudaStreamSynchronize(h->side);
+  if (h->side2) cudaStreamSynchronize(h->side2);
   if (h->dens) cudaStreamSynchronize(h->dens);
   free_all(h);
   delete h;
