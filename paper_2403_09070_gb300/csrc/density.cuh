@@ -539,17 +539,86 @@ __device__ __forceinline__ int tile_of(const DensC<T> &c, const TileC &tc, T X, 
   return ty * tc.ntx + tx;
 }
 
+constexpr int kCountBlock = 512;  // threads of a tile-count block
+
+// Exclusive scan of the tile counts into the tile starts and the work-item
+// list (items of at most kChunk cells per tile), by one block of
+// kCountBlock threads; the counts are read from the L2 (they were written by
+// other blocks' atomics).
+__device__ __forceinline__ void tile_scan_block(int ntiles, const int *__restrict__ count, int *__restrict__ start,
+                                                int2 *__restrict__ items, int *__restrict__ nitems) {
+  __shared__ int s_cells[kCountBlock / 32], s_items[kCountBlock / 32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, per = (ntiles + kCountBlock - 1) / kCountBlock;
+  const int t0 = t * per, t1 = min(ntiles, t0 + per);
+  int cells = 0, its = 0;
+  for (int k = t0; k < t1; ++k) {
+    const int ck = __ldcg(count + k * kCountPad);
+    cells += ck;
+    its += (ck + kChunk - 1) / kChunk;
+  }
+  int ic = cells, ii = its;  // inclusive warp scans
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int vc = __shfl_up_sync(0xffffffffu, ic, d), vi = __shfl_up_sync(0xffffffffu, ii, d);
+    if (lane >= d) {
+      ic += vc;
+      ii += vi;
+    }
+  }
+  if (lane == 31) {
+    s_cells[warp] = ic;
+    s_items[warp] = ii;
+  }
+  __syncthreads();
+  if (warp == 0) {  // the warp totals, scanned by the first warp
+    constexpr int NW = kCountBlock / 32;
+    int wc = lane < NW ? s_cells[lane] : 0, wi = lane < NW ? s_items[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int vc = __shfl_up_sync(0xffffffffu, wc, d), vi = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= d) {
+        wc += vc;
+        wi += vi;
+      }
+    }
+    if (lane < NW) {
+      s_cells[lane] = wc;
+      s_items[lane] = wi;
+    }
+  }
+  __syncthreads();
+  int cs = ic - cells + (warp ? s_cells[warp - 1] : 0), is = ii - its + (warp ? s_items[warp - 1] : 0);
+  for (int k = t0; k < t1; ++k) {
+    const int ck = __ldcg(count + k * kCountPad);
+    start[k] = cs;
+    const int nc = (ck + kChunk - 1) / kChunk;
+    for (int j = 0; j < nc; ++j) items[is + j] = make_int2(k, j);
+    cs += ck;
+    is += nc;
+  }
+  if (t == kCountBlock - 1) {
+    start[ntiles] = cs;
+    *nitems = is;
+  }
+}
+
 // Tile of every cell and its rank inside the tile (macros get -1).  Each
 // block of kCountBlock threads takes kCountPerThread cells per thread (few,
 // large blocks: the per-(block, tile) global atomics contend less), ranks them in a
 // shared-memory histogram, then reserves its range of every tile it holds
-// cells of with one global atomic per (block, tile).
-constexpr int kCountBlock = 512;
+// cells of with one global atomic per (block, tile).  The last block to
+// finish (a ticket counter after a memory fence; no block waits for
+// another) scans the counts into the tile starts and the work items.
+// count holds the ntiles counters (one per kCountPad ints) and then the
+// ticket counter; all are zero on entry.
 template <typename T>
 __global__ void __launch_bounds__(kCountBlock) k_tile_count(int n, const V4<T> *__restrict__ pos,
                                                      const uint8_t *__restrict__ flags, DensC<T> c, TileC tc,
-                                                     int ntiles, int *__restrict__ count, int2 *__restrict__ key) {
+                                                     int ntiles, int *__restrict__ count, int2 *__restrict__ key,
+                                                     int *__restrict__ start, int2 *__restrict__ items,
+                                                     int *__restrict__ nitems) {
   extern __shared__ int hist[];
+  __shared__ int last;
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
   __syncthreads();
   const int base = blockIdx.x * blockDim.x * kCountPerThread + threadIdx.x;
@@ -576,43 +645,14 @@ __global__ void __launch_bounds__(kCountBlock) k_tile_count(int n, const V4<T> *
     const int i = base + u * blockDim.x;
     if (i < n) key[i] = tl[u] >= 0 ? make_int2(tl[u], hist[tl[u]] + rk[u]) : make_int2(-1, 0);
   }
-}
-
-// Exclusive scan of the tile counts and the work-item list (one block).
-static __global__ void __launch_bounds__(1024) k_tile_scan(int ntiles, const int *__restrict__ count,
-                                                           int *__restrict__ start, int2 *__restrict__ items,
-                                                           int *__restrict__ nitems) {
-  __shared__ int s_cells[1024], s_items[1024];
-  const int t = threadIdx.x, per = (ntiles + 1023) / 1024;
-  const int t0 = t * per, t1 = min(ntiles, t0 + per);
-  int cells = 0, its = 0;
-  for (int k = t0; k < t1; ++k) {
-    cells += count[k * kCountPad];
-    its += (count[k * kCountPad] + kChunk - 1) / kChunk;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(count + ntiles * kCountPad, 1) == (int)gridDim.x - 1;
   }
-  s_cells[t] = cells;
-  s_items[t] = its;
   __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {  // inclusive Hillis-Steele scan
-    const int a = t >= off ? s_cells[t - off] : 0, b = t >= off ? s_items[t - off] : 0;
-    __syncthreads();
-    s_cells[t] += a;
-    s_items[t] += b;
-    __syncthreads();
-  }
-  int cs = s_cells[t] - cells, is = s_items[t] - its;
-  for (int k = t0; k < t1; ++k) {
-    const int ck = count[k * kCountPad];
-    start[k] = cs;
-    const int nc = (ck + kChunk - 1) / kChunk;
-    for (int j = 0; j < nc; ++j) items[is + j] = make_int2(k, j);
-    cs += ck;
-    is += nc;
-  }
-  if (t == 1023) {
-    start[ntiles] = s_cells[1023];
-    *nitems = s_items[1023];
-  }
+  if (!last) return;
+  __threadfence();
+  tile_scan_block(ntiles, count, start, items, nitems);
 }
 
 // One cell in tile order: its stretched cuboid in bin units (unclipped, as

@@ -636,15 +636,15 @@ int eval_impl(place3d_handle *h, void *gx, void *gy, void *gz, int dtype, int me
     StageScope sc(h, ST_SCATTER, s);
     P3D_CUDA(h, cudaMemsetAsync(h->q, 0, sizeof(long long) * h->nb, s));
     if (n > 0 && h->tiles) {
-      P3D_CUDA(h, cudaMemsetAsync(h->tcount, 0, sizeof(int) * kCountPad * h->ntiles, s));
+      P3D_CUDA(h, cudaMemsetAsync(h->tcount, 0, sizeof(int) * kCountPad * (h->ntiles + 1), s));
       k_tile_count<T><<<grid_for(n, kCountBlock * kCountPerThread), kCountBlock, sizeof(int) * h->ntiles, s>>>(
-          n, as<V4<T>>(h->pos), h->flags_d, dc, h->tcfg, h->ntiles, h->tcount, h->tkey);
-      k_tile_scan<<<1, 1024, 0, s>>>(h->ntiles, h->tcount, h->tstart, h->titems, h->tnitems);
+          n, as<V4<T>>(h->pos), h->flags_d, dc, h->tcfg, h->ntiles, h->tcount, h->tkey, h->tstart, h->titems,
+          h->tnitems);
       k_tile_place<T><<<grid_for(n, 256), 256, 0, s>>>(n, h->tkey, h->tstart, as<V4<T>>(h->pos), as<V4<T>>(h->size),
                                                        h->flags_d, dc, as<TileRec<T>>(h->trec));
       k_scatter_tiles<T><<<h->max_items, 256, h->smem_scatter, s>>>(h->titems, h->tnitems, h->tstart,
                                                                     as<TileRec<T>>(h->trec), dc, h->tcfg, h->q);
-      for (int k = 0; k < 4; ++k) count_launch(h, ST_SCATTER);
+      for (int k = 0; k < 3; ++k) count_launch(h, ST_SCATTER);
     } else if (n > 0) {
       k_scatter_cells<T><<<grid_for(2 * (long long)n, 256), 256, 0, s>>>(n, as<V4<T>>(h->pos), as<V4<T>>(h->size), h->flags_d,
                                                           dc, h->q);
@@ -1171,7 +1171,7 @@ int place3d_create(const place3d_problem *p, int device, void *cuda_stream, plac
       {(void **)&h->tkey, sizeof(int2) * nn},
       {&h->trec, (p->precision == PLACE3D_FP64 ? sizeof(TileRec<double>) : sizeof(TileRec<float>)) * nn},
       {&h->g4, v4 * nn},
-      {(void **)&h->tcount, sizeof(int) * kCountPad * (size_t)std::max(h->ntiles, 1)},
+      {(void **)&h->tcount, sizeof(int) * kCountPad * (size_t)(h->ntiles + 1)},  // counters, then the ticket
       {(void **)&h->tstart, sizeof(int) * (size_t)(h->ntiles + 1)},
       {(void **)&h->titems, sizeof(int2) * (size_t)std::max(h->max_items, 1)}, {(void **)&h->tnitems, sizeof(int)}};
   for (auto &a : allocs) {
@@ -1802,7 +1802,7 @@ int place3d_autotune(place3d_handle *h, int repeats) {
       const size_t es = h->esz, n = (size_t)h->n;
       void *tgt[3] = {h->gout, (char *)h->gout + n * es, (char *)h->gout + 2 * n * es};
       std::vector<float> tbest(cand.size(), 1e30f);
-      const int rounds = std::max(repeats, 3), per = 4;
+      const int rounds = std::max(2 * repeats, 6), per = 8;  // the candidates differ by a few percent
       for (int r = 0; r <= rounds && !bad; ++r)  // round 0 captures and warms up
         for (size_t k = 0; k < cand.size() && !bad; ++k) {
           h->buckets = cand[k];
