@@ -218,7 +218,8 @@ int place3d_eval_objective_and_grad(place3d_handle *h, place3d_result *out,
  *   are held in degree classes (2, 3, 4, 5-6, 7-8, 9-12, 13-16, 17-24,
  *   25-32, 33-48, 49-64, 65-128, above 128); every run of adjacent classes
  *   up to 128 pins is timed alone `repeats` times with every (lanes per
- *   net, pins per lane) form that fits it; the splits into runs (one launch
+ *   net, pins per lane) form that fits it (of forms within 3 % of a run's
+ *   fastest, the one with the fewest lanes per net); the splits into runs (one launch
  *   each) with the least total time, with runs of at most two classes and
  *   with single classes are found by dynamic programming, and of these up
  *   to three plans the one whose whole evaluations (one graph launch each,

@@ -287,13 +287,23 @@ __global__ void __launch_bounds__(256) k_densify(int nxy, int nz, const long lon
   T v[2] = {0, 0};
   if (t < nxy) {
     long long acc = 0;
-    for (int z = 0; z < nz; ++z) {
-      const size_t id = (size_t)z * nxy + t;
-      if (A) acc += A[id];
-      const T r = r_ll2f(q[id] + acc, T(0)) * (T)(1.0 / kFixedScale);
-      rho.put(id, r);
-      v[0] += r > T(1) ? r - T(1) : T(0);
-      v[1] += r;
+    for (int z0 = 0; z0 < nz; z0 += 4) {  // the loads of up to four layers issued together
+      long long qv[4], av[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const size_t id = (size_t)(z0 + u) * nxy + t;
+        qv[u] = z0 + u < nz ? q[id] : 0;
+        av[u] = A && z0 + u < nz ? A[id] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (z0 + u >= nz) break;
+        acc += av[u];
+        const T r = r_ll2f(qv[u] + acc, T(0)) * (T)(1.0 / kFixedScale);
+        rho.put((size_t)(z0 + u) * nxy + t, r);
+        v[0] += r > T(1) ? r - T(1) : T(0);
+        v[1] += r;
+      }
     }
   }
   if (part) warp_sum_part<2>(v, part);

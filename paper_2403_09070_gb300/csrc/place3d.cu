@@ -1755,6 +1755,24 @@ int place3d_autotune(place3d_handle *h, int repeats) {
         }
         tt[((size_t)i * nd + j) * kNumForms + f] = t;
       }
+  // Near ties between forms of one run (within 3 %, inside the timing
+  // noise) go to the fewest lanes per net: fewer shuffle rounds and more
+  // nets per warp, which measured faster beside the density path.
+  for (int j = 0; j < nd && !bad; ++j)
+    for (int i = 0; i <= j; ++i) {
+      float *row = &tt[((size_t)i * nd + j) * kNumForms];
+      float tmin = 1e30f;
+      for (int f = 0; f < kNumForms; ++f)
+        if (row[f] >= 0) tmin = std::min(tmin, row[f]);
+      int keep = -1;
+      for (int f = 0; f < kNumForms; ++f)
+        if (row[f] >= 0 && row[f] <= 1.03f * tmin &&
+            (keep < 0 || kForms[f][0] < kForms[keep][0] ||
+             (kForms[f][0] == kForms[keep][0] && row[f] < row[keep])))
+          keep = f;
+      for (int f = 0; f < kNumForms; ++f)
+        if (f != keep) row[f] = -1.0f;
+    }
   auto plan_for = [&](int span) {
     std::vector<double> best(nd + 1, 1e300);
     std::vector<int> from(nd + 1, 0), fG(nd + 1, 0), fP(nd + 1, 0);
