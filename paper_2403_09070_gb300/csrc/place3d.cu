@@ -1821,7 +1821,7 @@ int place3d_autotune(place3d_handle *h, int repeats) {
       void *tgt[3] = {h->gout, (char *)h->gout + n * es, (char *)h->gout + 2 * n * es};
       std::vector<float> tbest(cand.size(), 1e30f);
       const int rounds = std::max(2 * repeats, 6), per = 8;  // the candidates differ by a few percent
-      for (int r = 0; r <= rounds && !bad; ++r)  // round 0 captures and warms up
+      for (int r = 0; r <= rounds && !bad; ++r)  // pass 0 captures and warms up
         for (size_t k = 0; k < cand.size() && !bad; ++k) {
           h->buckets = cand[k];
           ++h->version;
