@@ -456,20 +456,26 @@ __global__ void __launch_bounds__(256) k_final(int n, const V4<T> *__restrict__ 
                                                TO *__restrict__ gx, TO *__restrict__ gy,
                                                TO *__restrict__ gz, int skip_macros) {
   __shared__ T g_sh, lam_sh[4];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // the instance's loads issued before the block waits for g
+  uint8_t f = 0;
+  V4<T> p{}, sz4{};
+  if (i < n) {
+    f = flags[i];
+    p = pos[i];
+    sz4 = size[i];
+  }
   if (threadIdx.x == 0) g_sh = g_scale_t<T>(fc.scal);  // once per block
   if (threadIdx.x < 4) lam_sh[threadIdx.x] = fc.lam_dev[threadIdx.x];
   __syncthreads();
   fc.g = g_sh;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const uint8_t f = flags[i];
-  const V4<T> p = pos[i];
   T dgx = 0, dgy = 0, dgz = 0;
   if (f & 1) {
     if (skip_macros) return;
     macro_force(mgrad, macro_slot[i], fc.volb, dgx, dgy, dgz);
   } else {
-    const Box<T> b = inst_box(c, p.x, p.y, p.z, size[i], false, (f & 4) != 0);
+    const Box<T> b = inst_box(c, p.x, p.y, p.z, sz4, false, (f & 4) != 0);
     T cl[3], chh[3];
     int b0[3], b1[3];
     if (clip_axis(b.lo[0], b.hi[0], c.fnx, c.nx, cl[0], chh[0], b0[0], b1[0]) &&
@@ -969,14 +975,21 @@ __global__ void __launch_bounds__(256) k_combine(int n, const V4<T> *__restrict_
                                                  const uint8_t *__restrict__ flags, FinalC<T> fc,
                                                  TO *__restrict__ gx, TO *__restrict__ gy, TO *__restrict__ gz) {
   __shared__ T g_sh;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // the instance's loads issued before the block waits for g
+  V4<T> a{}, d{};
+  uint8_t f = 0;
+  if (i < n) {
+    a = acc[i];
+    d = d4[i];
+    f = flags[i];
+  }
   if (threadIdx.x == 0) g_sh = g_scale_t<T>(fc.scal);  // once per block
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const V4<T> a = acc[i], d = d4[i];
   const T g = g_sh;
   T ozg = g * a.z + fc.alpha * a.w + d.z;
-  if ((flags[i] & 2) || fc.mode2d) ozg = T(0);
+  if ((f & 2) || fc.mode2d) ozg = T(0);
   gx[i] = (TO)(a.x + d.x);
   gy[i] = (TO)(a.y + d.y);
   gz[i] = (TO)ozg;
