@@ -20,6 +20,7 @@
 #include "transform.cuh"
 #include "wirelength.cuh"
 #include "nesterov.cuh"
+#include "plan.h"
 #include "batch.cuh"
 
 using namespace p3d;
@@ -1755,42 +1756,15 @@ int place3d_autotune(place3d_handle *h, int repeats) {
         }
         tt[((size_t)i * nd + j) * kNumForms + f] = t;
       }
-  // Near ties between forms of one run (within 3 %, inside the timing
-  // noise) go to the fewest lanes per net: fewer shuffle rounds and more
-  // nets per warp, which measured faster beside the density path.
-  for (int j = 0; j < nd && !bad; ++j)
-    for (int i = 0; i <= j; ++i) {
-      float *row = &tt[((size_t)i * nd + j) * kNumForms];
-      float tmin = 1e30f;
-      for (int f = 0; f < kNumForms; ++f)
-        if (row[f] >= 0) tmin = std::min(tmin, row[f]);
-      int keep = -1;
-      for (int f = 0; f < kNumForms; ++f)
-        if (row[f] >= 0 && row[f] <= 1.03f * tmin &&
-            (keep < 0 || kForms[f][0] < kForms[keep][0] ||
-             (kForms[f][0] == kForms[keep][0] && row[f] < row[keep])))
-          keep = f;
-      for (int f = 0; f < kNumForms; ++f)
-        if (f != keep) row[f] = -1.0f;
-    }
+  // near ties between forms of one run (within 3 %) go to the fewest lanes per net
+  int lanes[kNumForms];
+  for (int f = 0; f < kNumForms; ++f) lanes[f] = kForms[f][0];
+  if (!bad) p3d_plan::break_ties(tt, nd, kNumForms, lanes, 0.03f);
   auto plan_for = [&](int span) {
-    std::vector<double> best(nd + 1, 1e300);
-    std::vector<int> from(nd + 1, 0), fG(nd + 1, 0), fP(nd + 1, 0);
-    best[0] = 0;
-    for (int j = 0; j < nd; ++j)
-      for (int i = std::max(0, j - span + 1); i <= j; ++i)
-        for (int f = 0; f < kNumForms; ++f) {
-          const float t = tt[((size_t)i * nd + j) * kNumForms + f];
-          if (t >= 0 && best[i] + t < best[j + 1]) {
-            best[j + 1] = best[i] + t;
-            from[j + 1] = i;
-            fG[j + 1] = kForms[f][0];
-            fP[j + 1] = kForms[f][1];
-          }
-        }
     std::vector<Bucket> groups;
-    for (int j = nd; j > 0; j = from[j]) groups.push_back(make_group_of(h, from[j], j - 1, fG[j], fP[j]));
-    std::reverse(groups.begin(), groups.end());
+    for (const p3d_plan::Run &r : p3d_plan::best_split(tt, nd, kNumForms, span))
+      groups.push_back(make_group_of(h, r.i, r.j, kForms[r.f][0], kForms[r.f][1]));
+    if (groups.empty()) return h->buckets;  // some class fits no form: keep the current plan
     if (nd < nf) groups.push_back(make_group_of(h, nd, nf - 1, 0, 0));  // above 128 pins: the chunked form
     return groups;
   };
